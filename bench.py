@@ -1,0 +1,311 @@
+"""Benchmark: walk-on-boundary path vertices per second on one GB300.
+
+Workload (the second configuration of the method's benchmark set): a
+non-convex star-shaped mesh (icosphere level 6, 81,920 triangles, radius
+1 + 0.3 * seeded real spherical harmonics up to degree 6), Dirichlet data
+g = 1 / |x - (3, 0, 0)|, double-layer formulation, query points on a
+256 x 256 z = 0 slice of [-1.3, 1.3]^2 clipped to the interior, 1,024 walks
+per point, up to 16 boundary vertices per walk, Philox seed 0.  A step is one
+wob_solve over all queries (walk kernel + per-query FP64 reduction); a path
+vertex is one line query.
+
+Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
+launching stream, with a 512 MB buffer written between steps to flush L2;
+max over ranks.  Under torchrun every rank solves its own replica (problem
+index = rank, independent random streams): weak scaling, no collective on
+the data path.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WoB path vertices/sec on 1 GB300"
+UNIT = "path vertices/s"
+WALKS, MAX_LEN, SEED = 1024, 16, 0
+X0 = (3.0, 0.0, 0.0)
+
+# Algorithmic per-event costs: lane operations of the FP32/INT32 pipes counted
+# from the traversal source (per interior node: two 3-slab box tests; per
+# triangle: the sheared edge functions, flags and hit test; per hit: one
+# Philox block and the key comparison; per line: axis, setup, FP64 refinement,
+# data term and accumulation), and the bytes fetched per node and triangle.
+OPS_NODE, OPS_TRI, OPS_HIT, OPS_LINE = 34, 41, 100, 235
+BYTES_NODE, BYTES_TRI = 64, 48
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _workload():
+    from paper_2305_04403_gb300 import inputs as I
+    v, f, shape = I.star_mesh(6)
+    q = I.star_slice_queries(shape, 256)
+    return v, f, q
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self) -> dict:
+        mhz, maxmhz, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1].split()[0]))
+                maxmhz = float(parts[2].split()[0])
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": maxmhz,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    v, f, q = _workload()
+    if args.queries:
+        q = q[:: max(1, len(q) // args.queries)][:args.queries].copy()
+    Q = q.shape[0]
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    prob = wob.Problem(bvh, kind=wob.DIRICHLET_DL, side=1, data_mode=wob.DATA_POINT, x0=X0,
+                       problem=rank)
+    qd = torch.from_numpy(q).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # algorithmic work of one step (deterministic walks: exact counts)
+    _, _, st = wob.solve_counted(prob, qd, WALKS, MAX_LEN, seed=SEED)
+    lines = st["lines"]
+
+    for _ in range(args.warmup):
+        wob.solve(prob, qd, WALKS, MAX_LEN, seed=SEED)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            est, var = wob.solve(prob, qd, WALKS, MAX_LEN, seed=SEED)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    clocks = clk.summary()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    qh = torch.from_numpy(q).pin_memory()
+    est_h = torch.empty(Q, dtype=torch.float64).pin_memory()
+    var_h = torch.empty(Q, dtype=torch.float64).pin_memory()
+    lib = wob.load_library()
+    import ctypes
+    pc = prob._c()
+
+    def host_step():
+        rc = lib.wob_solve_host(ctypes.byref(pc), ctypes.c_void_p(qh.data_ptr()), None, Q, WALKS,
+                                MAX_LEN, SEED, ctypes.c_void_p(est_h.data_ptr()),
+                                ctypes.c_void_p(var_h.data_ptr()),
+                                ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(lib.wob_last_error().decode())
+
+    host_step()
+    e2e_steps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host_step()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+
+    peaks, which = _peaks()
+    per_launch_s = total_ms / 1e3 / args.steps
+    ops = (st["node_visits"] * OPS_NODE + st["tri_tests"] * OPS_TRI + st["hits"] * OPS_HIT
+           + st["lines"] * OPS_LINE)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
+    achieved_ops = ops / per_launch_s / 1e12
+    bytes_step = st["node_visits"] * BYTES_NODE + st["tri_tests"] * BYTES_TRI
+    value = ws * lines * args.steps / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry / f64 accumulation",
+        "data": "synthetic (seeded star mesh, slice queries)",
+        "config": {"workload": f"star-shaped icosphere L6 (81,920 tris), z=0 slice Q={Q}, "
+                               f"{WALKS} walks, M={MAX_LEN}, Dirichlet double layer, g=1/|x-(3,0,0)|",
+                   "queries": Q, "walks": WALKS, "max_len": MAX_LEN, "leaf_size": args.leaf,
+                   "l2": "flushed (512 MB write) between timed steps",
+                   "parallelism": f"{ws} independent replica(s)"},
+        "clocks": clocks,
+        "e2e": {"value": ws * lines * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": Q * 12, "d2h_bytes_per_step": Q * 16},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
+                     "unit": "T lane-ops/s", "frac": achieved_ops / alu_peak,
+                     "traffic": None,
+                     "kernel": "k_dl_walks",
+                     "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
+                                    f"({which} sm_max_mhz)"},
+        "memory": {"l1_l2_bytes_per_step": bytes_step,
+                   "achieved_gbs": bytes_step / per_launch_s / 1e9,
+                   "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                   "per_line": {"nodes": st["node_visits"] / lines, "tris": st["tri_tests"] / lines,
+                                "hits": st["hits"] / lines, "flagged": st["flagged"] / lines}},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(v, f, q, args.cpu_queries)
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(v, f, q, nq: int) -> dict:
+    """The oracle as it stands, on the host cores, on a bounded sample."""
+    import oracle as O
+    sel = q[:: max(1, len(q) // nq)][:nq]
+    t0 = time.perf_counter()
+    r = O.dl_walks(v, f, sel, WALKS, MAX_LEN, seed=SEED, mode=O.DATA_POINT, x0=X0,
+                   want_lines=True)
+    dt = time.perf_counter() - t0
+    lines = int((r["line_m"] >= 0).sum())
+    return {"value": lines / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{len(sel)} queries x {WALKS} walks x up to {MAX_LEN} vertices "
+                      f"({lines} line queries, brute force over 81,920 triangles), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return None
+    import oracle as O
+    v, f, q = _workload()
+    sel = q[:: max(1, len(q) // args.cpu_queries)][:args.cpu_queries]
+    for _ in range(args.warmup):
+        O.dl_walks(v, f, sel[:1], 64, MAX_LEN, seed=SEED, mode=O.DATA_POINT, x0=X0)
+    t_total, lines_total = 0.0, 0
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.dl_walks(v, f, sel, WALKS // 8, MAX_LEN, seed=SEED, mode=O.DATA_POINT, x0=X0,
+                       walk_begin=i * (WALKS // 8), want_lines=True)
+        t_total += time.perf_counter() - t0
+        lines_total += int((r["line_m"] >= 0).sum())
+    value = lines_total / t_total
+    sample = (f"{len(sel)} queries x {WALKS // 8} walks x up to {MAX_LEN} vertices per step, "
+              f"brute force over 81,920 triangles")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "same mesh, data and walks as the GPU arm; bounded query "
+                                   "sample per step (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--leaf", type=int, default=4)
+    ap.add_argument("--cpu-queries", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="evenly subsample this many queries (profiling runs; 0 = all)")
+    args = ap.parse_args()
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

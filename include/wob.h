@@ -1,0 +1,235 @@
+/*
+ * wob.h -- C ABI of the GB300 walk-on-boundary (WoB) library.
+ *
+ * The library estimates solutions of Laplace boundary value problems on
+ * closed triangle meshes with the walk-on-boundary method of Sugimoto et al.,
+ * "A Practical Walk-on-Boundary Method for Boundary Value Problems"
+ * (SIGGRAPH 2023).  Every step of the estimator runs in the library's own
+ * CUDA kernels for sm_103a; this header uses plain pointers and sizes only.
+ *
+ * Conventions for every function:
+ *  - The return value is a status: WOB_OK (0) or a negative WOB_ERR_* code.
+ *    wob_last_error() returns a message for the calling thread's last error.
+ *    No C++ exception crosses this interface.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls enqueue work on it and return without synchronising,
+ *    except where noted ("synchronises").
+ *  - "device" pointers are CUDA device memory (for example a torch tensor's
+ *    data_ptr()); "host" pointers are ordinary host memory.  The library
+ *    never frees or keeps memory it did not allocate.
+ *  - Meshes: vertices float32 V x 3 (row-major), triangles int32 T x 3,
+ *    counter-clockwise when seen from outside the interior domain Omega, so
+ *    that (v1 - v0) x (v2 - v0) points out of Omega (the paper keeps normals
+ *    oriented outward from Omega for both interior and exterior problems,
+ *    Sec. 4.5.1).  The surface must be closed.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *    (seed_lo ^ problem, seed_hi) and counter (query, walk,
+ *    step << 16 | purpose << 12 | attempt, extra); results are a
+ *    deterministic function of (inputs, seed, walk range) and do not depend
+ *    on launch configuration.
+ */
+#ifndef WOB_H
+#define WOB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WOB_OK 0
+#define WOB_ERR_INVALID_ARG (-1)     /* bad pointer, size or enum value */
+#define WOB_ERR_CUDA (-2)            /* a CUDA runtime call failed */
+#define WOB_ERR_OOM (-3)             /* device allocation failed */
+#define WOB_ERR_TIMEOUT (-4)         /* a bounded device-side wait gave up */
+#define WOB_ERR_DEGENERATE_MESH (-5) /* non-finite vertex, bad index, zero-area
+                                        triangle or inward orientation */
+#define WOB_ERR_UNSUPPORTED (-6)     /* combination not implemented */
+#define WOB_ERR_DEVICE_CHECK (-7)    /* a device-side check fired (traversal
+                                        stack overflow) */
+
+/* Boundary-integral formulation (Table 1 of the paper). */
+typedef enum {
+    WOB_DIRICHLET_DL = 0, /* Dirichlet data, double-layer potential (Sec. 4.1) */
+    WOB_NEUMANN_SL = 1,   /* Neumann data, single-layer potential (Sec. 4.3) */
+    WOB_ROBIN_SL = 2      /* Robin data, single-layer potential (Sec. 4.3) */
+} wob_kind;
+
+/* How the boundary data is given. */
+typedef enum {
+    WOB_DATA_VERTEX_P1 = 0, /* per-vertex values, linear over each triangle */
+    WOB_DATA_POLY = 1,      /* field h = c0 + c.x + quadratic terms (poly[10]) */
+    WOB_DATA_POINT = 2      /* field h = scale / |x - x0| */
+} wob_data_mode;
+
+typedef struct wob_mesh_s *wob_mesh;
+typedef struct wob_bvh_s *wob_bvh;
+
+typedef struct {
+    int64_t V, T;
+    double bbox_lo[3], bbox_hi[3];
+    double L;        /* bounding-box diagonal */
+    double area;     /* total surface area |Gamma| */
+    double volume;   /* signed enclosed volume (> 0 for outward orientation) */
+    double max_edge; /* longest triangle edge */
+} wob_mesh_info;
+
+typedef struct {
+    int32_t leaf_size; /* max triangles per leaf, 1..8 (0 = default 4) */
+    int32_t reserved[7];
+} wob_bvh_params;
+
+typedef struct {
+    int64_t nodes;   /* reachable interior nodes */
+    int64_t leaves;  /* leaves */
+    int32_t depth;   /* maximum depth (root = 0) */
+    int32_t leaf_size;
+    int64_t bytes;   /* device bytes of nodes + leaf triangles */
+} wob_bvh_info;
+
+/*
+ * One boundary value problem.
+ *   kind/side: formulation and phi = +1 (interior) or -1 (exterior), Table 1.
+ *   alpha:     Robin coefficient (WOB_ROBIN_SL), Eq. (PoissonBC).
+ *   data:      Dirichlet data g (DL), Neumann flux dh/dn (NEUMANN_SL) or Robin
+ *              data dh/dn + alpha h (ROBIN_SL).  In the POLY and POINT modes
+ *              the library evaluates these from the harmonic field h; in the
+ *              VERTEX_P1 mode vertex_data (device, V floats) is the data itself.
+ *   poly:      coefficients of 1, x, y, z, x^2, y^2, z^2, xy, yz, zx.
+ *   problem:   stream index folded into the generator key.
+ *   tau:       near-degenerate line threshold relative to the mesh diagonal
+ *              (0 = default 2e-6); lines passing closer than tau*L to a
+ *              triangle edge are flagged in the debug outputs.
+ */
+typedef struct {
+    wob_bvh bvh;
+    int32_t kind;
+    int32_t side;
+    float alpha;
+    int32_t data_mode;
+    const float *vertex_data;
+    float poly[10];
+    float x0[3];
+    float scale;
+    uint32_t problem;
+    float tau;
+} wob_problem;
+
+/* Per-walk outputs for parity checks (each pointer device, may be NULL). */
+typedef struct {
+    double *per_walk;   /* Q x N walk values */
+    uint8_t *walk_flag; /* Q x N: 1 if any line of the walk was near-degenerate */
+    int32_t *line_m;    /* Q x N x M hit counts, -1 for lines not traced */
+} wob_debug_out;
+
+/* Counters of the most recent wob_solve_counted() call. */
+typedef struct {
+    int64_t lines;        /* line queries (DL) or area samples (SL) issued */
+    int64_t node_visits;  /* BVH interior nodes fetched */
+    int64_t tri_tests;    /* triangles tested */
+    int64_t hits;         /* intersections found */
+    int64_t flagged;      /* near-degenerate lines */
+} wob_stats;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int wob_version(void);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *wob_last_error(void);
+
+/*
+ * Upload a mesh and precompute per-triangle data (unit normals, areas and
+ * the area prefix sums used by area sampling).  `verts`/`tris` are device
+ * pointers if on_device != 0, host pointers otherwise; the library copies
+ * them.  Validates the mesh (finite vertices, indices in [0, V), non-zero
+ * areas, positive signed volume) and synchronises on `stream`.
+ * Errors: WOB_ERR_INVALID_ARG, WOB_ERR_DEGENERATE_MESH, WOB_ERR_OOM, WOB_ERR_CUDA.
+ */
+int wob_build_mesh(const float *verts, int64_t V, const int32_t *tris, int64_t T,
+                   int on_device, void *stream, wob_mesh *out);
+int wob_mesh_get_info(wob_mesh m, wob_mesh_info *out);
+void wob_destroy_mesh(wob_mesh m);
+
+/*
+ * Build the bounding-volume hierarchy used by the all-hits line queries of
+ * ray sampling (Sec. 4.4.1): a linear BVH over Morton-ordered triangle
+ * centroids (Karras 2012), bottom-up boxes, leaves of up to leaf_size
+ * triangles.  The BVH keeps a reference to the mesh; destroy the BVH first.
+ * Synchronises on `stream`.
+ */
+int wob_build_bvh(wob_mesh m, const wob_bvh_params *p, void *stream, wob_bvh *out);
+int wob_bvh_get_info(wob_bvh b, wob_bvh_info *out);
+void wob_destroy_bvh(wob_bvh b);
+
+/*
+ * Estimate u at Q query points with `walks` walks of at most `max_len`
+ * boundary vertices each (Sec. 4.1.1, 4.1.2, 4.3):
+ *   est[q] = mean of the walk values, var[q] = their unbiased sample variance
+ *   (the standard error is sqrt(var / walks)).
+ * queries: device, Q x 3 float.  query_prim: device, Q int32 (the triangle a
+ * query lies on, -1 off the boundary) or NULL; used only by the single-layer
+ * kinds, where it marks points on Gamma; must be NULL for WOB_DIRICHLET_DL.
+ * est, var: device, Q doubles.  walks >= 2, 1 <= max_len <= 4096.
+ * Allocates scratch of Q * walks doubles on `stream` (stream-ordered).
+ */
+int wob_solve(const wob_problem *prob, const float *queries, const int32_t *query_prim,
+              int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
+              double *var, void *stream);
+
+/*
+ * Walks walk_begin .. walk_begin + walks - 1 only, ACCUMULATED into device
+ * sum[q] += sum of walk values and sumsq[q] += sum of squares.  Calls over
+ * disjoint walk ranges combine exactly into the result of one larger call
+ * (up to summation order): the basis of progressive refinement.
+ */
+int wob_solve_range(const wob_problem *prob, const float *queries, const int32_t *query_prim,
+                    int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len,
+                    uint64_t seed, double *sum, double *sumsq, void *stream);
+
+/* As wob_solve, also writing the per-walk outputs of `dbg` (Q x walks). */
+int wob_solve_debug(const wob_problem *prob, const float *queries, const int32_t *query_prim,
+                    int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
+                    double *var, const wob_debug_out *dbg, void *stream);
+
+/* As wob_solve, counting traversal work into *stats (synchronises). */
+int wob_solve_counted(const wob_problem *prob, const float *queries, const int32_t *query_prim,
+                      int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
+                      double *var, wob_stats *stats, void *stream);
+
+/*
+ * wob_solve with HOST queries / query_prim / est / var: copies the inputs to
+ * the device, solves, copies the results back and synchronises.  Device
+ * buffers are allocated on `stream` and freed before returning.
+ */
+int wob_solve_host(const wob_problem *prob, const float *queries_host,
+                   const int32_t *query_prim_host, int64_t Q, int32_t walks, int32_t max_len,
+                   uint64_t seed, double *est_host, double *var_host, void *stream);
+
+/*
+ * All-hits queries of n explicit lines {o + t d, t real} (Sec. 4.4.1), all
+ * pointers device.  origins/dirs: n x 3 double (dirs unit length).
+ * exclude: n int32 triangle ids skipped (the point's own face), or NULL.
+ * keys: n x 3 uint32 (query, walk, step) addressing the hit-selection keys.
+ * Outputs (n each, any may be NULL except m): hit count m, sum of
+ * s = sign(omega . n) over all hits, picked triangle id (-1 if none), its s,
+ * its line parameter t and point y (n x 3), and the near-degenerate flag.
+ */
+int wob_trace_lines(wob_bvh b, const double *origins, const double *dirs,
+                    const int32_t *exclude, const uint32_t *keys, int64_t n, uint64_t seed,
+                    uint32_t problem, float tau, int32_t *m, int32_t *sum_s, int32_t *prim,
+                    int32_t *s, double *t, double *y, uint8_t *flag, void *stream);
+
+/* Line axes the walks use, for (query, walk, step) triples (device, n x 3)
+ * -> device n x 3 doubles.  Marsaglia (1972) sampling of the unit sphere. */
+int wob_line_axes(uint64_t seed, uint32_t problem, const uint32_t *qws, int64_t n, double *d,
+                  void *stream);
+
+/* Raw Philox4x32-10 blocks: ctr n x 4, key n x 2, out n x 4 (device). */
+int wob_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out,
+                      void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WOB_H */

@@ -82,11 +82,11 @@ def _load():
                                                P, P, P, P, P, P, P, ctypes.c_int]
             lib.oracle_trace_lines.restype = ctypes.c_int
             lib.oracle_dl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, P, I64,
-                                            I64, I64, I32, I32, U64, U32, D, D, P, P, P,
+                                            I64, I64, I32, I32, U64, U32, D, D, P, P, P, P,
                                             ctypes.c_int]
             lib.oracle_dl_walks.restype = ctypes.c_int
             lib.oracle_sl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, D, I32,
-                                            P, I64, I64, I64, I32, I32, U64, U32, P,
+                                            P, I64, I64, I64, I32, I32, U64, U32, P, P,
                                             ctypes.c_int]
             lib.oracle_sl_walks.restype = ctypes.c_int
             lib.oracle_reduce.argtypes = [P, I64, I32, P, P]
@@ -202,8 +202,9 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
              phi: int = 1, mode: int = DATA_POLY, vertex_data=None, poly=None, x0=None,
              scale: float = 1.0, q_offset: int = 0, walk_begin: int = 0, tau: float = TAU,
              graze: float = GRAZE, want_lines: bool = False, nthreads: int = 0) -> dict:
-    """Double-layer Dirichlet walks; returns per_walk (Q,N), flag (Q,N) and,
-    with want_lines, line_m (Q,N,M)."""
+    """Double-layer Dirichlet walks; returns per_walk (Q,N), flag (Q,N),
+    abs_terms (Q,N: sum over the walk's terms of |term|, the scale of its
+    rounding error) and, with want_lines, line_m (Q,N,M)."""
     v = _c(verts, np.float32)
     t = _c(tris, np.int32)
     q = _c(queries, np.float32).reshape(-1, 3)
@@ -212,13 +213,15 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     per_walk = np.empty((Q, walks), np.float64)
     flag = np.empty((Q, walks), np.uint8)
     line_m = np.empty((Q, walks, max_len), np.int32) if want_lines else None
+    abs_terms = np.empty((Q, walks), np.float64)
     rc = _load().oracle_dl_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
                                  _p(q), Q, q_offset, walk_begin, walks, max_len, seed, problem,
-                                 tau, graze, _p(per_walk), _p(flag), _p(line_m), nthreads)
+                                 tau, graze, _p(per_walk), _p(flag), _p(line_m), _p(abs_terms),
+                                 nthreads)
     del keep
     if rc != 0:
         raise RuntimeError("oracle_dl_walks failed")
-    out = dict(per_walk=per_walk, flag=flag)
+    out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
     if want_lines:
         out["line_m"] = line_m
     return out
@@ -227,21 +230,24 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
 def sl_walks(verts, tris, queries, walks: int, max_len: int, kind: int = KIND_NEUMANN_SL,
              alpha: float = 0.0, seed: int = 0, problem: int = 0, phi: int = 1,
              mode: int = DATA_POINT, vertex_data=None, poly=None, x0=None, scale: float = 1.0,
-             q_offset: int = 0, walk_begin: int = 0, nthreads: int = 0) -> np.ndarray:
-    """Single-layer Neumann / Robin walks with area sampling; (Q,N)."""
+             q_offset: int = 0, walk_begin: int = 0, nthreads: int = 0,
+             want_abs: bool = False):
+    """Single-layer Neumann / Robin walks with area sampling; per_walk (Q,N)
+    (and, with want_abs, the per-walk sum of |term|)."""
     v = _c(verts, np.float32)
     t = _c(tris, np.int32)
     q = _c(queries, np.float32).reshape(-1, 3)
     Q = q.shape[0]
     data, keep = _data(mode, vertex_data, poly, x0, scale)
     per_walk = np.empty((Q, walks), np.float64)
+    abs_terms = np.empty((Q, walks), np.float64)
     rc = _load().oracle_sl_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), kind,
                                  alpha, phi, _p(q), Q, q_offset, walk_begin, walks, max_len,
-                                 seed, problem, _p(per_walk), nthreads)
+                                 seed, problem, _p(per_walk), _p(abs_terms), nthreads)
     del keep
     if rc != 0:
         raise RuntimeError("oracle_sl_walks failed")
-    return per_walk
+    return (per_walk, abs_terms) if want_abs else per_walk
 
 
 def reduce(per_walk) -> tuple[np.ndarray, np.ndarray]:

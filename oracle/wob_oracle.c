@@ -396,11 +396,12 @@ static void trace_line(const mesh_t *M, const double o[3], const double d[3], in
 /* ------------------------------------------------------------------------ */
 static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const double x0[3],
                       uint32_t q, uint32_t walk, int32_t Mlen, uint64_t seed, uint32_t problem,
-                      double tauL, double graze, uint8_t *flag, int32_t *line_m)
+                      double tauL, double graze, uint8_t *flag, int32_t *line_m,
+                      double *abs_terms)
 {
     double x[3] = { x0[0], x0[1], x0[2] };
     int64_t exclude = -1;
-    double S = 0.0, P = 1.0, W0 = 0.0;
+    double S = 0.0, P = 1.0, W0 = 0.0, A = 0.0;
     *flag = 0;
     for (int32_t k = 0; k < Mlen; ++k) {
         double d[3];
@@ -418,9 +419,11 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
         double g = boundary_data(D, M, r.prim, r.y, r.b, n, KIND_DIRICHLET_DL, 0.0);
         double c = (k == Mlen - 1) ? (double)phi : 2.0 * (double)phi;
         S += P * c * g;
+        A += fabs(P * c * g);
         x[0] = r.y[0]; x[1] = r.y[1]; x[2] = r.y[2];
         exclude = r.prim;
     }
+    *abs_terms = fabs(W0) * A;
     return W0 * S;
 }
 
@@ -458,11 +461,11 @@ static void area_sample(const mesh_t *M, uint64_t seed, uint32_t problem, uint32
 
 static double sl_walk(const mesh_t *M, const oracle_data *D, int kind, double alpha, int32_t phi,
                       const double x0[3], uint32_t q, uint32_t walk, int32_t Mlen,
-                      uint64_t seed, uint32_t problem)
+                      uint64_t seed, uint32_t problem, double *abs_terms)
 {
     double x[3] = { x0[0], x0[1], x0[2] };
     double nx[3] = { 0.0, 0.0, 0.0 };
-    double S = 0.0, P = 1.0, W0 = 0.0;
+    double S = 0.0, P = 1.0, W0 = 0.0, Aabs = 0.0;
     const double four_pi = 4.0 * ORACLE_PI;
     for (int32_t k = 0; k < Mlen; ++k) {
         int64_t j;
@@ -485,9 +488,11 @@ static double sl_walk(const mesh_t *M, const oracle_data *D, int kind, double al
         double f = boundary_data(D, M, j, y, b, n, kind, alpha);
         double c = (k == Mlen - 1) ? (double)phi : 2.0 * (double)phi;
         S += P * c * f;
+        Aabs += fabs(P * c * f);
         x[0] = y[0]; x[1] = y[1]; x[2] = y[2];
         nx[0] = n[0]; nx[1] = n[1]; nx[2] = n[2];
     }
+    *abs_terms = fabs(W0) * Aabs;
     return W0 * S;
 }
 
@@ -601,7 +606,8 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
                     const oracle_data *D, int32_t phi, const float *queries, int64_t Q,
                     int64_t q_offset, int64_t walk_begin, int32_t N, int32_t Mlen,
                     uint64_t seed, uint32_t problem, double tau, double graze,
-                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, int nthreads)
+                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, double *abs_terms,
+                    int nthreads)
 {
     mesh_t M;
     if (mesh_init(&M, verts, V, tris, T, 0)) return -1;
@@ -618,9 +624,12 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
             for (int32_t k = 0; k < Mlen; ++k) lm[k] = -1;
         }
         uint8_t f;
+        double at;
         per_walk[i] = dl_walk(&M, D, phi, x0, (uint32_t)(q_offset + qi),
-                              (uint32_t)(walk_begin + w), Mlen, seed, problem, tauL, graze, &f, lm);
+                              (uint32_t)(walk_begin + w), Mlen, seed, problem, tauL, graze, &f, lm,
+                              &at);
         if (walk_flag) walk_flag[i] = f;
+        if (abs_terms) abs_terms[i] = at;
     }
     mesh_free(&M);
     return 0;
@@ -633,7 +642,7 @@ int oracle_sl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
                     const oracle_data *D, int32_t kind, double alpha, int32_t phi,
                     const float *queries, int64_t Q, int64_t q_offset, int64_t walk_begin,
                     int32_t N, int32_t Mlen, uint64_t seed, uint32_t problem,
-                    double *per_walk, int nthreads)
+                    double *per_walk, double *abs_terms, int nthreads)
 {
     mesh_t M;
     if (mesh_init(&M, verts, V, tris, T, 1)) return -1;
@@ -643,8 +652,10 @@ int oracle_sl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
     for (int64_t i = 0; i < total; ++i) {
         int64_t qi = i / N, w = i % N;
         double x0[3] = { queries[3 * qi], queries[3 * qi + 1], queries[3 * qi + 2] };
+        double at;
         per_walk[i] = sl_walk(&M, D, kind, alpha, phi, x0, (uint32_t)(q_offset + qi),
-                              (uint32_t)(walk_begin + w), Mlen, seed, problem);
+                              (uint32_t)(walk_begin + w), Mlen, seed, problem, &at);
+        if (abs_terms) abs_terms[i] = at;
     }
     mesh_free(&M);
     return 0;

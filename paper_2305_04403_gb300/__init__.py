@@ -1,1 +1,381 @@
-"""GB300-native walk-on-boundary (WoB) estimator."""
+"""GB300-native walk-on-boundary (WoB) estimator -- Python binding.
+
+Thin ctypes layer over ``libwob.so`` (built from ``csrc/`` for sm_103a by
+``paper_2305_04403_gb300.build``); every step of the estimator runs in the
+library's CUDA kernels.  Functions take and return torch tensors on the
+GPU (torch provides device memory and streams only) and carry the names of
+the C entry points in ``include/wob.h``.  If the library is not built the
+first call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
+    "WobError", "Mesh", "BVH", "Problem", "build_mesh", "build_bvh", "solve", "solve_range",
+    "solve_debug", "solve_counted", "solve_host", "trace_lines", "line_axes", "philox4x32_10",
+    "library_path", "load_library",
+]
+
+DIRICHLET_DL, NEUMANN_SL, ROBIN_SL = 0, 1, 2
+DATA_VERTEX_P1, DATA_POLY, DATA_POINT = 0, 1, 2
+
+_ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "DEGENERATE_MESH",
+           -6: "UNSUPPORTED", -7: "DEVICE_CHECK"}
+
+
+class WobError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"WOB_ERR_{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _MeshInfo(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_int64), ("T", ctypes.c_int64), ("bbox_lo", ctypes.c_double * 3),
+                ("bbox_hi", ctypes.c_double * 3), ("L", ctypes.c_double),
+                ("area", ctypes.c_double), ("volume", ctypes.c_double),
+                ("max_edge", ctypes.c_double)]
+
+
+class _BvhParams(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class _BvhInfo(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_int64), ("leaves", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("leaf_size", ctypes.c_int32), ("bytes", ctypes.c_int64)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("bvh", ctypes.c_void_p), ("kind", ctypes.c_int32), ("side", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("data_mode", ctypes.c_int32),
+                ("vertex_data", ctypes.c_void_p), ("poly", ctypes.c_float * 10),
+                ("x0", ctypes.c_float * 3), ("scale", ctypes.c_float),
+                ("problem", ctypes.c_uint32), ("tau", ctypes.c_float)]
+
+
+class _DebugOut(ctypes.Structure):
+    _fields_ = [("per_walk", ctypes.c_void_p), ("walk_flag", ctypes.c_void_p),
+                ("line_m", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("lines", ctypes.c_int64), ("node_visits", ctypes.c_int64),
+                ("tri_tests", ctypes.c_int64), ("hits", ctypes.c_int64),
+                ("flagged", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libwob.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build it with "
+                               "paper_2305_04403_gb300.build.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        P, I64, I32, U32, U64, F = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float)
+        sig = {
+            "wob_version": ([], ctypes.c_int),
+            "wob_last_error": ([], ctypes.c_char_p),
+            "wob_build_mesh": ([P, I64, P, I64, ctypes.c_int, P, ctypes.POINTER(P)], ctypes.c_int),
+            "wob_mesh_get_info": ([P, ctypes.POINTER(_MeshInfo)], ctypes.c_int),
+            "wob_destroy_mesh": ([P], None),
+            "wob_build_bvh": ([P, ctypes.POINTER(_BvhParams), P, ctypes.POINTER(P)], ctypes.c_int),
+            "wob_bvh_get_info": ([P, ctypes.POINTER(_BvhInfo)], ctypes.c_int),
+            "wob_destroy_bvh": ([P], None),
+            "wob_solve": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
+                          ctypes.c_int),
+            "wob_solve_range": ([ctypes.POINTER(_Problem), P, P, I64, I64, I32, I32, U64, P, P, P],
+                                ctypes.c_int),
+            "wob_solve_debug": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P,
+                                 ctypes.POINTER(_DebugOut), P], ctypes.c_int),
+            "wob_solve_counted": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P,
+                                   ctypes.POINTER(_Stats), P], ctypes.c_int),
+            "wob_solve_host": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
+                               ctypes.c_int),
+            "wob_trace_lines": ([P, P, P, P, P, I64, U64, U32, F, P, P, P, P, P, P, P, P],
+                                ctypes.c_int),
+            "wob_line_axes": ([U64, U32, P, I64, P, P], ctypes.c_int),
+            "wob_philox4x32_10": ([P, P, I64, P, P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load_library().wob_last_error()
+        raise WobError(rc, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(x, dtype):
+    """Contiguous CUDA tensor of dtype from a tensor or array."""
+    import torch
+    if isinstance(x, torch.Tensor):
+        t = x.to(device="cuda", dtype=dtype)
+    else:
+        t = torch.as_tensor(np.asarray(x), dtype=dtype, device="cuda")
+    return t.contiguous()
+
+
+class Mesh:
+    """A device-resident triangle mesh (wob_build_mesh)."""
+
+    def __init__(self, verts, tris, stream=None):
+        import torch
+        lib = load_library()
+        v = _dev(verts, torch.float32).reshape(-1, 3)
+        t = _dev(tris, torch.int32).reshape(-1, 3)
+        h = ctypes.c_void_p()
+        _check(lib.wob_build_mesh(_ptr(v), v.shape[0], _ptr(t), t.shape[0], 1, _stream(stream),
+                                  ctypes.byref(h)))
+        self._h = h
+        self.V, self.T = v.shape[0], t.shape[0]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _MeshInfo()
+        _check(load_library().wob_mesh_get_info(self._h, ctypes.byref(i)))
+        return dict(V=i.V, T=i.T, bbox_lo=list(i.bbox_lo), bbox_hi=list(i.bbox_hi), L=i.L,
+                    area=i.area, volume=i.volume, max_edge=i.max_edge)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.wob_destroy_mesh(h)
+            self._h = None
+
+
+class BVH:
+    """Bounding-volume hierarchy over a mesh (wob_build_bvh)."""
+
+    def __init__(self, mesh: Mesh, leaf_size: int = 4, stream=None):
+        lib = load_library()
+        p = _BvhParams()
+        p.leaf_size = leaf_size
+        h = ctypes.c_void_p()
+        _check(lib.wob_build_bvh(mesh.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.mesh = mesh  # keeps the mesh alive
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _BvhInfo()
+        _check(load_library().wob_bvh_get_info(self._h, ctypes.byref(i)))
+        return dict(nodes=i.nodes, leaves=i.leaves, depth=i.depth, leaf_size=i.leaf_size,
+                    bytes=i.bytes)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.wob_destroy_bvh(h)
+            self._h = None
+
+
+def build_mesh(verts, tris, stream=None) -> Mesh:
+    return Mesh(verts, tris, stream)
+
+
+def build_bvh(mesh: Mesh, leaf_size: int = 4, stream=None) -> BVH:
+    return BVH(mesh, leaf_size, stream)
+
+
+@dataclass
+class Problem:
+    """One boundary value problem (the wob_problem struct)."""
+    bvh: BVH
+    kind: int = DIRICHLET_DL
+    side: int = 1
+    alpha: float = 0.0
+    data_mode: int = DATA_POLY
+    vertex_data: object = None          # device float tensor (V,) in P1 mode
+    poly: tuple = (0.0,) * 10
+    x0: tuple = (0.0, 0.0, 0.0)
+    scale: float = 1.0
+    problem: int = 0
+    tau: float = 0.0
+    _keep: list = field(default_factory=list, repr=False)
+
+    def _c(self) -> _Problem:
+        import torch
+        p = _Problem()
+        p.bvh = self.bvh.handle
+        p.kind, p.side, p.alpha, p.data_mode = self.kind, self.side, self.alpha, self.data_mode
+        if self.vertex_data is not None:
+            vd = _dev(self.vertex_data, torch.float32)
+            self._keep = [vd]
+            p.vertex_data = vd.data_ptr()
+        for i, c in enumerate(self.poly):
+            p.poly[i] = float(c)
+        for i, c in enumerate(self.x0):
+            p.x0[i] = float(c)
+        p.scale, p.problem, p.tau = self.scale, self.problem, self.tau
+        return p
+
+
+def solve(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
+          query_prim=None, stream=None):
+    """wob_solve: (est, var) float64 CUDA tensors of length Q."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    qp = None if query_prim is None else _dev(query_prim, torch.int32)
+    Q = q.shape[0]
+    est = torch.empty(Q, dtype=torch.float64, device="cuda")
+    var = torch.empty(Q, dtype=torch.float64, device="cuda")
+    pc = problem._c()
+    _check(load_library().wob_solve(ctypes.byref(pc), _ptr(q), _ptr(qp), Q, walks, max_len,
+                                    seed, _ptr(est), _ptr(var), _stream(stream)))
+    return est, var
+
+
+def solve_range(problem: Problem, queries, walk_begin: int, walks: int, max_len: int,
+                sum_, sumsq, seed: int = 0, query_prim=None, stream=None):
+    """wob_solve_range: accumulates into the float64 tensors sum_ and sumsq."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    qp = None if query_prim is None else _dev(query_prim, torch.int32)
+    pc = problem._c()
+    _check(load_library().wob_solve_range(ctypes.byref(pc), _ptr(q), _ptr(qp), q.shape[0],
+                                          walk_begin, walks, max_len, seed, _ptr(sum_),
+                                          _ptr(sumsq), _stream(stream)))
+
+
+def solve_debug(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
+                query_prim=None, want_lines: bool = True, stream=None) -> dict:
+    """wob_solve_debug: est, var and per-walk values, flags and hit counts."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    qp = None if query_prim is None else _dev(query_prim, torch.int32)
+    Q = q.shape[0]
+    out = dict(est=torch.empty(Q, dtype=torch.float64, device="cuda"),
+               var=torch.empty(Q, dtype=torch.float64, device="cuda"),
+               per_walk=torch.empty((Q, walks), dtype=torch.float64, device="cuda"),
+               flag=torch.zeros((Q, walks), dtype=torch.uint8, device="cuda"))
+    if want_lines:
+        out["line_m"] = torch.empty((Q, walks, max_len), dtype=torch.int32, device="cuda")
+    dbg = _DebugOut(out["per_walk"].data_ptr(), out["flag"].data_ptr(),
+                    out["line_m"].data_ptr() if want_lines else None)
+    pc = problem._c()
+    _check(load_library().wob_solve_debug(ctypes.byref(pc), _ptr(q), _ptr(qp), Q, walks, max_len,
+                                          seed, _ptr(out["est"]), _ptr(out["var"]),
+                                          ctypes.byref(dbg), _stream(stream)))
+    return out
+
+
+def solve_counted(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
+                  query_prim=None, stream=None):
+    """wob_solve_counted: (est, var, stats dict)."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    qp = None if query_prim is None else _dev(query_prim, torch.int32)
+    Q = q.shape[0]
+    est = torch.empty(Q, dtype=torch.float64, device="cuda")
+    var = torch.empty(Q, dtype=torch.float64, device="cuda")
+    st = _Stats()
+    pc = problem._c()
+    _check(load_library().wob_solve_counted(ctypes.byref(pc), _ptr(q), _ptr(qp), Q, walks,
+                                            max_len, seed, _ptr(est), _ptr(var),
+                                            ctypes.byref(st), _stream(stream)))
+    return est, var, dict(lines=st.lines, node_visits=st.node_visits, tri_tests=st.tri_tests,
+                          hits=st.hits, flagged=st.flagged)
+
+
+def solve_host(problem: Problem, queries: np.ndarray, walks: int, max_len: int, seed: int = 0,
+               query_prim: np.ndarray | None = None, stream=None):
+    """wob_solve_host: host numpy in, host numpy (est, var) out."""
+    q = np.ascontiguousarray(queries, np.float32).reshape(-1, 3)
+    qp = None if query_prim is None else np.ascontiguousarray(query_prim, np.int32)
+    Q = q.shape[0]
+    est = np.empty(Q, np.float64)
+    var = np.empty(Q, np.float64)
+    pc = problem._c()
+    _check(load_library().wob_solve_host(
+        ctypes.byref(pc), q.ctypes.data_as(ctypes.c_void_p),
+        None if qp is None else qp.ctypes.data_as(ctypes.c_void_p), Q, walks, max_len, seed,
+        est.ctypes.data_as(ctypes.c_void_p), var.ctypes.data_as(ctypes.c_void_p),
+        _stream(stream)))
+    return est, var
+
+
+def trace_lines(bvh: BVH, origins, dirs, exclude=None, keys=None, seed: int = 0,
+                problem: int = 0, tau: float = 0.0, stream=None) -> dict:
+    """wob_trace_lines on explicit lines; returns CUDA tensors."""
+    import torch
+    o = _dev(origins, torch.float64).reshape(-1, 3)
+    d = _dev(dirs, torch.float64).reshape(-1, 3)
+    n = o.shape[0]
+    ex = None if exclude is None else _dev(exclude, torch.int32)
+    if keys is None:
+        keys = np.stack([np.arange(n), np.zeros(n), np.zeros(n)], 1)
+    k = _dev(np.asarray(keys, np.int64).astype(np.uint32).view(np.int32), torch.int32).reshape(-1, 3)
+    dev = dict(device="cuda")
+    out = dict(m=torch.empty(n, dtype=torch.int32, **dev), sum_s=torch.empty(n, dtype=torch.int32, **dev),
+               prim=torch.empty(n, dtype=torch.int32, **dev), s=torch.empty(n, dtype=torch.int32, **dev),
+               t=torch.empty(n, dtype=torch.float64, **dev), y=torch.empty((n, 3), dtype=torch.float64, **dev),
+               flag=torch.empty(n, dtype=torch.uint8, **dev))
+    _check(load_library().wob_trace_lines(
+        bvh.handle, _ptr(o), _ptr(d), _ptr(ex), _ptr(k), n, seed, problem, tau, _ptr(out["m"]),
+        _ptr(out["sum_s"]), _ptr(out["prim"]), _ptr(out["s"]), _ptr(out["t"]), _ptr(out["y"]),
+        _ptr(out["flag"]), _stream(stream)))
+    return out
+
+
+def line_axes(seed: int, problem: int, qws, stream=None):
+    """wob_line_axes: (n,3) float64 CUDA tensor."""
+    import torch
+    k = _dev(np.asarray(qws, np.int64).astype(np.uint32).view(np.int32), torch.int32).reshape(-1, 3)
+    d = torch.empty((k.shape[0], 3), dtype=torch.float64, device="cuda")
+    _check(load_library().wob_line_axes(seed, problem, _ptr(k), k.shape[0], _ptr(d),
+                                        _stream(stream)))
+    return d
+
+
+def philox4x32_10(ctr, key, stream=None):
+    """wob_philox4x32_10 on (n,4) counters and (n,2) keys (uint32 values)."""
+    import torch
+    c = _dev(np.asarray(ctr, np.uint64).astype(np.uint32).view(np.int32), torch.int32).reshape(-1, 4)
+    kk = np.broadcast_to(np.asarray(key, np.uint64), (c.shape[0], 2))
+    k = _dev(np.ascontiguousarray(kk).astype(np.uint32).view(np.int32), torch.int32).reshape(-1, 2)
+    out = torch.empty_like(c)
+    _check(load_library().wob_philox4x32_10(_ptr(c), _ptr(k), c.shape[0], _ptr(out),
+                                            _stream(stream)))
+    return out

@@ -1,0 +1,500 @@
+// api.cu -- the extern "C" entry points declared in include/wob.h:
+// argument validation, handle management, scratch allocation and launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "wob_host.h"
+
+namespace wob {
+
+namespace {
+thread_local std::string g_error;
+}
+
+void set_error(const char* fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+}
+
+void clear_error() { g_error.clear(); }
+
+int grid_for(const void* kernel, int threads, size_t smem, int64_t work_items)
+{
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t full = (int64_t)sms * per_sm;
+    int64_t need = (work_items + threads - 1) / threads;
+    if (need < 1) need = 1;
+    return (int)(need < full ? need : full);
+}
+
+namespace {
+
+int check_problem(const wob_problem* prob)
+{
+    if (!prob || !prob->bvh) {
+        set_error("problem or problem->bvh is NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->kind < WOB_DIRICHLET_DL || prob->kind > WOB_ROBIN_SL) {
+        set_error("unknown kind %d", prob->kind);
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->side != 1 && prob->side != -1) {
+        set_error("side must be +1 (interior) or -1 (exterior), got %d", prob->side);
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->data_mode < WOB_DATA_VERTEX_P1 || prob->data_mode > WOB_DATA_POINT) {
+        set_error("unknown data mode %d", prob->data_mode);
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->data_mode == WOB_DATA_VERTEX_P1 && !prob->vertex_data) {
+        set_error("vertex_data is NULL in WOB_DATA_VERTEX_P1 mode");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(prob->alpha) || !(prob->tau >= 0.0f)) {
+        set_error("alpha must be finite and tau >= 0");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return WOB_OK;
+}
+
+int check_sizes(int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len)
+{
+    if (Q < 0 || Q > (int64_t)UINT32_MAX) {
+        set_error("Q = %lld outside [0, 2^32)", (long long)Q);
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (walks < 1 || walk_begin < 0 || walk_begin + walks > (int64_t)UINT32_MAX + 1) {
+        set_error("walk range [%lld, %lld) invalid", (long long)walk_begin,
+                  (long long)(walk_begin + walks));
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (max_len < 1 || max_len > kMaxLen) {
+        set_error("max_len = %d outside [1, %d]", max_len, kMaxLen);
+        return WOB_ERR_INVALID_ARG;
+    }
+    return WOB_OK;
+}
+
+void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
+                 const int32_t* query_prim, int64_t Q, int64_t walk_begin, int32_t walks,
+                 int32_t max_len, uint64_t seed)
+{
+    memset(&p, 0, sizeof(p));
+    const BvhDev& b = prob->bvh->d;
+    const MeshDev& m = *b.mesh;
+    p.nodes = b.nodes;
+    p.tv = b.tv;
+    p.inv_order = b.inv_order;
+    p.root = b.root;
+    p.iter_limit = (int)(4 * b.n_nodes_alloc + 64);
+    p.verts = m.verts;
+    p.tris = m.tris;
+    p.tri_n = m.tri_n;
+    p.cdf = m.cdf;
+    p.T = m.T;
+    p.area = m.area;
+    p.L = m.L;
+    p.kind = prob->kind;
+    p.phi = prob->side;
+    p.alpha = prob->alpha;
+    p.data.mode = prob->data_mode;
+    p.data.vdata = prob->vertex_data;
+    p.data.tris = m.tris;
+    for (int i = 0; i < 10; ++i) p.data.poly[i] = prob->poly[i];
+    for (int i = 0; i < 3; ++i) p.data.x0[i] = prob->x0[i];
+    p.data.scale = prob->scale;
+    p.key0 = (uint32_t)seed ^ prob->problem;
+    p.key1 = (uint32_t)(seed >> 32);
+    p.queries = queries;
+    p.query_prim = query_prim;
+    p.Q = Q;
+    p.N = walks;
+    p.M = max_len;
+    p.walk_begin = walk_begin;
+    p.q_base = 0;
+    const float tau = prob->tau > 0.0f ? prob->tau : kDefaultTau;
+    p.tauL = (float)(tau * m.L);
+    p.edge_thr_L = (float)(tau * m.L * m.max_edge);
+    p.graze = kGraze;
+}
+
+// Run the walks of one problem into per_walk (device, Q x walks).
+int run_walks(WalkParams& p, const wob_debug_out* dbg, bool counted, cudaStream_t s,
+              int* err_dev)
+{
+    p.error_word = err_dev;
+    if (dbg) {
+        p.walk_flag = dbg->walk_flag;
+        p.line_m = dbg->line_m;
+    }
+    if (p.kind == WOB_DIRICHLET_DL) return launch_dl_walks(p, counted, dbg != nullptr, s);
+    return launch_sl_walks(p, dbg != nullptr, s);
+}
+
+struct Scratch {
+    double* per_walk = nullptr;
+    int* err = nullptr;
+    unsigned long long* counters = nullptr;
+    cudaStream_t s = nullptr;
+    ~Scratch()
+    {
+        if (per_walk) cudaFreeAsync(per_walk, s);
+        if (err) cudaFreeAsync(err, s);
+        if (counters) cudaFreeAsync(counters, s);
+    }
+};
+
+int solve_common(const wob_problem* prob, const float* queries, const int32_t* query_prim,
+                 int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len, uint64_t seed,
+                 double* est, double* var, double* sum, double* sumsq,
+                 const wob_debug_out* dbg, wob_stats* stats, cudaStream_t s)
+{
+    WOB_TRY(check_problem(prob));
+    WOB_TRY(check_sizes(Q, walk_begin, walks, max_len));
+    if (Q == 0) return WOB_OK;
+    if (!queries) {
+        set_error("queries is NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->kind == WOB_DIRICHLET_DL && query_prim) {
+        set_error("query_prim must be NULL for WOB_DIRICHLET_DL (the solution on the "
+                  "boundary is the Dirichlet data)");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    WalkParams p;
+    fill_params(p, prob, queries, query_prim, Q, walk_begin, walks, max_len, seed);
+    Scratch sc;
+    sc.s = s;
+    double* per_walk = dbg && dbg->per_walk ? dbg->per_walk : nullptr;
+    if (!per_walk) {
+        WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.per_walk, Q * walks * sizeof(double), s));
+        per_walk = sc.per_walk;
+    }
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(int), s));
+    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(int), s));
+    if (stats) {
+        WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.counters, 5 * sizeof(unsigned long long), s));
+        WOB_CUDA_TRY(cudaMemsetAsync(sc.counters, 0, 5 * sizeof(unsigned long long), s));
+        p.counters = sc.counters;
+    }
+    p.per_walk = per_walk;
+    WOB_TRY(run_walks(p, dbg, stats != nullptr, s, sc.err));
+    if (est) WOB_TRY(launch_reduce(per_walk, Q, walks, est, var, s));
+    if (sum) WOB_TRY(launch_reduce_accum(per_walk, Q, walks, sum, sumsq, s));
+    if (stats) {
+        unsigned long long h[5];
+        int herr = 0;
+        WOB_CUDA_TRY(cudaMemcpyAsync(h, sc.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        WOB_CUDA_TRY(cudaMemcpyAsync(&herr, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        WOB_CUDA_TRY(cudaStreamSynchronize(s));
+        stats->lines = (int64_t)h[0];
+        stats->node_visits = (int64_t)h[1];
+        stats->tri_tests = (int64_t)h[2];
+        stats->hits = (int64_t)h[3];
+        stats->flagged = (int64_t)h[4];
+        if (herr) {
+            set_error("traversal check failed (%s)", herr & 2 ? "iteration bound" : "stack overflow");
+            return WOB_ERR_DEVICE_CHECK;
+        }
+    }
+    return WOB_OK;
+}
+
+}  // namespace
+}  // namespace wob
+
+using namespace wob;
+
+extern "C" {
+
+int wob_version(void) { return 100; }
+
+const char* wob_last_error(void) { return wob::g_error.c_str(); }
+
+int wob_build_mesh(const float* verts, int64_t V, const int32_t* tris, int64_t T,
+                   int on_device, void* stream, wob_mesh* out)
+{
+    clear_error();
+    if (!verts || !tris || !out || V < 3 || T < 1 || T > kMaxTriangles ||
+        V > (int64_t)INT32_MAX) {
+        set_error("wob_build_mesh: invalid arguments (V=%lld, T=%lld)", (long long)V,
+                  (long long)T);
+        return WOB_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    wob_mesh m = new (std::nothrow) wob_mesh_s();
+    if (!m) {
+        set_error("host allocation failed");
+        return WOB_ERR_OOM;
+    }
+    const int rc = build_mesh_impl(verts, V, tris, T, on_device != 0, (cudaStream_t)stream, m->d);
+    if (rc != WOB_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        free_mesh(m->d);
+        delete m;
+        return rc;
+    }
+    *out = m;
+    return WOB_OK;
+}
+
+int wob_mesh_get_info(wob_mesh m, wob_mesh_info* out)
+{
+    clear_error();
+    if (!m || !out) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    out->V = m->d.V;
+    out->T = m->d.T;
+    for (int c = 0; c < 3; ++c) {
+        out->bbox_lo[c] = m->d.lo[c];
+        out->bbox_hi[c] = m->d.hi[c];
+    }
+    out->L = m->d.L;
+    out->area = m->d.area;
+    out->volume = m->d.volume;
+    out->max_edge = m->d.max_edge;
+    return WOB_OK;
+}
+
+void wob_destroy_mesh(wob_mesh m)
+{
+    if (!m) return;
+    free_mesh(m->d);
+    delete m;
+}
+
+int wob_build_bvh(wob_mesh m, const wob_bvh_params* p, void* stream, wob_bvh* out)
+{
+    clear_error();
+    if (!m || !out) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    int leaf = p && p->leaf_size ? p->leaf_size : 4;
+    if (leaf < 1 || leaf > 8) {
+        set_error("leaf_size %d outside [1, 8]", leaf);
+        return WOB_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    wob_bvh b = new (std::nothrow) wob_bvh_s();
+    if (!b) {
+        set_error("host allocation failed");
+        return WOB_ERR_OOM;
+    }
+    const int rc = build_bvh_impl(m->d, leaf, (cudaStream_t)stream, b->d);
+    if (rc != WOB_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        free_bvh(b->d);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return WOB_OK;
+}
+
+int wob_bvh_get_info(wob_bvh b, wob_bvh_info* out)
+{
+    clear_error();
+    if (!b || !out) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    out->nodes = b->d.nodes_reachable;
+    out->leaves = b->d.leaves;
+    out->depth = b->d.depth;
+    out->leaf_size = b->d.leaf_size;
+    out->bytes = b->d.n_nodes_alloc * 64 + b->d.mesh->T * 48;
+    return WOB_OK;
+}
+
+void wob_destroy_bvh(wob_bvh b)
+{
+    if (!b) return;
+    free_bvh(b->d);
+    delete b;
+}
+
+int wob_solve(const wob_problem* prob, const float* queries, const int32_t* query_prim,
+              int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double* est,
+              double* var, void* stream)
+{
+    clear_error();
+    if (walks < 2) {
+        set_error("walks must be >= 2 for a sample variance");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (Q > 0 && (!est || !var)) {
+        set_error("est/var is NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return solve_common(prob, queries, query_prim, Q, 0, walks, max_len, seed, est, var,
+                        nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int wob_solve_range(const wob_problem* prob, const float* queries, const int32_t* query_prim,
+                    int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len,
+                    uint64_t seed, double* sum, double* sumsq, void* stream)
+{
+    clear_error();
+    if (Q > 0 && (!sum || !sumsq)) {
+        set_error("sum/sumsq is NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return solve_common(prob, queries, query_prim, Q, walk_begin, walks, max_len, seed,
+                        nullptr, nullptr, sum, sumsq, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int wob_solve_debug(const wob_problem* prob, const float* queries, const int32_t* query_prim,
+                    int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double* est,
+                    double* var, const wob_debug_out* dbg, void* stream)
+{
+    clear_error();
+    if (!dbg) {
+        set_error("dbg is NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (walks < 2 || (Q > 0 && (!est || !var))) {
+        set_error("walks < 2 or est/var NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return solve_common(prob, queries, query_prim, Q, 0, walks, max_len, seed, est, var,
+                        nullptr, nullptr, dbg, nullptr, (cudaStream_t)stream);
+}
+
+int wob_solve_counted(const wob_problem* prob, const float* queries, const int32_t* query_prim,
+                      int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double* est,
+                      double* var, wob_stats* stats, void* stream)
+{
+    clear_error();
+    if (!stats || walks < 2 || (Q > 0 && (!est || !var))) {
+        set_error("stats NULL, walks < 2 or est/var NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    memset(stats, 0, sizeof(*stats));
+    return solve_common(prob, queries, query_prim, Q, 0, walks, max_len, seed, est, var,
+                        nullptr, nullptr, nullptr, stats, (cudaStream_t)stream);
+}
+
+int wob_solve_host(const wob_problem* prob, const float* queries_host,
+                   const int32_t* query_prim_host, int64_t Q, int32_t walks, int32_t max_len,
+                   uint64_t seed, double* est_host, double* var_host, void* stream)
+{
+    clear_error();
+    if (walks < 2 || Q < 0 || (Q > 0 && (!queries_host || !est_host || !var_host))) {
+        set_error("wob_solve_host: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (Q == 0) return WOB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // one device block: queries | query_prim | est | var
+    const size_t qb = (size_t)Q * 3 * sizeof(float);
+    const size_t pb = query_prim_host ? (size_t)Q * sizeof(int32_t) : 0;
+    const size_t ob = (size_t)Q * sizeof(double);
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t total = align(qb) + align(pb) + 2 * align(ob);
+    char* buf = nullptr;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, total, s));
+    float* dq = (float*)buf;
+    int32_t* dp = query_prim_host ? (int32_t*)(buf + align(qb)) : nullptr;
+    double* de = (double*)(buf + align(qb) + align(pb));
+    double* dv = (double*)(buf + align(qb) + align(pb) + align(ob));
+    int rc = WOB_OK;
+    if (cudaMemcpyAsync(dq, queries_host, qb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (dp && cudaMemcpyAsync(dp, query_prim_host, pb, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+        set_error("host-to-device copy failed");
+        rc = WOB_ERR_CUDA;
+    }
+    if (rc == WOB_OK)
+        rc = solve_common(prob, dq, dp, Q, 0, walks, max_len, seed, de, dv, nullptr, nullptr,
+                          nullptr, nullptr, s);
+    if (rc == WOB_OK &&
+        (cudaMemcpyAsync(est_host, de, ob, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(var_host, dv, ob, cudaMemcpyDeviceToHost, s) != cudaSuccess)) {
+        set_error("device-to-host copy failed");
+        rc = WOB_ERR_CUDA;
+    }
+    cudaFreeAsync(buf, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (rc == WOB_OK && e != cudaSuccess) {
+        set_error("wob_solve_host: %s", cudaGetErrorString(e));
+        rc = WOB_ERR_CUDA;
+    }
+    return rc;
+}
+
+int wob_trace_lines(wob_bvh b, const double* origins, const double* dirs,
+                    const int32_t* exclude, const uint32_t* keys, int64_t n, uint64_t seed,
+                    uint32_t problem, float tau, int32_t* m, int32_t* sum_s, int32_t* prim,
+                    int32_t* s, double* t, double* y, uint8_t* flag, void* stream)
+{
+    clear_error();
+    if (!b || n < 0 || (n > 0 && (!origins || !dirs || !keys || !m))) {
+        set_error("wob_trace_lines: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (n == 0) return WOB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const MeshDev& md = *b->d.mesh;
+    const float tu = tau > 0.0f ? tau : kDefaultTau;
+    int* err = nullptr;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&err, sizeof(int), st));
+    WOB_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    int rc = launch_trace_lines(b->d, origins, dirs, exclude, keys, n, (uint32_t)seed ^ problem,
+                                (uint32_t)(seed >> 32), (float)(tu * md.L),
+                                (float)(tu * md.L * md.max_edge), m, sum_s, prim, s, t, y, flag,
+                                err, st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(err, st);
+    WOB_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rc == WOB_OK && herr) {
+        set_error("traversal stack overflow");
+        rc = WOB_ERR_DEVICE_CHECK;
+    }
+    return rc;
+}
+
+int wob_line_axes(uint64_t seed, uint32_t problem, const uint32_t* qws, int64_t n, double* d,
+                  void* stream)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!qws || !d))) {
+        set_error("wob_line_axes: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (n == 0) return WOB_OK;
+    return launch_line_axes((uint32_t)seed ^ problem, (uint32_t)(seed >> 32), qws, n, d,
+                            (cudaStream_t)stream);
+}
+
+int wob_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                      void* stream)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) {
+        set_error("wob_philox4x32_10: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (n == 0) return WOB_OK;
+    return launch_philox(ctr, key, n, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,425 @@
+// walk.cu -- the walk-on-boundary kernels:
+//   k_dl_walks   Dirichlet problems, double-layer formulation, ray (line)
+//                sampling with all-hits queries (Sec. 4.1, 4.4.1)
+//   k_sl_walks   Neumann / Robin problems, single-layer formulation, area
+//                sampling (Sec. 4.3)
+//   k_reduce*    per-query FP64 mean and variance (Sec. 4.1.1)
+// plus the debug kernels behind wob_trace_lines / wob_line_axes /
+// wob_philox4x32_10.
+//
+// One thread owns one walk from start to end; a walk's value is written to
+// per_walk[q * N + w] and reduced per query in a fixed order, so results do
+// not depend on scheduling.
+#include <cmath>
+
+#include "wob_device.cuh"
+#include "wob_host.h"
+
+namespace wob {
+
+namespace {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+// Dirichlet data g at a boundary point y of the triangle in leaf order `pos`.
+__device__ __forceinline__ float dl_data(const DataDev& D, const float4* __restrict__ tv, int pos,
+                                         double3 yd)
+{
+    const float3 y = make_float3((float)yd.x, (float)yd.y, (float)yd.z);
+    if (D.mode == WOB_DATA_POLY) {
+        const float* c = D.poly;
+        return c[0] + c[1] * y.x + c[2] * y.y + c[3] * y.z + c[4] * y.x * y.x +
+               c[5] * y.y * y.y + c[6] * y.z * y.z + c[7] * y.x * y.y + c[8] * y.y * y.z +
+               c[9] * y.z * y.x;
+    }
+    if (D.mode == WOB_DATA_POINT) {
+        const float dx = y.x - D.x0[0], dy = y.y - D.x0[1], dz = y.z - D.x0[2];
+        return D.scale / sqrtf(dx * dx + dy * dy + dz * dz);
+    }
+    // linear interpolation of vertex values over the triangle
+    const float4 a = __ldg(tv + 3 * pos), b = __ldg(tv + 3 * pos + 1), c = __ldg(tv + 3 * pos + 2);
+    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    const float px = y.x - a.x, py = y.y - a.y, pz = y.z - a.z;
+    const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float nn = nx * nx + ny * ny + nz * nz;
+    const float b1 = ((py * e2z - pz * e2y) * nx + (pz * e2x - px * e2z) * ny +
+                      (px * e2y - py * e2x) * nz) / nn;
+    const float b2 = ((e1y * pz - e1z * py) * nx + (e1z * px - e1x * pz) * ny +
+                      (e1x * py - e1y * px) * nz) / nn;
+    const int prim = __float_as_int(a.w);
+    const int32_t* t = D.tris + 3 * (int64_t)prim;
+    return (1.f - b1 - b2) * __ldg(D.vdata + t[0]) + b1 * __ldg(D.vdata + t[1]) +
+           b2 * __ldg(D.vdata + t[2]);
+}
+
+template <bool COUNT, bool DEBUG>
+__global__ void __launch_bounds__(128) k_dl_walks(WalkParams p)
+{
+    const StreamKey key{p.key0, p.key1};
+    const int64_t total = p.Q * (int64_t)p.N;
+    const double phi = (double)p.phi;
+    unsigned long long c_lines = 0, c_nodes = 0, c_tris = 0, c_hits = 0, c_flag = 0;
+    int overflow = 0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = idx / p.N;
+        const int64_t wi = idx - qi * p.N;
+        const uint32_t q = p.q_base + (uint32_t)qi;
+        const uint32_t w = (uint32_t)(p.walk_begin + wi);
+        double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+        int self = -1;
+        double S = 0.0, P = 1.0, W0 = 0.0;
+        int wflag = 0;
+        int traced = 0;
+        for (int k = 0; k < p.M; ++k) {
+            const double3 d = line_axis(key, q, w, (uint32_t)k);
+            TraverseCounters cnt{0u, 0u};
+            const LineHits h = trace_line<COUNT>(
+                p.nodes, p.tv, p.root, make_float3((float)x.x, (float)x.y, (float)x.z),
+                make_float3((float)d.x, (float)d.y, (float)d.z), self, key, q, w, (uint32_t)k,
+                p.edge_thr_L, p.tauL, p.graze, false, cnt, overflow, p.iter_limit);
+            if (COUNT) {
+                c_lines++;
+                c_nodes += cnt.nodes;
+                c_tris += cnt.tris;
+                c_hits += h.m;
+                c_flag += h.flag;
+            }
+            if (DEBUG) {
+                wflag |= h.flag;
+                if (p.line_m) p.line_m[idx * p.M + k] = h.m;
+                traced = k + 1;
+            }
+            if (h.m == 0) break;
+            const Refined r = refine_hit(p.tv, h.pos, x, d);
+            const double ms = (double)h.m * (double)r.s;
+            if (k == 0)
+                W0 = 0.5 * ms;  // -dG/dn_y / p
+            else
+                P *= -phi * ms;  // 2 phi dG/dn_y / p
+            const double g = (double)dl_data(p.data, p.tv, h.pos, r.y);
+            const double c = (k == p.M - 1) ? phi : 2.0 * phi;  // half the last source term
+            S = fma(P * c, g, S);
+            x = r.y;
+            self = h.pos;
+        }
+        p.per_walk[idx] = W0 * S;
+        if (DEBUG) {
+            if (p.line_m)
+                for (int k = traced; k < p.M; ++k) p.line_m[idx * p.M + k] = -1;
+            if (p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
+        }
+    }
+    if (overflow) atomicOr(p.error_word, overflow);
+    if (COUNT) {
+        atomicAdd(p.counters + 0, c_lines);
+        atomicAdd(p.counters + 1, c_nodes);
+        atomicAdd(p.counters + 2, c_tris);
+        atomicAdd(p.counters + 3, c_hits);
+        atomicAdd(p.counters + 4, c_flag);
+    }
+}
+
+// Data of the single-layer problems at y on triangle j (original order):
+// Neumann flux dh/dn or Robin data dh/dn + alpha h (P1: the vertex values).
+__device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double3 y, double b0,
+                                          double b1, double b2, double3 n)
+{
+    const DataDev& D = p.data;
+    if (D.mode == WOB_DATA_VERTEX_P1) {
+        const int32_t* t = D.tris + 3 * j;
+        return b0 * __ldg(D.vdata + t[0]) + b1 * __ldg(D.vdata + t[1]) + b2 * __ldg(D.vdata + t[2]);
+    }
+    double h, gx, gy, gz;
+    if (D.mode == WOB_DATA_POLY) {
+        const float* c = D.poly;
+        h = c[0] + c[1] * y.x + c[2] * y.y + c[3] * y.z + c[4] * y.x * y.x + c[5] * y.y * y.y +
+            c[6] * y.z * y.z + c[7] * y.x * y.y + c[8] * y.y * y.z + c[9] * y.z * y.x;
+        gx = c[1] + 2.0 * c[4] * y.x + c[7] * y.y + c[9] * y.z;
+        gy = c[2] + 2.0 * c[5] * y.y + c[7] * y.x + c[8] * y.z;
+        gz = c[3] + 2.0 * c[6] * y.z + c[8] * y.y + c[9] * y.x;
+    } else {
+        const double rx = y.x - D.x0[0], ry = y.y - D.x0[1], rz = y.z - D.x0[2];
+        const double rl = sqrt(rx * rx + ry * ry + rz * rz);
+        h = D.scale / rl;
+        const double f = -D.scale / (rl * rl * rl);
+        gx = f * rx;
+        gy = f * ry;
+        gz = f * rz;
+    }
+    const double dhdn = n.x * gx + n.y * gy + n.z * gz;
+    return p.kind == WOB_NEUMANN_SL ? dhdn : dhdn + (double)p.alpha * h;
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
+{
+    const StreamKey key{p.key0, p.key1};
+    const int64_t total = p.Q * (int64_t)p.N;
+    const double phi = (double)p.phi;
+    const double area = p.area;
+    const double rmin = 1e-12 * p.L;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = idx / p.N;
+        const int64_t wi = idx - qi * p.N;
+        const uint32_t q = p.q_base + (uint32_t)qi;
+        const uint32_t w = (uint32_t)(p.walk_begin + wi);
+        double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+        double3 nx = make_double3(0.0, 0.0, 0.0);
+        double S = 0.0, P = 1.0, W0 = 0.0;
+        for (int k = 0; k < p.M; ++k) {
+            // area-uniform point: triangle by inverse CDF of the areas, then
+            // a uniform point on it (square-root warp)
+            const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeArea, 0u, 0u);
+            const double target = u53(u.x, u.y) * area;
+            int64_t lo = 0, hi = p.T - 1;
+            while (lo < hi) {
+                const int64_t mid = lo + ((hi - lo) >> 1);
+                if (__ldg(p.cdf + mid) > target) hi = mid; else lo = mid + 1;
+            }
+            const double su = sqrt(u24(u.z)), u2 = u24(u.w);
+            const double b0 = 1.0 - su, b1 = su * (1.0 - u2), b2 = su * u2;
+            const int32_t* t = p.tris + 3 * lo;
+            const float* v0 = p.verts + 3 * (int64_t)__ldg(t);
+            const float* v1 = p.verts + 3 * (int64_t)__ldg(t + 1);
+            const float* v2 = p.verts + 3 * (int64_t)__ldg(t + 2);
+            const double3 y = make_double3(
+                b0 * __ldg(v0) + b1 * __ldg(v1) + b2 * __ldg(v2),
+                b0 * __ldg(v0 + 1) + b1 * __ldg(v1 + 1) + b2 * __ldg(v2 + 1),
+                b0 * __ldg(v0 + 2) + b1 * __ldg(v1 + 2) + b2 * __ldg(v2 + 2));
+            const double rx = y.x - x.x, ry = y.y - x.y, rz = y.z - x.z;
+            const double rl = sqrt(rx * rx + ry * ry + rz * rz);
+            if (rl < rmin) break;
+            if (k == 0) {
+                W0 = area / (kFourPi * rl);  // |Gamma| G
+            } else {
+                double wk = (rx * nx.x + ry * nx.y + rz * nx.z) / (kFourPi * rl * rl * rl);
+                if (p.kind == WOB_ROBIN_SL) wk += (double)p.alpha / (kFourPi * rl);
+                P *= -2.0 * phi * area * wk;
+            }
+            const double2 nxy = __ldg(reinterpret_cast<const double2*>(p.tri_n + lo));
+            const double nz = __ldg(reinterpret_cast<const double*>(p.tri_n + lo) + 2);
+            const double3 n = make_double3(nxy.x, nxy.y, nz);
+            const double f = sl_data(p, lo, y, b0, b1, b2, n);
+            const double c = (k == p.M - 1) ? phi : 2.0 * phi;
+            S = fma(P * c, f, S);
+            x = y;
+            nx = n;
+        }
+        p.per_walk[idx] = W0 * S;
+        if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
+    }
+}
+
+// One warp per query: mean and unbiased variance in a fixed order.
+__global__ void k_reduce(const double* __restrict__ per_walk, int64_t Q, int32_t N,
+                         double* __restrict__ est, double* __restrict__ var)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < Q;
+         q += warps) {
+        const double* v = per_walk + q * N;
+        double s = 0.0;
+        for (int i = lane; i < N; i += 32) s += v[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        const double mean = s / N;
+        double ss = 0.0;
+        for (int i = lane; i < N; i += 32) {
+            const double e = v[i] - mean;
+            ss = fma(e, e, ss);
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+        if (lane == 0) {
+            est[q] = mean;
+            var[q] = N > 1 ? ss / (N - 1) : 0.0;
+        }
+    }
+}
+
+__global__ void k_reduce_accum(const double* __restrict__ per_walk, int64_t Q, int32_t N,
+                               double* __restrict__ sum, double* __restrict__ sumsq)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < Q;
+         q += warps) {
+        const double* v = per_walk + q * N;
+        double s = 0.0, ss = 0.0;
+        for (int i = lane; i < N; i += 32) {
+            s += v[i];
+            ss = fma(v[i], v[i], ss);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+            ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+        }
+        if (lane == 0) {
+            sum[q] += s;
+            sumsq[q] += ss;
+        }
+    }
+}
+
+__global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __restrict__ tv,
+                              const int32_t* __restrict__ inv_order, int root, int64_t n_tris,
+                              int iter_limit,
+                              const double* __restrict__ o, const double* __restrict__ d,
+                              const int32_t* __restrict__ exclude,
+                              const uint32_t* __restrict__ keys, int64_t n, uint32_t key0,
+                              uint32_t key1, float tauL, float edge_thr_L, int32_t* m,
+                              int32_t* sum_s, int32_t* prim, int32_t* s_out, double* t_out,
+                              double* y_out, uint8_t* flag, int* error_word)
+{
+    int overflow = 0;
+    const StreamKey key{key0, key1};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double3 x = make_double3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+        const double3 dd = make_double3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+        const int ex = exclude ? exclude[i] : -1;
+        const int self = (ex >= 0 && ex < n_tris) ? inv_order[ex] : -1;
+        TraverseCounters cnt{0u, 0u};
+        const LineHits h = trace_line<false>(
+            nodes, tv, root, make_float3((float)x.x, (float)x.y, (float)x.z),
+            make_float3((float)dd.x, (float)dd.y, (float)dd.z), self, key, keys[3 * i],
+            keys[3 * i + 1], keys[3 * i + 2], edge_thr_L, tauL, kGraze, true, cnt, overflow,
+            iter_limit);
+        m[i] = h.m;
+        if (sum_s) sum_s[i] = h.sum_s;
+        if (flag) flag[i] = (uint8_t)h.flag;
+        int pr = -1, sg = 0;
+        double tt = 0.0;
+        double3 yy = make_double3(0.0, 0.0, 0.0);
+        if (h.m > 0) {
+            const Refined r = refine_hit(tv, h.pos, x, dd);
+            pr = __float_as_int(__ldg(tv + 3 * h.pos).w);
+            sg = r.s;
+            yy = r.y;
+            tt = (r.y.x - x.x) * dd.x + (r.y.y - x.y) * dd.y + (r.y.z - x.z) * dd.z;
+        }
+        if (prim) prim[i] = pr;
+        if (s_out) s_out[i] = sg;
+        if (t_out) t_out[i] = tt;
+        if (y_out) {
+            y_out[3 * i] = yy.x;
+            y_out[3 * i + 1] = yy.y;
+            y_out[3 * i + 2] = yy.z;
+        }
+    }
+    if (overflow) atomicOr(error_word, overflow);
+}
+
+__global__ void k_line_axes(uint32_t key0, uint32_t key1, const uint32_t* __restrict__ qws,
+                            int64_t n, double* __restrict__ d)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double3 a = line_axis(StreamKey{key0, key1}, qws[3 * i], qws[3 * i + 1], qws[3 * i + 2]);
+        d[3 * i] = a.x;
+        d[3 * i + 1] = a.y;
+        d[3 * i + 2] = a.z;
+    }
+}
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ keyv,
+                         int64_t n, uint32_t* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const u32x4 r = philox4x32_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3],
+                                      keyv[2 * i], keyv[2 * i + 1]);
+        out[4 * i] = r.x;
+        out[4 * i + 1] = r.y;
+        out[4 * i + 2] = r.z;
+        out[4 * i + 3] = r.w;
+    }
+}
+
+}  // namespace
+
+int launch_dl_walks(const WalkParams& p, bool counted, bool debug, cudaStream_t s)
+{
+    const int threads = 128;
+    const int64_t work = p.Q * (int64_t)p.N;
+    if (counted) {
+        k_dl_walks<true, true><<<grid_for((const void*)k_dl_walks<true, true>, threads, 0, work),
+                                 threads, 0, s>>>(p);
+    } else if (debug) {
+        k_dl_walks<false, true><<<grid_for((const void*)k_dl_walks<false, true>, threads, 0, work),
+                                  threads, 0, s>>>(p);
+    } else {
+        k_dl_walks<false, false><<<grid_for((const void*)k_dl_walks<false, false>, threads, 0, work),
+                                   threads, 0, s>>>(p);
+    }
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s)
+{
+    const int threads = 128;
+    const int64_t work = p.Q * (int64_t)p.N;
+    if (debug)
+        k_sl_walks<true><<<grid_for((const void*)k_sl_walks<true>, threads, 0, work), threads, 0, s>>>(p);
+    else
+        k_sl_walks<false><<<grid_for((const void*)k_sl_walks<false>, threads, 0, work), threads, 0, s>>>(p);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
+                  cudaStream_t s)
+{
+    const int threads = 256;
+    k_reduce<<<grid_for((const void*)k_reduce, threads, 0, Q * 32), threads, 0, s>>>(per_walk, Q, N, est, var);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum, double* sumsq,
+                        cudaStream_t s)
+{
+    const int threads = 256;
+    k_reduce_accum<<<grid_for((const void*)k_reduce_accum, threads, 0, Q * 32), threads, 0, s>>>(
+        per_walk, Q, N, sum, sumsq);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_trace_lines(const BvhDev& b, const double* o, const double* d, const int32_t* exclude,
+                       const uint32_t* keys, int64_t n, uint32_t key0, uint32_t key1, float tauL,
+                       float edge_thr_L, int32_t* m, int32_t* sum_s, int32_t* prim,
+                       int32_t* s_out, double* t, double* y, uint8_t* flag, int* error_word,
+                       cudaStream_t s)
+{
+    const int threads = 128;
+    k_trace_lines<<<grid_for((const void*)k_trace_lines, threads, 0, n), threads, 0, s>>>(
+        b.nodes, b.tv, b.inv_order, b.root, b.mesh->T, (int)(4 * b.n_nodes_alloc + 64), o, d,
+        exclude, keys, n, key0, key1, tauL,
+        edge_thr_L, m, sum_s, prim, s_out, t, y, flag, error_word);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_line_axes(uint32_t key0, uint32_t key1, const uint32_t* qws, int64_t n, double* d,
+                     cudaStream_t s)
+{
+    const int threads = 256;
+    k_line_axes<<<grid_for((const void*)k_line_axes, threads, 0, n), threads, 0, s>>>(key0, key1, qws, n, d);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                  cudaStream_t s)
+{
+    const int threads = 256;
+    k_philox<<<grid_for((const void*)k_philox, threads, 0, n), threads, 0, s>>>(ctr, key, n, out);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+}  // namespace wob

@@ -1,0 +1,63 @@
+// wob_host.h -- host-side helpers: error reporting, CUDA checks and the
+// internal entry points implemented by the library's .cu files.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wob_internal.h"
+
+namespace wob {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define WOB_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            ::wob::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e),    \
+                             __FILE__, __LINE__);                                       \
+            return _e == cudaErrorMemoryAllocation ? WOB_ERR_OOM : WOB_ERR_CUDA;        \
+        }                                                                               \
+    } while (0)
+
+#define WOB_TRY(expr)                 \
+    do {                              \
+        int _rc = (expr);             \
+        if (_rc != WOB_OK) return _rc; \
+    } while (0)
+
+// Persistent-grid size: SM count x resident blocks of `kernel` at `threads`.
+int grid_for(const void* kernel, int threads, size_t smem, int64_t work_items);
+
+// mesh.cu
+int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t T,
+                    bool on_device, cudaStream_t s, MeshDev& m);
+void free_mesh(MeshDev& m);
+template <typename T>
+int inclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s);
+
+// bvh.cu
+int build_bvh_impl(MeshDev& m, int leaf_size, cudaStream_t s, BvhDev& b);
+void free_bvh(BvhDev& b);
+
+// walk.cu
+int launch_dl_walks(const WalkParams& p, bool counted, bool debug, cudaStream_t s);
+int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s);
+int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
+                  cudaStream_t s);
+int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum,
+                        double* sumsq, cudaStream_t s);
+int launch_trace_lines(const BvhDev& b, const double* o, const double* d, const int32_t* exclude,
+                       const uint32_t* keys, int64_t n, uint32_t key0, uint32_t key1,
+                       float tauL, float edge_thr_L, int32_t* m, int32_t* sum_s, int32_t* prim,
+                       int32_t* s_out, double* t, double* y, uint8_t* flag, int* error_word,
+                       cudaStream_t s);
+int launch_line_axes(uint32_t key0, uint32_t key1, const uint32_t* qws, int64_t n, double* d,
+                     cudaStream_t s);
+int launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                  cudaStream_t s);
+
+}  // namespace wob

@@ -1,0 +1,104 @@
+// wob_internal.h -- library-internal constants, handle layouts and the
+// launch parameter blocks shared by the host code and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wob.h"
+
+namespace wob {
+
+constexpr uint32_t kPurposeDir = 0;   // line axis draws
+constexpr uint32_t kPurposeHit = 1;   // hit-selection keys
+constexpr uint32_t kPurposeArea = 2;  // area-sampled boundary points
+constexpr int kStackSize = 64;        // traversal stack entries per line
+constexpr int kNoRef = INT32_MIN;     // empty traversal stack marker
+constexpr int64_t kMaxTriangles = (int64_t(1) << 28) - 2;
+constexpr float kDefaultTau = 2e-6f;
+constexpr float kGraze = 1e-4f;
+constexpr int kMaxLen = 4096;
+
+struct MeshDev {
+    float* verts = nullptr;   // V x 3
+    int32_t* tris = nullptr;  // T x 3
+    double4* tri_n = nullptr; // unit normal (FP64), area
+    double* cdf = nullptr;    // inclusive prefix sums of areas
+    int64_t V = 0, T = 0;
+    double lo[3], hi[3];
+    double L = 0, area = 0, volume = 0, max_edge = 0;
+    int device = 0;
+};
+
+struct BvhDev {
+    float4* nodes = nullptr;  // 4 float4 per interior node
+    float4* tv = nullptr;     // 3 float4 per triangle, leaf order
+    int32_t* order = nullptr; // leaf order -> original triangle id
+    int32_t* inv_order = nullptr; // original triangle id -> leaf order
+    int root = kNoRef;
+    int64_t n_nodes_alloc = 0;
+    int64_t nodes_reachable = 0, leaves = 0;
+    int depth = 0;
+    int leaf_size = 4;
+    MeshDev* mesh = nullptr;
+};
+
+// Data term, evaluated at a boundary point.
+struct DataDev {
+    int mode;
+    const float* vdata;
+    const int32_t* tris;  // original triangles (P1 lookup)
+    float poly[10];
+    float x0[3];
+    float scale;
+};
+
+struct WalkParams {
+    // geometry
+    const float4* nodes;
+    const float4* tv;
+    const int32_t* inv_order;
+    int root;
+    int iter_limit;  // traversal loop bound (4 x nodes + 64)
+    const float* verts;
+    const int32_t* tris;
+    const double4* tri_n;
+    const double* cdf;
+    int64_t T;
+    double area;
+    double L;
+    // problem
+    int kind;
+    int phi;
+    float alpha;
+    DataDev data;
+    uint32_t key0, key1;
+    // queries and walks
+    const float* queries;
+    const int32_t* query_prim;
+    int64_t Q;
+    int32_t N;
+    int32_t M;
+    int64_t walk_begin;
+    uint32_t q_base;
+    // near-degenerate thresholds
+    float tauL;
+    float edge_thr_L;  // tau * L * max_edge
+    float graze;
+    // outputs
+    double* per_walk;    // Q x N
+    uint8_t* walk_flag;  // Q x N (optional)
+    int32_t* line_m;     // Q x N x M (optional)
+    unsigned long long* counters;  // [lines, nodes, tris, hits, flagged] (optional)
+    int* error_word;
+};
+
+}  // namespace wob
+
+// Host-side handle types named in the public header.
+struct wob_mesh_s {
+    wob::MeshDev d;
+};
+struct wob_bvh_s {
+    wob::BvhDev d;
+};

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/wob.h (no compute calls: no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2305_04403_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(wob_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    try:
+        return B.build()
+    except RuntimeError as e:  # pragma: no cover - no nvcc
+        pytest.skip(f"cannot build: {e}")
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for must in ("wob_build_mesh", "wob_build_bvh", "wob_solve", "wob_solve_range",
+                 "wob_destroy_mesh", "wob_destroy_bvh", "wob_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_string_without_gpu(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.wob_version.restype = ctypes.c_int
+    assert lib.wob_version() >= 100
+    lib.wob_last_error.restype = ctypes.c_char_p
+    assert lib.wob_last_error() == b""
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.wob_build_mesh.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert lib.wob_build_mesh(None, 3, None, 1, 0, None, ctypes.byref(out)) == -1
+    lib.wob_last_error.restype = ctypes.c_char_p
+    assert b"invalid" in lib.wob_last_error()
+    lib.wob_solve.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_int32,
+                                                      ctypes.c_int32, ctypes.c_uint64] + [ctypes.c_void_p] * 3
+    assert lib.wob_solve(None, None, None, 4, 1, 4, 0, None, None, None) == -1
+
+
+def test_ptxas_reports_no_spills(lib_path):
+    log = open(os.path.join(os.path.dirname(lib_path), "ptxas.log")).read()
+    spills = re.findall(r"(\d+) bytes spill stores", log)
+    assert all(int(s) == 0 for s in spills), "register spills in the kernels"
