@@ -206,6 +206,28 @@ int wob_solve_host(const wob_problem *prob, const float *queries_host,
                    uint64_t seed, double *est_host, double *var_host, void *stream);
 
 /*
+ * wob_solve for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of wob_solve.  wob_solve
+ * allocates one double per walk of scratch on every call; a caller whose
+ * process has handed the GPU's memory to its own allocator, or that cannot
+ * afford an allocation and the synchronisation it may imply on its path,
+ * calls this instead.  The per-walk values live in a fixed array inside the
+ * library (2^20 doubles = 8 MiB, held on every GPU that loads the library's
+ * device code until exit), so:
+ *   - Q * walks must be <= 2^20 (else WOB_ERR_INVALID_ARG, nothing launched);
+ *   - no cudaMalloc, cudaFree or other allocating routine is called;
+ *   - all calls share that array: calls that overlap on the GPU (other
+ *     streams or host threads) race; serialise them;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ * Arguments, outputs and results are those of wob_solve (bit-identical).
+ */
+int wob_solve_noalloc(const wob_problem *prob, const float *queries, const int32_t *query_prim,
+                      int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
+                      double *var, void *stream);
+
+/*
  * All-hits queries of n explicit lines {o + t d, t real} (Sec. 4.4.1), all
  * pointers device.  origins/dirs: n x 3 double (dirs unit length).
  * exclude: n int32 triangle ids skipped (the point's own face), or NULL.

@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
     "WobError", "Mesh", "BVH", "Problem", "build_mesh", "build_bvh", "solve", "solve_range",
-    "solve_debug", "solve_counted", "solve_host", "trace_lines", "line_axes", "philox4x32_10",
+    "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
 
@@ -112,6 +112,8 @@ def load_library() -> ctypes.CDLL:
                                    ctypes.POINTER(_Stats), P], ctypes.c_int),
             "wob_solve_host": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
                                ctypes.c_int),
+            "wob_solve_noalloc": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
+                                  ctypes.c_int),
             "wob_trace_lines": ([P, P, P, P, P, I64, U64, U32, F, P, P, P, P, P, P, P, P],
                                 ctypes.c_int),
             "wob_line_axes": ([U64, U32, P, I64, P, P], ctypes.c_int),
@@ -264,6 +266,24 @@ def solve(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
     pc = problem._c()
     _check(load_library().wob_solve(ctypes.byref(pc), _ptr(q), _ptr(qp), Q, walks, max_len,
                                     seed, _ptr(est), _ptr(var), _stream(stream)))
+    return est, var
+
+
+def solve_noalloc(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
+                  query_prim=None, stream=None):
+    """wob_solve_noalloc: wob_solve without any device allocation by the
+    library (Q * walks <= 2^20; see include/wob.h).  The est / var tensors
+    are allocated here by torch, i.e. by the caller."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    qp = None if query_prim is None else _dev(query_prim, torch.int32)
+    Q = q.shape[0]
+    est = torch.empty(Q, dtype=torch.float64, device="cuda")
+    var = torch.empty(Q, dtype=torch.float64, device="cuda")
+    pc = problem._c()
+    _check(load_library().wob_solve_noalloc(ctypes.byref(pc), _ptr(q), _ptr(qp), Q, walks,
+                                            max_len, seed, _ptr(est), _ptr(var),
+                                            _stream(stream)))
     return est, var
 
 

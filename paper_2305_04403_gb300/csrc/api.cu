@@ -42,8 +42,6 @@ int grid_for(const void* kernel, int threads, size_t smem, int64_t work_items)
     return (int)(need < full ? need : full);
 }
 
-namespace {
-
 int check_problem(const wob_problem* prob)
 {
     if (!prob || !prob->bvh) {
@@ -133,6 +131,8 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     p.edge_thr_L = (float)(tau * m.L * m.max_edge);
     p.graze = kGraze;
 }
+
+namespace {
 
 // Run the walks of one problem into per_walk (device, Q x walks).
 int run_walks(WalkParams& p, const wob_debug_out* dbg, bool counted, cudaStream_t s,

@@ -29,6 +29,13 @@ void clear_error();
         if (_rc != WOB_OK) return _rc; \
     } while (0)
 
+// api.cu: argument checks and the launch parameter block of one solve.
+int check_problem(const wob_problem* prob);
+int check_sizes(int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len);
+void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
+                 const int32_t* query_prim, int64_t Q, int64_t walk_begin, int32_t walks,
+                 int32_t max_len, uint64_t seed);
+
 // Persistent-grid size: SM count x resident blocks of `kernel` at `threads`.
 int grid_for(const void* kernel, int threads, size_t smem, int64_t work_items);
 
