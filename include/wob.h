@@ -75,7 +75,7 @@ typedef struct {
 } wob_mesh_info;
 
 typedef struct {
-    int32_t leaf_size; /* max triangles per leaf, 1..8 (0 = default 4) */
+    int32_t leaf_size; /* max triangles per leaf, 1..8 (0 = default 2) */
     int32_t reserved[7];
 } wob_bvh_params;
 

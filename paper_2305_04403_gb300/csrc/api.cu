@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -288,7 +289,7 @@ int wob_build_bvh(wob_mesh m, const wob_bvh_params* p, void* stream, wob_bvh* ou
         set_error("NULL argument");
         return WOB_ERR_INVALID_ARG;
     }
-    int leaf = p && p->leaf_size ? p->leaf_size : 4;
+    int leaf = p && p->leaf_size ? p->leaf_size : 2;
     if (leaf < 1 || leaf > 8) {
         set_error("leaf_size %d outside [1, 8]", leaf);
         return WOB_ERR_INVALID_ARG;

@@ -11,6 +11,7 @@
 // per_walk[q * N + w] and reduced per query in a fixed order, so results do
 // not depend on scheduling.
 #include <cmath>
+#include <cstdlib>
 
 #include "wob_device.cuh"
 #include "wob_host.h"
@@ -21,97 +22,76 @@ namespace {
 
 constexpr double kFourPi = 12.566370614359172953850573533118;
 
-// Dirichlet data g at a boundary point y of the triangle in leaf order `pos`.
-__device__ __forceinline__ float dl_data(const DataDev& D, const float4* __restrict__ tv, int pos,
-                                         double3 yd)
-{
-    const float3 y = make_float3((float)yd.x, (float)yd.y, (float)yd.z);
-    if (D.mode == WOB_DATA_POLY) {
-        const float* c = D.poly;
-        return c[0] + c[1] * y.x + c[2] * y.y + c[3] * y.z + c[4] * y.x * y.x +
-               c[5] * y.y * y.y + c[6] * y.z * y.z + c[7] * y.x * y.y + c[8] * y.y * y.z +
-               c[9] * y.z * y.x;
-    }
-    if (D.mode == WOB_DATA_POINT) {
-        const float dx = y.x - D.x0[0], dy = y.y - D.x0[1], dz = y.z - D.x0[2];
-        return D.scale / sqrtf(dx * dx + dy * dy + dz * dz);
-    }
-    // linear interpolation of vertex values over the triangle
-    const float4 a = __ldg(tv + 3 * pos), b = __ldg(tv + 3 * pos + 1), c = __ldg(tv + 3 * pos + 2);
-    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
-    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
-    const float px = y.x - a.x, py = y.y - a.y, pz = y.z - a.z;
-    const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-    const float nn = nx * nx + ny * ny + nz * nz;
-    const float b1 = ((py * e2z - pz * e2y) * nx + (pz * e2x - px * e2z) * ny +
-                      (px * e2y - py * e2x) * nz) / nn;
-    const float b2 = ((e1y * pz - e1z * py) * nx + (e1z * px - e1x * pz) * ny +
-                      (e1x * py - e1y * px) * nz) / nn;
-    const int prim = __float_as_int(a.w);
-    const int32_t* t = D.tris + 3 * (int64_t)prim;
-    return (1.f - b1 - b2) * __ldg(D.vdata + t[0]) + b1 * __ldg(D.vdata + t[1]) +
-           b2 * __ldg(D.vdata + t[2]);
-}
+#ifndef WOB_DL_MIN_BLOCKS
+#define WOB_DL_MIN_BLOCKS 8
+#endif
 
+// One thread owns one walk (grid-stride over the Q x N walks).  Per line:
+// draw the axis, traverse (descend to a leaf, test it, repeat), then pick
+// the hit (keys only when m > 1), refine it in FP64 and accumulate.  The
+// kernel is limited to 64 registers (8 blocks of 128 threads per SM): the
+// traversal is latency-bound and occupancy pays more than the few values
+// the compiler keeps in local memory.  Lanes that start their lines
+// together share the fetches of the upper tree levels; variants that broke
+// this (persistent lanes refilled from a global counter, or a wavefront of
+// separate traversal and FP64-update kernels) measured 8-18% slower.
 template <bool COUNT, bool DEBUG>
-__global__ void __launch_bounds__(128) k_dl_walks(WalkParams p)
+__global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams p)
 {
     const StreamKey key{p.key0, p.key1};
     const int64_t total = p.Q * (int64_t)p.N;
     const double phi = (double)p.phi;
+    int err = 0;
+    int stack[kStackSize];
+    int hits[kMaxHits];
     unsigned long long c_lines = 0, c_nodes = 0, c_tris = 0, c_hits = 0, c_flag = 0;
-    int overflow = 0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t qi = idx / p.N;
-        const int64_t wi = idx - qi * p.N;
         const uint32_t q = p.q_base + (uint32_t)qi;
-        const uint32_t w = (uint32_t)(p.walk_begin + wi);
+        const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
         double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
-        int self = -1;
-        double S = 0.0, P = 1.0, W0 = 0.0;
-        int wflag = 0;
-        int traced = 0;
-        for (int k = 0; k < p.M; ++k) {
+        int self = -1, wflag = 0, k = 0;
+        double S = 0.0, P = 1.0;
+        for (; k < p.M; ++k) {
             const double3 d = line_axis(key, q, w, (uint32_t)k);
-            TraverseCounters cnt{0u, 0u};
-            const LineHits h = trace_line<COUNT>(
-                p.nodes, p.tv, p.root, make_float3((float)x.x, (float)x.y, (float)x.z),
-                make_float3((float)d.x, (float)d.y, (float)d.z), self, key, q, w, (uint32_t)k,
-                p.edge_thr_L, p.tauL, p.graze, false, cnt, overflow, p.iter_limit);
+            const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
+                                       make_float3((float)d.x, (float)d.y, (float)d.z));
+            const float Tthr = p.edge_thr_L * fabsf(L.Sz);
+            Trav t;
+            trav_init(t, p.root);
+            uint32_t nn = 0, nt = 0;
+            while (t.ref != kNoRef) {
+                descend<COUNT>(p.nodes, L, t, stack, nn, err, p.iter_limit);
+                if (t.ref == kNoRef) break;
+                test_leaf<COUNT, false>(p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL, p.graze,
+                                        self, t, hits, stack, key, q, w, (uint32_t)k, nt);
+            }
             if (COUNT) {
                 c_lines++;
-                c_nodes += cnt.nodes;
-                c_tris += cnt.tris;
-                c_hits += h.m;
-                c_flag += h.flag;
+                c_nodes += nn;
+                c_tris += nt;
+                c_hits += t.m;
+                c_flag += t.flag;
             }
-            if (DEBUG) {
-                wflag |= h.flag;
-                if (p.line_m) p.line_m[idx * p.M + k] = h.m;
-                traced = k + 1;
+            wflag |= t.flag;
+            if (DEBUG && p.line_m) p.line_m[idx * p.M + k] = t.m;
+            if (t.m == 0) {
+                ++k;
+                break;
             }
-            if (h.m == 0) break;
-            const Refined r = refine_hit(p.tv, h.pos, x, d);
-            const double ms = (double)h.m * (double)r.s;
-            if (k == 0)
-                W0 = 0.5 * ms;  // -dG/dn_y / p
-            else
-                P *= -phi * ms;  // 2 phi dG/dn_y / p
-            const double g = (double)dl_data(p.data, p.tv, h.pos, r.y);
-            const double c = (k == p.M - 1) ? phi : 2.0 * phi;  // half the last source term
-            S = fma(P * c, g, S);
-            x = r.y;
-            self = h.pos;
+            const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
+            dl_accumulate(p.tv, p.data, pos, t.m, k, p.M, phi, x, d, S, P);
+            self = pos;
         }
-        p.per_walk[idx] = W0 * S;
+        p.per_walk[idx] = S;
         if (DEBUG) {
             if (p.line_m)
-                for (int k = traced; k < p.M; ++k) p.line_m[idx * p.M + k] = -1;
+                for (int k2 = k; k2 < p.M; ++k2) p.line_m[idx * p.M + k2] = -1;
             if (p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
         }
     }
-    if (overflow) atomicOr(p.error_word, overflow);
+    if (err) atomicOr(p.error_word, err);
     if (COUNT) {
         atomicAdd(p.counters + 0, c_lines);
         atomicAdd(p.counters + 1, c_nodes);
@@ -265,15 +245,14 @@ __global__ void k_reduce_accum(const double* __restrict__ per_walk, int64_t Q, i
 
 __global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __restrict__ tv,
                               const int32_t* __restrict__ inv_order, int root, int64_t n_tris,
-                              int iter_limit,
-                              const double* __restrict__ o, const double* __restrict__ d,
-                              const int32_t* __restrict__ exclude,
+                              int iter_limit, const double* __restrict__ o,
+                              const double* __restrict__ d, const int32_t* __restrict__ exclude,
                               const uint32_t* __restrict__ keys, int64_t n, uint32_t key0,
                               uint32_t key1, float tauL, float edge_thr_L, int32_t* m,
                               int32_t* sum_s, int32_t* prim, int32_t* s_out, double* t_out,
                               double* y_out, uint8_t* flag, int* error_word)
 {
-    int overflow = 0;
+    int err = 0;
     const StreamKey key{key0, key1};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -281,21 +260,20 @@ __global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __
         const double3 dd = make_double3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
         const int ex = exclude ? exclude[i] : -1;
         const int self = (ex >= 0 && ex < n_tris) ? inv_order[ex] : -1;
-        TraverseCounters cnt{0u, 0u};
-        const LineHits h = trace_line<false>(
+        Trav t;
+        const int pos = trace_line<true>(
             nodes, tv, root, make_float3((float)x.x, (float)x.y, (float)x.z),
             make_float3((float)dd.x, (float)dd.y, (float)dd.z), self, key, keys[3 * i],
-            keys[3 * i + 1], keys[3 * i + 2], edge_thr_L, tauL, kGraze, true, cnt, overflow,
-            iter_limit);
-        m[i] = h.m;
-        if (sum_s) sum_s[i] = h.sum_s;
-        if (flag) flag[i] = (uint8_t)h.flag;
+            keys[3 * i + 1], keys[3 * i + 2], edge_thr_L, tauL, kGraze, t, err, iter_limit);
+        m[i] = t.m;
+        if (sum_s) sum_s[i] = t.sum_s;
+        if (flag) flag[i] = (uint8_t)t.flag;
         int pr = -1, sg = 0;
         double tt = 0.0;
         double3 yy = make_double3(0.0, 0.0, 0.0);
-        if (h.m > 0) {
-            const Refined r = refine_hit(tv, h.pos, x, dd);
-            pr = __float_as_int(__ldg(tv + 3 * h.pos).w);
+        if (pos >= 0) {
+            const Refined r = refine_hit(tv, pos, x, dd);
+            pr = (int)prim_of(tv, pos);
             sg = r.s;
             yy = r.y;
             tt = (r.y.x - x.x) * dd.x + (r.y.y - x.y) * dd.y + (r.y.z - x.z) * dd.z;
@@ -309,7 +287,7 @@ __global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __
             y_out[3 * i + 2] = yy.z;
         }
     }
-    if (overflow) atomicOr(error_word, overflow);
+    if (err) atomicOr(error_word, err);
 }
 
 __global__ void k_line_axes(uint32_t key0, uint32_t key1, const uint32_t* __restrict__ qws,

@@ -115,8 +115,7 @@ struct LinePre {
     float oix, oiy, oiz;  // o / d
     // Woop-Benthin-Wald watertight shear
     int kx, ky, kz;
-    float Sx, Sy, Sz;
-    float dkz_abs;
+    float Sx, Sy, Sz;  // shear; |Sz| = 1 / |d_kz|
 };
 
 __device__ __forceinline__ float guard_inv(float d)
@@ -143,7 +142,6 @@ __device__ __forceinline__ LinePre line_pre(float3 o, float3 d)
     L.Sx = comp(d, kx) / dkz;
     L.Sy = comp(d, ky) / dkz;
     L.Sz = 1.0f / dkz;
-    L.dkz_abs = fabsf(dkz);
     return L;
 }
 
@@ -159,131 +157,206 @@ __device__ __forceinline__ bool line_box(const LinePre& L, float lox, float hix,
     return tn <= tf;
 }
 
-// Result of one all-hits line query.
-struct LineHits {
-    int m;          // number of hits
-    int pos;        // leaf-order index of the picked triangle (-1: none)
-    int sum_s;      // sum over hits of sign(omega . n) (debug)
-    int flag;       // near-degenerate
-    uint64_t best;  // smallest key
+// ---------------------------------------------------------------------------
+// All-hits traversal of one line, in resumable pieces so that a persistent
+// kernel can interleave lines: descend() walks interior nodes until it holds
+// a leaf (or the line is done), test_leaf() tests that leaf's triangles and
+// pops the next reference.  Hits are recorded by leaf position; the
+// selection keys are computed after the traversal (select_hit), and only when
+// there is more than one hit.
+// ---------------------------------------------------------------------------
+constexpr int kMaxHits = 8;
+
+struct Trav {
+    int ref;        // node (>= 0) or leaf (< 0) to visit next; kNoRef when done
+    int sp;         // stack depth
+    int m;          // hits so far
+    int flag;       // near-degenerate line
+    int sum_s;      // sum of sign(omega . n) over hits (debug only)
+    int iters;      // interior nodes visited (bounded)
+    uint64_t best;  // smallest key among hits, once m > kMaxHits
+    int bpos;       // its leaf position
 };
 
-struct TraverseCounters {
-    uint32_t nodes, tris;
-};
+__device__ __forceinline__ void trav_init(Trav& t, int root)
+{
+    t.ref = root;
+    t.sp = 0;
+    t.m = 0;
+    t.flag = 0;
+    t.sum_s = 0;
+    t.iters = 0;
+    t.best = ~0ull;
+    t.bpos = -1;
+}
 
+__device__ __forceinline__ uint64_t hit_key(StreamKey key, uint32_t q, uint32_t walk,
+                                            uint32_t step, uint32_t prim)
+{
+    const u32x4 k = stream_block(key, q, walk, step, kPurposeHit, 0u, prim);
+    return ((uint64_t)k.x << 32) | (uint64_t)k.y;
+}
+
+__device__ __forceinline__ uint32_t prim_of(const float4* __restrict__ tv, int pos)
+{
+    return __float_as_uint(__ldg(tv + 3 * pos).w);
+}
+
+// Smallest key wins; equal keys: smaller triangle id.
+__device__ __forceinline__ void keep_min(uint64_t k, uint32_t prim, int pos, uint64_t& best,
+                                         uint32_t& best_prim, int& bpos)
+{
+    if (k < best || (k == best && prim < best_prim)) {
+        best = k;
+        best_prim = prim;
+        bpos = pos;
+    }
+}
+
+// Descend interior nodes until t.ref is a leaf or the traversal is finished.
 template <bool COUNT>
-__device__ __forceinline__ LineHits trace_line(const float4* __restrict__ nodes,
-                                               const float4* __restrict__ tv, int root,
-                                               float3 o, float3 d, int exclude_pos,
-                                               StreamKey key, uint32_t q, uint32_t walk,
-                                               uint32_t step, float edge_thr_L, float tauL,
-                                               float graze, bool want_sum_s,
-                                               TraverseCounters& cnt, int& overflow,
-                                               int iter_limit)
+__device__ __forceinline__ void descend(const float4* __restrict__ nodes, const LinePre& L,
+                                        Trav& t, int* stack, uint32_t& n_nodes, int& err,
+                                        int iter_limit)
+{
+    while (t.ref >= 0) {
+        if (++t.iters > iter_limit) {  // a tree visits each node at most once
+            err |= 2;
+            t.ref = kNoRef;
+            t.sp = 0;
+            return;
+        }
+        const float4 n0 = __ldg(nodes + 4 * t.ref + 0);
+        const float4 n1 = __ldg(nodes + 4 * t.ref + 1);
+        const float4 n2 = __ldg(nodes + 4 * t.ref + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * t.ref + 3);
+        if (COUNT) n_nodes++;
+        const bool h0 = line_box(L, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
+        const bool h1 = line_box(L, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
+        if (h0 && h1) {
+            if (t.sp < kStackSize) {
+                stack[t.sp++] = n3.y;
+            } else {
+                err |= 1;
+            }
+            t.ref = n3.x;
+        } else if (h0) {
+            t.ref = n3.x;
+        } else if (h1) {
+            t.ref = n3.y;
+        } else {
+            t.ref = t.sp > 0 ? stack[--t.sp] : kNoRef;
+        }
+    }
+}
+
+// Test the triangles of leaf t.ref (Woop, Benthin, Wald, "Watertight
+// ray/triangle intersection", JCGT 2013, applied to a line: no parameter
+// range), record hits, flag near-degenerate configurations, then pop.
+template <bool COUNT, bool SUM_S>
+__device__ __forceinline__ void test_leaf(const float4* __restrict__ tv, const LinePre& L,
+                                          float3 d, float Tthr, float tauL, float graze,
+                                          int exclude_pos, Trav& t, int* hits, int* stack,
+                                          StreamKey key, uint32_t q, uint32_t walk,
+                                          uint32_t step, uint32_t& n_tris)
+{
+    const int first = leaf_first(t.ref), count = leaf_count(t.ref);
+    for (int p = first; p < first + count; ++p) {
+        if (p == exclude_pos) continue;
+        if (COUNT) n_tris++;
+        const float4 a4 = __ldg(tv + 3 * p + 0);
+        const float4 b4 = __ldg(tv + 3 * p + 1);
+        const float4 c4 = __ldg(tv + 3 * p + 2);
+        const float3 A = make_float3(a4.x - L.ox, a4.y - L.oy, a4.z - L.oz);
+        const float3 B = make_float3(b4.x - L.ox, b4.y - L.oy, b4.z - L.oz);
+        const float3 C = make_float3(c4.x - L.ox, c4.y - L.oy, c4.z - L.oz);
+        const float Akz = comp(A, L.kz), Bkz = comp(B, L.kz), Ckz = comp(C, L.kz);
+        const float Ax = fmaf(-L.Sx, Akz, comp(A, L.kx));
+        const float Ay = fmaf(-L.Sy, Akz, comp(A, L.ky));
+        const float Bx = fmaf(-L.Sx, Bkz, comp(B, L.kx));
+        const float By = fmaf(-L.Sy, Bkz, comp(B, L.ky));
+        const float Cx = fmaf(-L.Sx, Ckz, comp(C, L.kx));
+        const float Cy = fmaf(-L.Sy, Ckz, comp(C, L.ky));
+        const float U = Cx * By - Cy * Bx;
+        const float V = Ax * Cy - Ay * Cx;
+        const float W = Bx * Ay - By * Ax;
+        const bool pos_side = (U > -Tthr) && (V > -Tthr) && (W > -Tthr);
+        const bool neg_side = (U < Tthr) && (V < Tthr) && (W < Tthr);
+        if (!(pos_side || neg_side)) continue;
+        const float det = U + V + W;
+        const float mn = fminf(fminf(fabsf(U), fabsf(V)), fabsf(W));
+        if (mn < Tthr || fabsf(det) < graze * b4.w * fabsf(L.Sz)) t.flag = 1;
+        const bool hit = (U > 0.f && V > 0.f && W > 0.f) || (U < 0.f && V < 0.f && W < 0.f);
+        if (!hit) continue;
+        const float T = fmaf(U, L.Sz * Akz, fmaf(V, L.Sz * Bkz, W * (L.Sz * Ckz)));
+        const float tl = T / det;
+        if (fabsf(tl) < tauL) t.flag = 1;
+        if (t.m < kMaxHits) {
+            hits[t.m] = p;
+        } else {
+            // more hits than recorded: from here on keep a running minimum
+            uint32_t bprim = t.bpos >= 0 ? prim_of(tv, t.bpos) : 0xFFFFFFFFu;
+            if (t.m == kMaxHits)
+                for (int i = 0; i < kMaxHits; ++i)
+                    keep_min(hit_key(key, q, walk, step, prim_of(tv, hits[i])),
+                             prim_of(tv, hits[i]), hits[i], t.best, bprim, t.bpos);
+            keep_min(hit_key(key, q, walk, step, __float_as_uint(a4.w)), __float_as_uint(a4.w), p,
+                     t.best, bprim, t.bpos);
+        }
+        t.m++;
+        if (SUM_S) {
+            const float e1x = b4.x - a4.x, e1y = b4.y - a4.y, e1z = b4.z - a4.z;
+            const float e2x = c4.x - a4.x, e2y = c4.y - a4.y, e2z = c4.z - a4.z;
+            const float nx = e1y * e2z - e1z * e2y;
+            const float ny = e1z * e2x - e1x * e2z;
+            const float nz = e1x * e2y - e1y * e2x;
+            const float dn = d.x * nx + d.y * ny + d.z * nz;
+            t.sum_s += ((tl > 0.f) == (dn > 0.f)) ? 1 : -1;
+        }
+    }
+    t.ref = t.sp > 0 ? stack[--t.sp] : kNoRef;
+}
+
+// The picked hit (leaf position) after the traversal; -1 if m == 0.
+__device__ __forceinline__ int select_hit(const float4* __restrict__ tv, const Trav& t,
+                                          const int* hits, StreamKey key, uint32_t q,
+                                          uint32_t walk, uint32_t step)
+{
+    if (t.m == 0) return -1;
+    if (t.m == 1) return hits[0];
+    if (t.m > kMaxHits) return t.bpos;
+    uint64_t best = ~0ull;
+    uint32_t bprim = 0xFFFFFFFFu;
+    int bpos = -1;
+    for (int i = 0; i < t.m; ++i) {
+        const uint32_t prim = prim_of(tv, hits[i]);
+        keep_min(hit_key(key, q, walk, step, prim), prim, hits[i], best, bprim, bpos);
+    }
+    return bpos;
+}
+
+// Whole traversal of one line (debug entry point).
+template <bool SUM_S>
+__device__ __forceinline__ int trace_line(const float4* __restrict__ nodes,
+                                          const float4* __restrict__ tv, int root, float3 o,
+                                          float3 d, int exclude_pos, StreamKey key, uint32_t q,
+                                          uint32_t walk, uint32_t step, float edge_thr_L,
+                                          float tauL, float graze, Trav& t, int& err,
+                                          int iter_limit)
 {
     const LinePre L = line_pre(o, d);
-    // An edge closer than tau*L to the line has |U| < tau*L*max_edge/|d_kz|.
-    const float Tthr = edge_thr_L / L.dkz_abs;
-    LineHits h;
-    h.m = 0; h.pos = -1; h.sum_s = 0; h.flag = 0; h.best = ~0ull;
-    uint32_t best_prim = 0xFFFFFFFFu;
+    const float Tthr = edge_thr_L * fabsf(L.Sz);
     int stack[kStackSize];
-    int sp = 0;
-    int ref = root;
-    int iters = 0;  // a tree visits each node at most once: bounded loop
-    while (true) {
-        // interior nodes: descend until a leaf or nothing left
-        while (ref >= 0) {
-            if (++iters > iter_limit) {
-                overflow |= 2;
-                ref = kNoRef;
-                sp = 0;
-                break;
-            }
-            const float4 n0 = __ldg(nodes + 4 * ref + 0);
-            const float4 n1 = __ldg(nodes + 4 * ref + 1);
-            const float4 n2 = __ldg(nodes + 4 * ref + 2);
-            const int4 n3 = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * ref + 3);
-            if (COUNT) cnt.nodes++;
-            const bool h0 = line_box(L, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
-            const bool h1 = line_box(L, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
-            if (h0 && h1) {
-                if (sp < kStackSize) {
-                    stack[sp++] = n3.y;
-                } else {
-                    overflow |= 1;
-                }
-                ref = n3.x;
-            } else if (h0) {
-                ref = n3.x;
-            } else if (h1) {
-                ref = n3.y;
-            } else {
-                ref = sp > 0 ? stack[--sp] : kNoRef;
-            }
-        }
-        if (ref == kNoRef) break;
-        // leaf: test its triangles
-        const int first = leaf_first(ref), count = leaf_count(ref);
-        for (int p = first; p < first + count; ++p) {
-            if (p == exclude_pos) continue;
-            if (COUNT) cnt.tris++;
-            const float4 a4 = __ldg(tv + 3 * p + 0);
-            const float4 b4 = __ldg(tv + 3 * p + 1);
-            const float4 c4 = __ldg(tv + 3 * p + 2);
-            // vertices relative to the origin, then the shear that maps d to
-            // the kz axis (Woop, Benthin, Wald, JCGT 2013)
-            const float3 A = make_float3(a4.x - L.ox, a4.y - L.oy, a4.z - L.oz);
-            const float3 B = make_float3(b4.x - L.ox, b4.y - L.oy, b4.z - L.oz);
-            const float3 C = make_float3(c4.x - L.ox, c4.y - L.oy, c4.z - L.oz);
-            const float Akz = comp(A, L.kz), Bkz = comp(B, L.kz), Ckz = comp(C, L.kz);
-            const float Ax = fmaf(-L.Sx, Akz, comp(A, L.kx));
-            const float Ay = fmaf(-L.Sy, Akz, comp(A, L.ky));
-            const float Bx = fmaf(-L.Sx, Bkz, comp(B, L.kx));
-            const float By = fmaf(-L.Sy, Bkz, comp(B, L.ky));
-            const float Cx = fmaf(-L.Sx, Ckz, comp(C, L.kx));
-            const float Cy = fmaf(-L.Sy, Ckz, comp(C, L.ky));
-            const float U = Cx * By - Cy * Bx;
-            const float V = Ax * Cy - Ay * Cx;
-            const float W = Bx * Ay - By * Ax;
-            const bool pos_side = (U > -Tthr) && (V > -Tthr) && (W > -Tthr);
-            const bool neg_side = (U < Tthr) && (V < Tthr) && (W < Tthr);
-            if (pos_side || neg_side) {
-                const float det = U + V + W;
-                const float mn = fminf(fminf(fabsf(U), fabsf(V)), fabsf(W));
-                if (mn < Tthr || fabsf(det) * L.dkz_abs < graze * b4.w) h.flag = 1;
-                const bool hit = (U > 0.f && V > 0.f && W > 0.f) || (U < 0.f && V < 0.f && W < 0.f);
-                if (hit) {
-                    const float T = fmaf(U, L.Sz * Akz, fmaf(V, L.Sz * Bkz, W * (L.Sz * Ckz)));
-                    const float t = T / det;
-                    if (fabsf(t) < tauL) h.flag = 1;
-                    h.m++;
-                    const uint32_t prim = __float_as_uint(a4.w);
-                    const u32x4 k = stream_block(key, q, walk, step, kPurposeHit, 0u, prim);
-                    const uint64_t kk = ((uint64_t)k.x << 32) | (uint64_t)k.y;
-                    if (kk < h.best || (kk == h.best && prim < best_prim)) {
-                        h.best = kk;
-                        h.pos = p;
-                        best_prim = prim;
-                    }
-                    if (want_sum_s) {
-                        // s = sign(t) * sign(d . N)
-                        const float e1x = b4.x - a4.x, e1y = b4.y - a4.y, e1z = b4.z - a4.z;
-                        const float e2x = c4.x - a4.x, e2y = c4.y - a4.y, e2z = c4.z - a4.z;
-                        const float nx = e1y * e2z - e1z * e2y;
-                        const float ny = e1z * e2x - e1x * e2z;
-                        const float nz = e1x * e2y - e1y * e2x;
-                        const float dn = d.x * nx + d.y * ny + d.z * nz;
-                        h.sum_s += ((t > 0.f) == (dn > 0.f)) ? 1 : -1;
-                    }
-                }
-            }
-        }
-        ref = sp > 0 ? stack[--sp] : kNoRef;
-        if (ref == kNoRef) break;
+    int hits[kMaxHits];
+    uint32_t nn = 0, nt = 0;
+    trav_init(t, root);
+    while (t.ref != kNoRef) {
+        descend<false>(nodes, L, t, stack, nn, err, iter_limit);
+        if (t.ref == kNoRef) break;
+        test_leaf<false, SUM_S>(tv, L, d, Tthr, tauL, graze, exclude_pos, t, hits, stack, key, q,
+                                walk, step, nt);
     }
-    return h;
+    return select_hit(tv, t, hits, key, q, walk, step);
 }
 
 // FP64 refinement of the picked hit: intersection of the line x + t d with
@@ -311,6 +384,57 @@ __device__ __forceinline__ Refined refine_hit(const float4* __restrict__ tv, int
     r.y = make_double3(x.x + t * d.x, x.y + t * d.y, x.z + t * d.z);
     r.s = ((t > 0.0) == (dn > 0.0)) ? 1 : -1;
     return r;
+}
+
+// Dirichlet data g at a boundary point y of the triangle in leaf order `pos`.
+__device__ __forceinline__ float dl_data(const DataDev& D, const float4* __restrict__ tv, int pos,
+                                         double3 yd)
+{
+    const float3 y = make_float3((float)yd.x, (float)yd.y, (float)yd.z);
+    if (D.mode == WOB_DATA_POLY) {
+        const float* c = D.poly;
+        return c[0] + c[1] * y.x + c[2] * y.y + c[3] * y.z + c[4] * y.x * y.x +
+               c[5] * y.y * y.y + c[6] * y.z * y.z + c[7] * y.x * y.y + c[8] * y.y * y.z +
+               c[9] * y.z * y.x;
+    }
+    if (D.mode == WOB_DATA_POINT) {
+        const float dx = y.x - D.x0[0], dy = y.y - D.x0[1], dz = y.z - D.x0[2];
+        return D.scale / sqrtf(dx * dx + dy * dy + dz * dz);
+    }
+    // linear interpolation of vertex values over the triangle
+    const float4 a = __ldg(tv + 3 * pos), b = __ldg(tv + 3 * pos + 1), c = __ldg(tv + 3 * pos + 2);
+    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    const float px = y.x - a.x, py = y.y - a.y, pz = y.z - a.z;
+    const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float nn = nx * nx + ny * ny + nz * nz;
+    const float b1 = ((py * e2z - pz * e2y) * nx + (pz * e2x - px * e2z) * ny +
+                      (px * e2y - py * e2x) * nz) / nn;
+    const float b2 = ((e1y * pz - e1z * py) * nx + (e1z * px - e1x * pz) * ny +
+                      (e1x * py - e1y * px) * nz) / nn;
+    const int prim = __float_as_int(a.w);
+    const int32_t* t = D.tris + 3 * (int64_t)prim;
+    return (1.f - b1 - b2) * __ldg(D.vdata + t[0]) + b1 * __ldg(D.vdata + t[1]) +
+           b2 * __ldg(D.vdata + t[2]);
+}
+
+// One double-layer step after the line from x picked the hit at leaf
+// position `pos` among m hits (Sec. 4.1.1, 4.1.2): refine the hit in FP64,
+// update the weight product (first step -dG/dn_y/p = (m/2)s, later steps
+// 2 phi dG/dn_y/p = -phi m s) and add the source term (2 phi g, halved on the
+// last vertex).  Shared by every double-layer kernel so that they compute
+// identical values.
+__device__ __forceinline__ void dl_accumulate(const float4* __restrict__ tv, const DataDev& D,
+                                              int pos, int m, int k, int M, double phi,
+                                              double3& x, double3 d, double& S, double& P)
+{
+    const Refined r = refine_hit(tv, pos, x, d);
+    const double ms = (double)m * (double)r.s;
+    P = (k == 0) ? 0.5 * ms : P * (-phi * ms);
+    const double g = (double)dl_data(D, tv, pos, r.y);
+    const double c = (k == M - 1) ? phi : 2.0 * phi;
+    S = fma(P * c, g, S);
+    x = r.y;
 }
 
 }  // namespace wob

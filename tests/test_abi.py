@@ -64,7 +64,26 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib_path):
     assert lib.wob_solve(None, None, None, 4, 1, 4, 0, None, None, None) == -1
 
 
-def test_ptxas_reports_no_spills(lib_path):
+def _ptxas_functions(log):
+    """(function, registers, spill-store bytes) from a ptxas -v log."""
+    out = []
+    for block in log.split("Function properties for ")[1:]:
+        name = block.split()[0]
+        spill = re.search(r"(\d+) bytes spill stores", block)
+        regs = re.search(r"Used (\d+) registers", block)
+        out.append((name, int(regs.group(1)) if regs else 0, int(spill.group(1)) if spill else 0))
+    return out
+
+
+def test_ptxas_register_budget(lib_path):
+    """The walk kernel is held to 64 registers (8 blocks of 128 threads per
+    SM); only it may keep values in local memory, every other kernel fits in
+    registers."""
     log = open(os.path.join(os.path.dirname(lib_path), "ptxas.log")).read()
-    spills = re.findall(r"(\d+) bytes spill stores", log)
-    assert all(int(s) == 0 for s in spills), "register spills in the kernels"
+    funcs = _ptxas_functions(log)
+    assert funcs
+    for name, regs, spill in funcs:
+        if "k_dl_walks" in name:
+            assert regs <= 64, (name, regs)
+        else:
+            assert spill == 0, (name, spill)
