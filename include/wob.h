@@ -206,6 +206,58 @@ int wob_solve_host(const wob_problem *prob, const float *queries_host,
                    uint64_t seed, double *est_host, double *var_host, void *stream);
 
 /*
+ * Batched solves: P independent double-layer Dirichlet problems (each with
+ * its own mesh/BVH, data, walks and path length) run as ONE persistent
+ * launch, captured in a CUDA graph at creation and replayed by
+ * wob_batch_run.  The walks are cut into tiles of 32 * tile_rounds walks of
+ * one problem; warps take tiles from a global counter (one atomic per
+ * tile), so a warp always works on a single problem (one BVH, one path
+ * length).  Results equal P separate wob_solve calls with the same seed and
+ * the problems' own `problem` indices.
+ *   problems:      host array of P descriptors (kind must be WOB_DIRICHLET_DL)
+ *   query_offsets: host, P + 1; problem p owns queries/est/var rows
+ *                  [query_offsets[p], query_offsets[p+1])
+ *   walks, max_len: host, P each (walks >= 2, 1 <= max_len <= 4096)
+ *   queries:       device, query_offsets[P] x 3 float; est, var: device,
+ *                  query_offsets[P] doubles -- bound to the batch
+ *   params:        schedule; NULL or autotune = 1 times the candidate
+ *                  schedules once on this batch (walk counts scaled down)
+ *                  and caches the choice in $WOB_TUNE_CACHE (default
+ *                  ~/.cache/wob_autotune.json), keyed by GPU and batch shape
+ * The batch allocates Q_total * walks doubles of scratch at creation and
+ * keeps it until wob_batch_destroy.  The BVHs must outlive the batch.
+ */
+typedef struct wob_batch_s *wob_batch;
+
+typedef struct {
+    int32_t tile_rounds; /* tile = 32 * tile_rounds walks (1, 2 or 4) */
+    int32_t order;       /* 0: problem after problem; 1: costliest problems first */
+    int32_t autotune;    /* 1: choose tile_rounds and order by timing */
+    int32_t reserved[5];
+} wob_batch_params;
+
+typedef struct {
+    int32_t P;
+    int32_t tile_rounds;
+    int32_t order;
+    int32_t from_cache;    /* schedule read from the autotune cache */
+    int64_t queries;       /* total queries */
+    int64_t walks;         /* total walks */
+    int64_t max_lines;     /* total walks x their path lengths (upper bound) */
+    int64_t tiles;
+    double tune_ms[8];     /* measured candidates (tile_rounds x order), 0 if not run */
+} wob_batch_info;
+
+int wob_batch_create(const wob_problem *problems, int32_t P, const int64_t *query_offsets,
+                     const int32_t *walks, const int32_t *max_len, const float *queries,
+                     double *est, double *var, const wob_batch_params *params, void *stream,
+                     wob_batch *out);
+/* Replay the batch's graph on `stream` with this seed. */
+int wob_batch_run(wob_batch b, uint64_t seed, void *stream);
+int wob_batch_get_info(wob_batch b, wob_batch_info *out);
+void wob_batch_destroy(wob_batch b);
+
+/*
  * wob_solve for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of wob_solve.  wob_solve
  * allocates one double per walk of scratch on every call; a caller whose

@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
-    "WobError", "Mesh", "BVH", "Problem", "build_mesh", "build_bvh", "solve", "solve_range",
+    "WobError", "Mesh", "BVH", "Problem", "Batch", "build_mesh", "build_bvh", "solve", "solve_range",
     "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
@@ -60,6 +60,18 @@ class _Problem(ctypes.Structure):
                 ("vertex_data", ctypes.c_void_p), ("poly", ctypes.c_float * 10),
                 ("x0", ctypes.c_float * 3), ("scale", ctypes.c_float),
                 ("problem", ctypes.c_uint32), ("tau", ctypes.c_float)]
+
+
+class _BatchParams(ctypes.Structure):
+    _fields_ = [("tile_rounds", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("tile_rounds", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("queries", ctypes.c_int64),
+                ("walks", ctypes.c_int64), ("max_lines", ctypes.c_int64),
+                ("tiles", ctypes.c_int64), ("tune_ms", ctypes.c_double * 8)]
 
 
 class _DebugOut(ctypes.Structure):
@@ -116,6 +128,11 @@ def load_library() -> ctypes.CDLL:
                                   ctypes.c_int),
             "wob_trace_lines": ([P, P, P, P, P, I64, U64, U32, F, P, P, P, P, P, P, P, P],
                                 ctypes.c_int),
+            "wob_batch_create": ([P, I32, P, P, P, P, P, P, ctypes.POINTER(_BatchParams), P,
+                                  ctypes.POINTER(P)], ctypes.c_int),
+            "wob_batch_run": ([P, U64, P], ctypes.c_int),
+            "wob_batch_get_info": ([P, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
+            "wob_batch_destroy": ([P], None),
             "wob_line_axes": ([U64, U32, P, I64, P, P], ctypes.c_int),
             "wob_philox4x32_10": ([P, P, I64, P, P], ctypes.c_int),
         }
@@ -252,6 +269,65 @@ class Problem:
             p.x0[i] = float(c)
         p.scale, p.problem, p.tau = self.scale, self.problem, self.tau
         return p
+
+
+class Batch:
+    """Many double-layer problems in one graph-captured launch
+    (wob_batch_create / wob_batch_run).  `queries` is a list of per-problem
+    (Q_p, 3) arrays; est / var are (sum Q_p,) float64 CUDA tensors that every
+    run overwrites; `split()` returns them per problem."""
+
+    def __init__(self, problems, queries, walks, max_len, tile_rounds: int | None = None,
+                 order: int | None = None, stream=None):
+        import torch
+        lib = load_library()
+        P = len(problems)
+        qs = [np.asarray(q, np.float32).reshape(-1, 3) for q in queries]
+        self.offsets = np.zeros(P + 1, np.int64)
+        self.offsets[1:] = np.cumsum([len(q) for q in qs])
+        self.queries = _dev(np.concatenate(qs, 0) if P else np.zeros((0, 3), np.float32),
+                            torch.float32)
+        Qt = int(self.offsets[-1])
+        self.est = torch.empty(Qt, dtype=torch.float64, device="cuda")
+        self.var = torch.empty(Qt, dtype=torch.float64, device="cuda")
+        self._probs = (_Problem * P)(*[p._c() for p in problems])
+        self._keep = problems
+        w = np.ascontiguousarray(np.broadcast_to(np.asarray(walks, np.int32), (P,)))
+        m = np.ascontiguousarray(np.broadcast_to(np.asarray(max_len, np.int32), (P,)))
+        self.walks, self.max_len = w, m
+        bp = _BatchParams()
+        bp.autotune = 1 if tile_rounds is None else 0
+        bp.tile_rounds = tile_rounds or 1
+        bp.order = order or 0
+        h = ctypes.c_void_p()
+        _check(lib.wob_batch_create(self._probs, P, self.offsets.ctypes.data_as(ctypes.c_void_p),
+                                    w.ctypes.data_as(ctypes.c_void_p),
+                                    m.ctypes.data_as(ctypes.c_void_p), _ptr(self.queries),
+                                    _ptr(self.est), _ptr(self.var), ctypes.byref(bp),
+                                    _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, seed: int = 0, stream=None):
+        _check(load_library().wob_batch_run(self._h, seed, _stream(stream)))
+        return self.est, self.var
+
+    def info(self) -> dict:
+        i = _BatchInfo()
+        _check(load_library().wob_batch_get_info(self._h, ctypes.byref(i)))
+        return dict(P=i.P, tile_rounds=i.tile_rounds, order=i.order, from_cache=i.from_cache,
+                    queries=i.queries, walks=i.walks, max_lines=i.max_lines, tiles=i.tiles,
+                    tune_ms=list(i.tune_ms)[:6])
+
+    def split(self):
+        e, v = self.est.cpu().numpy(), self.var.cpu().numpy()
+        o = self.offsets
+        return [(e[o[i]:o[i + 1]], v[o[i]:o[i + 1]]) for i in range(len(o) - 1)]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.wob_batch_destroy(h)
+            self._h = None
 
 
 def solve(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,

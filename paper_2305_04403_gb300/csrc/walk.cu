@@ -40,64 +40,30 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
 {
     const StreamKey key{p.key0, p.key1};
     const int64_t total = p.Q * (int64_t)p.N;
-    const double phi = (double)p.phi;
+    const DLGeom G{p.nodes, p.tv, p.root, p.iter_limit, p.edge_thr_L, p.tauL, p.graze};
     int err = 0;
     int stack[kStackSize];
     int hits[kMaxHits];
-    unsigned long long c_lines = 0, c_nodes = 0, c_tris = 0, c_hits = 0, c_flag = 0;
+    WalkCount c{0, 0, 0, 0, 0};
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t qi = idx / p.N;
         const uint32_t q = p.q_base + (uint32_t)qi;
         const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
-        double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
-        int self = -1, wflag = 0, k = 0;
-        double S = 0.0, P = 1.0;
-        for (; k < p.M; ++k) {
-            const double3 d = line_axis(key, q, w, (uint32_t)k);
-            const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
-                                       make_float3((float)d.x, (float)d.y, (float)d.z));
-            const float Tthr = p.edge_thr_L * fabsf(L.Sz);
-            Trav t;
-            trav_init(t, p.root);
-            uint32_t nn = 0, nt = 0;
-            while (t.ref != kNoRef) {
-                descend<COUNT>(p.nodes, L, t, stack, nn, err, p.iter_limit);
-                if (t.ref == kNoRef) break;
-                test_leaf<COUNT, false>(p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL, p.graze,
-                                        self, t, hits, stack, key, q, w, (uint32_t)k, nt);
-            }
-            if (COUNT) {
-                c_lines++;
-                c_nodes += nn;
-                c_tris += nt;
-                c_hits += t.m;
-                c_flag += t.flag;
-            }
-            wflag |= t.flag;
-            if (DEBUG && p.line_m) p.line_m[idx * p.M + k] = t.m;
-            if (t.m == 0) {
-                ++k;
-                break;
-            }
-            const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
-            dl_accumulate(p.tv, p.data, pos, t.m, k, p.M, phi, x, d, S, P);
-            self = pos;
-        }
-        p.per_walk[idx] = S;
-        if (DEBUG) {
-            if (p.line_m)
-                for (int k2 = k; k2 < p.M; ++k2) p.line_m[idx * p.M + k2] = -1;
-            if (p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
-        }
+        const double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+        int wflag = 0;
+        p.per_walk[idx] = dl_walk<COUNT, DEBUG>(G, p.data, (double)p.phi, p.M, key, q, w, x, stack,
+                                                hits, err, wflag,
+                                                DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c);
+        if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
     }
     if (err) atomicOr(p.error_word, err);
     if (COUNT) {
-        atomicAdd(p.counters + 0, c_lines);
-        atomicAdd(p.counters + 1, c_nodes);
-        atomicAdd(p.counters + 2, c_tris);
-        atomicAdd(p.counters + 3, c_hits);
-        atomicAdd(p.counters + 4, c_flag);
+        atomicAdd(p.counters + 0, c.lines);
+        atomicAdd(p.counters + 1, c.nodes);
+        atomicAdd(p.counters + 2, c.tris);
+        atomicAdd(p.counters + 3, c.hits);
+        atomicAdd(p.counters + 4, c.flag);
     }
 }
 

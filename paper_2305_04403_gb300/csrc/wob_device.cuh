@@ -437,4 +437,68 @@ __device__ __forceinline__ void dl_accumulate(const float4* __restrict__ tv, con
     x = r.y;
 }
 
+// Geometry a double-layer walk needs.
+struct DLGeom {
+    const float4* nodes;
+    const float4* tv;
+    int root;
+    int iter_limit;
+    float edge_thr_L;
+    float tauL;
+    float graze;
+};
+
+struct WalkCount {
+    unsigned long long lines, nodes, tris, hits, flag;
+};
+
+// One double-layer walk from x (Sec. 4.1.1-4.1.2, ray sampling of Sec.
+// 4.4.1): per line, draw the axis, traverse (descend to a leaf, test it,
+// repeat), pick the hit (keys only when m > 1), refine it in FP64 and
+// accumulate.  Returns the walk value; `line_m` (optional) receives the hit
+// count of each line, -1 for lines not traced.
+template <bool COUNT, bool DEBUG>
+__device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, double phi, int M,
+                                          StreamKey key, uint32_t q, uint32_t w, double3 x,
+                                          int* stack, int* hits, int& err, int& wflag,
+                                          int32_t* line_m, WalkCount& c)
+{
+    int self = -1, k = 0;
+    double S = 0.0, P = 1.0;
+    for (; k < M; ++k) {
+        const double3 d = line_axis(key, q, w, (uint32_t)k);
+        const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
+                                   make_float3((float)d.x, (float)d.y, (float)d.z));
+        const float Tthr = G.edge_thr_L * fabsf(L.Sz);
+        Trav t;
+        trav_init(t, G.root);
+        uint32_t nn = 0, nt = 0;
+        while (t.ref != kNoRef) {
+            descend<COUNT>(G.nodes, L, t, stack, nn, err, G.iter_limit);
+            if (t.ref == kNoRef) break;
+            test_leaf<COUNT, false>(G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, G.tauL, G.graze,
+                                    self, t, hits, stack, key, q, w, (uint32_t)k, nt);
+        }
+        if (COUNT) {
+            c.lines++;
+            c.nodes += nn;
+            c.tris += nt;
+            c.hits += t.m;
+            c.flag += t.flag;
+        }
+        wflag |= t.flag;
+        if (DEBUG && line_m) line_m[k] = t.m;
+        if (t.m == 0) {
+            ++k;
+            break;
+        }
+        const int pos = select_hit(G.tv, t, hits, key, q, w, (uint32_t)k);
+        dl_accumulate(G.tv, D, pos, t.m, k, M, phi, x, d, S, P);
+        self = pos;
+    }
+    if (DEBUG && line_m)
+        for (int k2 = k; k2 < M; ++k2) line_m[k2] = -1;
+    return S;
+}
+
 }  // namespace wob

@@ -270,3 +270,59 @@ def poly_eval(c, p: np.ndarray) -> np.ndarray:
 def point_source_eval(x0, p: np.ndarray, scale: float = 1.0) -> np.ndarray:
     p = np.asarray(p, np.float64)
     return scale / np.linalg.norm(p - np.asarray(x0, np.float64), axis=-1)
+
+
+# --------------------------------------------------------------------------
+# many independent problems (the batched workload)
+# --------------------------------------------------------------------------
+@dataclass
+class BatchItem:
+    kind: str          # "star" or "torus"
+    verts: np.ndarray
+    tris: np.ndarray
+    queries: np.ndarray
+    max_len: int
+
+
+def _star_points(shape: StarShape, n: int, rng, lo: float = 0.05, hi: float = 0.85):
+    g = rng.standard_normal((n, 3))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    r = shape.radius(g) * (lo + (hi - lo) * rng.random(n))
+    return (g * r[:, None]).astype(np.float32)
+
+
+def _torus_points(shape: TorusShape, n: int, rng, frac: float = 0.8):
+    phi = rng.uniform(0, 2 * math.pi, n)
+    th = rng.uniform(0, 2 * math.pi, n)
+    rho = shape.tube(th, phi) * frac * np.sqrt(rng.random(n))
+    x = (shape.R + rho * np.cos(th)) * np.cos(phi)
+    y = (shape.R + rho * np.cos(th)) * np.sin(phi)
+    return np.stack([x, y, rho * np.sin(th)], 1).astype(np.float32)
+
+
+def batch_workload(n_problems: int = 512, t_range=(500, 50000), q_range=(64, 16384),
+                   m_range=(8, 24), seed: int = 4, q_scale: float = 1.0) -> list:
+    """Independent interior Dirichlet problems: each a seeded star-shaped
+    icosphere (level nearest to a log-uniform triangle count) or a displaced
+    torus (2 nu nv triangles ~ the same target), with a log-uniform number of
+    interior query points and a path length uniform in m_range."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for i in range(n_problems):
+        kind = "star" if rng.random() < 0.5 else "torus"
+        T = math.exp(rng.uniform(math.log(t_range[0]), math.log(t_range[1])))
+        Q = max(1, int(round(math.exp(rng.uniform(math.log(q_range[0]), math.log(q_range[1])))
+                             * q_scale)))
+        M = int(rng.integers(m_range[0], m_range[1] + 1))
+        sub = np.random.default_rng([seed, i])
+        if kind == "star":
+            level = int(min(6, max(2, round(math.log(T / 20.0, 4)))))
+            v, f, shape = star_mesh(level, 0.3, 6, int(sub.integers(1 << 30)))
+            q = _star_points(shape, Q, sub)
+        else:
+            nv = max(8, int(round(math.sqrt(T / 5.0))))
+            nu = max(8, int(round(2.5 * nv)))
+            v, f, shape = displaced_torus(nu, nv, seed=int(sub.integers(1 << 30)))
+            q = _torus_points(shape, Q, sub)
+        items.append(BatchItem(kind, v, f, q, M))
+    return items
