@@ -148,9 +148,16 @@ int run_walks(WalkParams& p, const wob_debug_out* dbg, bool counted, cudaStream_
     return launch_sl_walks(p, dbg != nullptr, s);
 }
 
+// Launch control words: traversal check word and the walk-tile counter.
+struct Control {
+    int err;
+    int pad;
+    unsigned long long next_tile;
+};
+
 struct Scratch {
     double* per_walk = nullptr;
-    int* err = nullptr;
+    Control* err = nullptr;
     unsigned long long* counters = nullptr;
     cudaStream_t s = nullptr;
     ~Scratch()
@@ -187,22 +194,23 @@ int solve_common(const wob_problem* prob, const float* queries, const int32_t* q
         WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.per_walk, Q * walks * sizeof(double), s));
         per_walk = sc.per_walk;
     }
-    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(int), s));
-    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(int), s));
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(Control), s));
+    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(Control), s));
+    p.tile_counter = &sc.err->next_tile;
     if (stats) {
         WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.counters, 5 * sizeof(unsigned long long), s));
         WOB_CUDA_TRY(cudaMemsetAsync(sc.counters, 0, 5 * sizeof(unsigned long long), s));
         p.counters = sc.counters;
     }
     p.per_walk = per_walk;
-    WOB_TRY(run_walks(p, dbg, stats != nullptr, s, sc.err));
+    WOB_TRY(run_walks(p, dbg, stats != nullptr, s, &sc.err->err));
     if (est) WOB_TRY(launch_reduce(per_walk, Q, walks, est, var, s));
     if (sum) WOB_TRY(launch_reduce_accum(per_walk, Q, walks, sum, sumsq, s));
     if (stats) {
         unsigned long long h[5];
         int herr = 0;
         WOB_CUDA_TRY(cudaMemcpyAsync(h, sc.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
-        WOB_CUDA_TRY(cudaMemcpyAsync(&herr, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        WOB_CUDA_TRY(cudaMemcpyAsync(&herr, &sc.err->err, sizeof(int), cudaMemcpyDeviceToHost, s));
         WOB_CUDA_TRY(cudaStreamSynchronize(s));
         stats->lines = (int64_t)h[0];
         stats->node_visits = (int64_t)h[1];

@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(128, 8)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t seed = *seed_dev;
+    __shared__ double slots[8 * 128];
+    const WalkSlot ws{slots + threadIdx.x, 128};
     int stack[kStackSize];
     int hits[kMaxHits];
     int err = 0;
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(128, 8)
                 int wflag = 0;
                 per_walk[P.walk_base + local] =
                     dl_walk<false, false>(G, P.data, (double)P.phi, P.M, key, (uint32_t)qi, w, x,
-                                          stack, hits, err, wflag, nullptr, c);
+                                          ws, stack, hits, err, wflag, nullptr, c);
             }
         }
     }

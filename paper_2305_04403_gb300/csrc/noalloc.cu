@@ -33,7 +33,7 @@ namespace {
 constexpr int64_t kNoAllocMaxWalkValues = int64_t(1) << 20;  // 8 MiB of doubles
 constexpr int kMaxDevices = 64;
 
-// Per-walk values of the most recent call, and the traversal check word.
+// Per-walk values of the most recent call; check word and walk-tile counter.
 static __device__ __align__(256) double g_walk_values[kNoAllocMaxWalkValues];
 static __device__ __align__(256) int g_check_word[64];
 
@@ -103,8 +103,9 @@ extern "C" int wob_solve_noalloc(const wob_problem* prob, const float* queries,
     WalkParams p;
     fill_params(p, prob, queries, query_prim, Q, 0, walks, max_len, seed);
     p.per_walk = values;  // every entry is written by the walk kernel
-    p.error_word = check;
-    WOB_CUDA_TRY(cudaMemsetAsync(check, 0, sizeof(int), s));  // must start at zero
+    p.error_word = check;                                                   // check[0]
+    p.tile_counter = reinterpret_cast<unsigned long long*>(check + 2);      // check[2..3]
+    WOB_CUDA_TRY(cudaMemsetAsync(check, 0, 4 * sizeof(int), s));  // both must start at zero
     if (p.kind == WOB_DIRICHLET_DL)
         WOB_TRY(launch_dl_walks(p, false, false, s));
     else

@@ -26,7 +26,9 @@ constexpr double kFourPi = 12.566370614359172953850573533118;
 #define WOB_DL_MIN_BLOCKS 8
 #endif
 
-// One thread owns one walk (grid-stride over the Q x N walks).  Per line:
+// One thread owns one walk; warps take tiles of 32 consecutive walks from a
+// global counter until none are left (dynamic balance; consecutive walks of
+// a query start their first lines at the same point).  Per line:
 // draw the axis, traverse (descend to a leaf, test it, repeat), then pick
 // the hit (keys only when m > 1), refine it in FP64 and accumulate.  The
 // kernel is limited to 64 registers (8 blocks of 128 threads per SM): the
@@ -41,19 +43,28 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
     const StreamKey key{p.key0, p.key1};
     const int64_t total = p.Q * (int64_t)p.N;
     const DLGeom G{p.nodes, p.tv, p.root, p.iter_limit, p.edge_thr_L, p.tauL, p.graze};
+    __shared__ double slots[8 * 128];
+    const WalkSlot ws{slots + threadIdx.x, 128};
     int err = 0;
     int stack[kStackSize];
     int hits[kMaxHits];
     WalkCount c{0, 0, 0, 0, 0};
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        // a warp takes the next 32 consecutive walks (one atomic per warp)
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(p.tile_counter, 1ull);
+        tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
+        if ((int64_t)tile * 32 >= total) break;
+        const int64_t idx = (int64_t)tile * 32 + lane;
+        if (idx >= total) continue;
         const int64_t qi = idx / p.N;
         const uint32_t q = p.q_base + (uint32_t)qi;
         const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
         const double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
         int wflag = 0;
-        p.per_walk[idx] = dl_walk<COUNT, DEBUG>(G, p.data, (double)p.phi, p.M, key, q, w, x, stack,
-                                                hits, err, wflag,
+        p.per_walk[idx] = dl_walk<COUNT, DEBUG>(G, p.data, (double)p.phi, p.M, key, q, w, x, ws,
+                                                stack, hits, err, wflag,
                                                 DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c);
         if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
     }

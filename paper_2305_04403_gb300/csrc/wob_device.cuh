@@ -452,6 +452,18 @@ struct WalkCount {
     unsigned long long lines, nodes, tris, hits, flag;
 };
 
+// Where a walk keeps its FP64 state (point, axis, S, P) while its lines are
+// traversed: eight doubles per thread in shared memory, structure of arrays
+// (field j of thread t at base[j * stride + t]) so that a warp's accesses
+// are conflict-free.  The state is touched once per line; keeping it out of
+// registers leaves the traversal loop its 64 registers.
+struct WalkSlot {
+    volatile double* base;  // &smem[threadIdx.x]
+    int stride;             // threads per block
+    __device__ __forceinline__ double get(int j) const { return base[j * stride]; }
+    __device__ __forceinline__ void set(int j, double v) const { base[j * stride] = v; }
+};
+
 // One double-layer walk from x (Sec. 4.1.1-4.1.2, ray sampling of Sec.
 // 4.4.1): per line, draw the axis, traverse (descend to a leaf, test it,
 // repeat), pick the hit (keys only when m > 1), refine it in FP64 and
@@ -459,16 +471,27 @@ struct WalkCount {
 // count of each line, -1 for lines not traced.
 template <bool COUNT, bool DEBUG>
 __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, double phi, int M,
-                                          StreamKey key, uint32_t q, uint32_t w, double3 x,
-                                          int* stack, int* hits, int& err, int& wflag,
-                                          int32_t* line_m, WalkCount& c)
+                                          StreamKey key, uint32_t q, uint32_t w, double3 x0,
+                                          const WalkSlot& ws, int* stack, int* hits, int& err,
+                                          int& wflag, int32_t* line_m, WalkCount& c)
 {
+    enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP };
+    ws.set(X0, x0.x);
+    ws.set(X1, x0.y);
+    ws.set(X2, x0.z);
+    ws.set(SS, 0.0);
+    ws.set(PP, 1.0);
     int self = -1, k = 0;
-    double S = 0.0, P = 1.0;
     for (; k < M; ++k) {
-        const double3 d = line_axis(key, q, w, (uint32_t)k);
-        const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
-                                   make_float3((float)d.x, (float)d.y, (float)d.z));
+        LinePre L;
+        {
+            const double3 d = line_axis(key, q, w, (uint32_t)k);
+            ws.set(D0, d.x);
+            ws.set(D1, d.y);
+            ws.set(D2, d.z);
+            L = line_pre(make_float3((float)ws.get(X0), (float)ws.get(X1), (float)ws.get(X2)),
+                         make_float3((float)d.x, (float)d.y, (float)d.z));
+        }
         const float Tthr = G.edge_thr_L * fabsf(L.Sz);
         Trav t;
         trav_init(t, G.root);
@@ -493,12 +516,20 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
             break;
         }
         const int pos = select_hit(G.tv, t, hits, key, q, w, (uint32_t)k);
+        double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
+        const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
+        double S = ws.get(SS), P = ws.get(PP);
         dl_accumulate(G.tv, D, pos, t.m, k, M, phi, x, d, S, P);
+        ws.set(X0, x.x);
+        ws.set(X1, x.y);
+        ws.set(X2, x.z);
+        ws.set(SS, S);
+        ws.set(PP, P);
         self = pos;
     }
     if (DEBUG && line_m)
         for (int k2 = k; k2 < M; ++k2) line_m[k2] = -1;
-    return S;
+    return ws.get(SS);
 }
 
 }  // namespace wob

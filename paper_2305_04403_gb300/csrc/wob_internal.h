@@ -91,6 +91,7 @@ struct WalkParams {
     int32_t* line_m;     // Q x N x M (optional)
     unsigned long long* counters;  // [lines, nodes, tris, hits, flagged] (optional)
     int* error_word;
+    unsigned long long* tile_counter;  // next walk tile (zero before the launch)
 };
 
 }  // namespace wob
