@@ -81,7 +81,7 @@ def _load():
             lib.oracle_trace_lines.argtypes = [P, I64, P, I64, P, P, P, P, I64, U64, U32, D, D,
                                                P, P, P, P, P, P, P, ctypes.c_int]
             lib.oracle_trace_lines.restype = ctypes.c_int
-            lib.oracle_dl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, P, I64,
+            lib.oracle_dl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, P, P, I64,
                                             I64, I64, I32, I32, U64, U32, D, D, P, P, P, P,
                                             ctypes.c_int]
             lib.oracle_dl_walks.restype = ctypes.c_int
@@ -201,8 +201,11 @@ def _data(mode: int, vertex_data=None, poly=None, x0=None, scale: float = 1.0):
 def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, problem: int = 0,
              phi: int = 1, mode: int = DATA_POLY, vertex_data=None, poly=None, x0=None,
              scale: float = 1.0, q_offset: int = 0, walk_begin: int = 0, tau: float = TAU,
-             graze: float = GRAZE, want_lines: bool = False, nthreads: int = 0) -> dict:
-    """Double-layer Dirichlet walks; returns per_walk (Q,N), flag (Q,N),
+             graze: float = GRAZE, want_lines: bool = False, nthreads: int = 0,
+             query_prim=None) -> dict:
+    """Double-layer Dirichlet walks; with query_prim (the triangle each query
+    lies on) the walks start on the boundary and estimate the density nu
+    there.  Returns per_walk (Q,N), flag (Q,N),
     abs_terms (Q,N: sum over the walk's terms of |term|, the scale of its
     rounding error) and, with want_lines, line_m (Q,N,M)."""
     v = _c(verts, np.float32)
@@ -214,8 +217,10 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     flag = np.empty((Q, walks), np.uint8)
     line_m = np.empty((Q, walks, max_len), np.int32) if want_lines else None
     abs_terms = np.empty((Q, walks), np.float64)
+    qp = None if query_prim is None else _c(query_prim, np.int32)
     rc = _load().oracle_dl_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
-                                 _p(q), Q, q_offset, walk_begin, walks, max_len, seed, problem,
+                                 _p(q), _p(qp), Q, q_offset, walk_begin, walks, max_len, seed,
+                                 problem,
                                  tau, graze, _p(per_walk), _p(flag), _p(line_m), _p(abs_terms),
                                  nthreads)
     del keep

@@ -394,16 +394,32 @@ static void trace_line(const mesh_t *M, const double o[3], const double d[3], in
 /*   first weight  -dG/dn_y / p        = (m/2) s                            */
 /*   later weights 2 phi dG/dn_y / p   = -phi m s                           */
 /* ------------------------------------------------------------------------ */
+/* start_prim >= 0: the walk starts ON the boundary, at x0 on that triangle,
+ * and estimates the density nu(x0) (Eq. indirect_double_boundary_reordered2):
+ * x0 is vertex 1 (first weight 1), and M - 1 lines follow. */
 static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const double x0[3],
-                      uint32_t q, uint32_t walk, int32_t Mlen, uint64_t seed, uint32_t problem,
-                      double tauL, double graze, uint8_t *flag, int32_t *line_m,
-                      double *abs_terms)
+                      int64_t start_prim, uint32_t q, uint32_t walk, int32_t Mlen,
+                      uint64_t seed, uint32_t problem, double tauL, double graze,
+                      uint8_t *flag, int32_t *line_m, double *abs_terms)
 {
     double x[3] = { x0[0], x0[1], x0[2] };
     int64_t exclude = -1;
     double S = 0.0, P = 1.0, W0 = 0.0, A = 0.0;
+    int32_t k0 = 0;
     *flag = 0;
-    for (int32_t k = 0; k < Mlen; ++k) {
+    if (start_prim >= 0) {
+        double b[3], n[3] = { 0.0, 0.0, 0.0 };
+        barycentric(M, start_prim, x, b);
+        double g = boundary_data(D, M, start_prim, x, b, n, KIND_DIRICHLET_DL, 0.0);
+        double c = (Mlen == 1) ? (double)phi : 2.0 * (double)phi;
+        W0 = 1.0;
+        S = c * g;
+        A = fabs(c * g);
+        exclude = start_prim;
+        k0 = 1;
+        if (line_m) line_m[0] = -1;
+    }
+    for (int32_t k = k0; k < Mlen; ++k) {
         double d[3];
         line_axis(seed, problem, q, walk, (uint32_t)k, d);
         line_result r;
@@ -415,6 +431,7 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
             W0 = 0.5 * (double)r.m * (double)r.s;
         else
             P *= -(double)phi * (double)r.m * (double)r.s;
+        /* line k reaches vertex k + 1 of the walk (density walks: vertex 1 is x0) */
         double n[3] = { 0.0, 0.0, 0.0 };
         double g = boundary_data(D, M, r.prim, r.y, r.b, n, KIND_DIRICHLET_DL, 0.0);
         double c = (k == Mlen - 1) ? (double)phi : 2.0 * (double)phi;
@@ -603,7 +620,8 @@ int oracle_trace_lines(const float *verts, int64_t V, const int32_t *tris, int64
  * walk_flag[q*N + w] = 1 if any line of the walk is near-degenerate;
  * line_m[(q*N + w)*M + k] = hit count of line k (-1: not traced). */
 int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t T,
-                    const oracle_data *D, int32_t phi, const float *queries, int64_t Q,
+                    const oracle_data *D, int32_t phi, const float *queries,
+                    const int32_t *query_prim, int64_t Q,
                     int64_t q_offset, int64_t walk_begin, int32_t N, int32_t Mlen,
                     uint64_t seed, uint32_t problem, double tau, double graze,
                     double *per_walk, uint8_t *walk_flag, int32_t *line_m, double *abs_terms,
@@ -625,7 +643,8 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
         }
         uint8_t f;
         double at;
-        per_walk[i] = dl_walk(&M, D, phi, x0, (uint32_t)(q_offset + qi),
+        per_walk[i] = dl_walk(&M, D, phi, x0, query_prim ? query_prim[qi] : -1,
+                              (uint32_t)(q_offset + qi),
                               (uint32_t)(walk_begin + w), Mlen, seed, problem, tauL, graze, &f, lm,
                               &at);
         if (walk_flag) walk_flag[i] = f;
