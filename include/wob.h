@@ -186,7 +186,21 @@ int wob_solve_range(const wob_problem *prob, const float *queries, const int32_t
                     int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len,
                     uint64_t seed, double *sum, double *sumsq, void *stream);
 
-/* As wob_solve, also writing the per-walk outputs of `dbg` (Q x walks). */
+/*
+ * Density of the double-layer representation at boundary points
+ * (Eq. indirect_double_boundary_reordered2, Sec. 4.1.1): walks start ON the
+ * boundary at points[q] (device, Q x 3) lying on triangle prims[q] (device,
+ * original triangle ids); the point is vertex 1 (weight 1) and M - 1 lines
+ * follow; est = mean of nu-hat, var = sample variance.  Only for
+ * WOB_DIRICHLET_DL.  These are the training targets of the control variate.
+ */
+int wob_solve_density(const wob_problem *prob, const float *points, const int32_t *prims,
+                      int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
+                      double *var, void *stream);
+
+/* As wob_solve, also writing the per-walk outputs of `dbg` (Q x walks);
+ * for WOB_DIRICHLET_DL a non-NULL query_prim selects density walks as in
+ * wob_solve_density. */
 int wob_solve_debug(const wob_problem *prob, const float *queries, const int32_t *query_prim,
                     int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
                     double *var, const wob_debug_out *dbg, void *stream);
@@ -256,6 +270,63 @@ int wob_batch_create(const wob_problem *problems, int32_t P, const int64_t *quer
 int wob_batch_run(wob_batch b, uint64_t seed, void *stream);
 int wob_batch_get_info(wob_batch b, wob_batch_info *out);
 void wob_batch_destroy(wob_batch b);
+
+/*
+ * Learned control variate (not in the paper; it reuses the double-layer
+ * representation of Sec. 3.3 and Table 1).  With nu = nu_t + rho, where
+ * nu_t is a network, rho solves rho = H rho + r with
+ *     r = 2 phi g - nu_t + H nu_t,   and   u(x0) = D nu_t(x0) + D rho(x0),
+ * (H f)(x) = 2 phi int dG/dn_y f dA, (D f)(x0) = -int dG/dn_y f dA.  The
+ * walks estimate only D rho; D nu_t and H nu_t are computed by quadrature
+ * (Radon's 7-point degree-5 rule per triangle; triangles whose centroid is
+ * within `near` x their longest edge of the target use 4^level
+ * sub-triangles; H subtracts nu_t(x) and adds H[1] = -phi).  Any nu_t keeps
+ * the estimator unbiased up to quadrature error; a good one makes r small.
+ *
+ * Network: 96 Fourier features (sin, cos of 2 pi 2^(k/3) y_d, k = 0..15,
+ * column 32 d + 2 k + {0: sin, 1: cos}) -> 4 x (64, SiLU) -> 1; parameters
+ * FP32 (device), layer by layer: W (out x in, row-major) then b; BF16
+ * tensor-core arithmetic with FP32 accumulation.
+ */
+int wob_mlp_num_params(void); /* 18753 */
+/* out[i] = network(x[i]), x device n x 3, out device n. */
+int wob_mlp_forward(const float *params, const float *x, int64_t n, float *out, void *stream);
+/* One step on the mean squared error of (network(x), target) over the n
+ * samples: gradients (deterministic, block order), then Adam (b1 0.9, b2
+ * 0.999, eps 1e-8, bias-corrected, `step` >= 1) on params / adam_m /
+ * adam_v unless lr == 0.  grad_out (n_params floats) and loss_out (1 float)
+ * are optional device outputs. */
+int wob_mlp_train_step(float *params, float *adam_m, float *adam_v, const float *x,
+                       const float *target, int64_t n, float lr, int32_t step, float *grad_out,
+                       float *loss_out, void *stream);
+
+typedef struct wob_cv_s *wob_cv;
+/* Quadrature nodes for a mesh (level 0..3, near > 0); node values start at 0.
+ * Synchronises.  The mesh must outlive the object. */
+int wob_cv_create(wob_mesh m, int32_t level, float near, void *stream, wob_cv *out);
+/* Node values = the network at every node. */
+int wob_cv_set_network(wob_cv c, const float *params, void *stream);
+/* Node values given directly (device; T x 7 coarse, T x F fine). */
+int wob_cv_set_node_values(wob_cv c, const float *coarse, const float *fine, void *stream);
+/* Copy the nodes (x, y, z, weight per node; T x 7 coarse, T x F fine) into
+ * caller device buffers of 4 floats per node. */
+int wob_cv_get_nodes(wob_cv c, float *coarse_out, float *fine_out, void *stream);
+int wob_cv_get_info(wob_cv c, int32_t *T, int32_t *F, int64_t *candidates);
+/* D f at n points off the surface / H f at n points on triangles prims with
+ * f(x) = fx (all device). */
+int wob_cv_quad_D(wob_cv c, const float *points, int64_t n, float *out, void *stream);
+int wob_cv_quad_H(wob_cv c, int32_t phi, const float *points, const int32_t *prims,
+                  const float *fx, int64_t n, float *out, void *stream);
+/* Residual walks walk_begin .. walk_begin + walks - 1 of Q queries:
+ * sum[q] += sum of walk values, sumsq[q] += sum of squares (as
+ * wob_solve_range); per_walk (Q x walks, optional) receives the values and
+ * dnt (Q floats, optional) D nu_t at the queries.  The estimate is
+ * dnt[q] + sum[q] / total walks.  prob: WOB_DIRICHLET_DL on c's mesh; the
+ * node values must come from the same `params` (wob_cv_set_network). */
+int wob_cv_solve(const wob_problem *prob, wob_cv c, const float *params, const float *queries,
+                 int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len, uint64_t seed,
+                 double *sum, double *sumsq, double *per_walk, float *dnt, void *stream);
+void wob_cv_destroy(wob_cv c);
 
 /*
  * wob_solve for callers that cannot allocate device memory.  The paper has no

@@ -261,7 +261,8 @@ def quad_H(nodes: Nodes, vals, x, prim: int, fx: float, phi: int = 1, near: floa
 # walks
 # --------------------------------------------------------------------------
 def cv_walks(verts, tris, queries, walks: int, max_len: int, params, nodes: Nodes, node_vals,
-             poly, seed: int = 0, problem: int = 0, phi: int = 1, tau: float = O.TAU):
+             poly, seed: int = 0, problem: int = 0, phi: int = 1, tau: float = O.TAU,
+             near: float = 3.0):
     """Residual walks for D rho (per walk values, Q x N) and D nu_t per query.
     Data: the harmonic polynomial `poly` evaluated at the walk's vertices.
     `params` None means nu_t = 0 (then the walks are plain WoB)."""
@@ -296,7 +297,7 @@ def cv_walks(verts, tris, queries, walks: int, max_len: int, params, nodes: Node
             src = 2.0 * phi * g
         else:
             nt, _ = mlp_forward(params, y)
-            hn = np.array([quad_H(nodes, node_vals, y[j], prim[j], nt[j], phi)
+            hn = np.array([quad_H(nodes, node_vals, y[j], prim[j], nt[j], phi, near)
                            for j in range(len(idx))])
             src = 2.0 * phi * g - nt + hn
         c = 0.5 if k == max_len - 1 else 1.0
@@ -305,7 +306,8 @@ def cv_walks(verts, tris, queries, walks: int, max_len: int, params, nodes: Node
         excl[idx] = prim
     Dnt = np.zeros(Q)
     if params is not None:
-        Dnt = np.array([quad_D(nodes, node_vals, q[j].astype(np.float64)) for j in range(Q)])
+        Dnt = np.array([quad_D(nodes, node_vals, q[j].astype(np.float64), near)
+                        for j in range(Q)])
     return S.reshape(Q, walks), flag.reshape(Q, walks), Dnt
 
 

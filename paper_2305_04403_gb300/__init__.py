@@ -21,7 +21,8 @@ from . import build as _build
 __all__ = [
     "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
     "WobError", "Mesh", "BVH", "Problem", "Batch", "build_mesh", "build_bvh", "solve", "solve_range",
-    "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "trace_lines", "line_axes", "philox4x32_10",
+    "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "solve_density",
+    "mlp_num_params", "mlp_forward", "mlp_train_step", "ControlVariate", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
 
@@ -128,6 +129,22 @@ def load_library() -> ctypes.CDLL:
                                   ctypes.c_int),
             "wob_trace_lines": ([P, P, P, P, P, I64, U64, U32, F, P, P, P, P, P, P, P, P],
                                 ctypes.c_int),
+            "wob_solve_density": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
+                                  ctypes.c_int),
+            "wob_mlp_num_params": ([], ctypes.c_int),
+            "wob_mlp_forward": ([P, P, I64, P, P], ctypes.c_int),
+            "wob_mlp_train_step": ([P, P, P, P, P, I64, F, I32, P, P, P], ctypes.c_int),
+            "wob_cv_create": ([P, I32, F, P, ctypes.POINTER(P)], ctypes.c_int),
+            "wob_cv_set_network": ([P, P, P], ctypes.c_int),
+            "wob_cv_set_node_values": ([P, P, P, P], ctypes.c_int),
+            "wob_cv_get_nodes": ([P, P, P, P], ctypes.c_int),
+            "wob_cv_get_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                 ctypes.POINTER(I64)], ctypes.c_int),
+            "wob_cv_quad_D": ([P, P, I64, P, P], ctypes.c_int),
+            "wob_cv_quad_H": ([P, I32, P, P, P, I64, P, P], ctypes.c_int),
+            "wob_cv_solve": ([ctypes.POINTER(_Problem), P, P, P, I64, I64, I32, I32, U64, P, P, P,
+                              P, P], ctypes.c_int),
+            "wob_cv_destroy": ([P], None),
             "wob_batch_create": ([P, I32, P, P, P, P, P, P, ctypes.POINTER(_BatchParams), P,
                                   ctypes.POINTER(P)], ctypes.c_int),
             "wob_batch_run": ([P, U64, P], ctypes.c_int),
@@ -361,6 +378,115 @@ def solve_noalloc(problem: Problem, queries, walks: int, max_len: int, seed: int
                                             max_len, seed, _ptr(est), _ptr(var),
                                             _stream(stream)))
     return est, var
+
+
+def solve_density(problem: Problem, points, prims, walks: int, max_len: int, seed: int = 0,
+                  stream=None):
+    """wob_solve_density: (est, var) of the density nu at boundary points."""
+    import torch
+    q = _dev(points, torch.float32).reshape(-1, 3)
+    pr = _dev(prims, torch.int32)
+    Q = q.shape[0]
+    est = torch.empty(Q, dtype=torch.float64, device="cuda")
+    var = torch.empty(Q, dtype=torch.float64, device="cuda")
+    pc = problem._c()
+    _check(load_library().wob_solve_density(ctypes.byref(pc), _ptr(q), _ptr(pr), Q, walks,
+                                            max_len, seed, _ptr(est), _ptr(var), _stream(stream)))
+    return est, var
+
+
+def mlp_num_params() -> int:
+    return load_library().wob_mlp_num_params()
+
+
+def mlp_forward(params, x, stream=None):
+    """wob_mlp_forward: the network at points x (n, 3) -> (n,) float32."""
+    import torch
+    pp = _dev(params, torch.float32)
+    xx = _dev(x, torch.float32).reshape(-1, 3)
+    out = torch.empty(xx.shape[0], dtype=torch.float32, device="cuda")
+    _check(load_library().wob_mlp_forward(_ptr(pp), _ptr(xx), xx.shape[0], _ptr(out),
+                                          _stream(stream)))
+    return out
+
+
+def mlp_train_step(params, adam_m, adam_v, x, target, lr: float, step: int, grad=None,
+                   loss=None, stream=None):
+    """wob_mlp_train_step on CUDA float32 tensors (params / adam_m / adam_v
+    updated in place)."""
+    _check(load_library().wob_mlp_train_step(
+        _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(x), _ptr(target), x.shape[0], lr, step,
+        _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+class ControlVariate:
+    """Quadrature nodes of a mesh and the residual walks (wob_cv_*)."""
+
+    def __init__(self, mesh: Mesh, level: int = 2, near: float = 2.0, stream=None):
+        h = ctypes.c_void_p()
+        _check(load_library().wob_cv_create(mesh.handle, level, near, _stream(stream),
+                                            ctypes.byref(h)))
+        self._h = h
+        self.mesh = mesh
+        T, F, nc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load_library().wob_cv_get_info(h, ctypes.byref(T), ctypes.byref(F), ctypes.byref(nc)))
+        self.T, self.F, self.candidates = T.value, F.value, nc.value
+
+    def nodes(self):
+        """(coarse (T, 7, 4), fine (T, F, 4)) float32 host copies: position, weight."""
+        import torch
+        c = torch.empty(self.T * 7 * 4, dtype=torch.float32, device="cuda")
+        f = torch.empty(self.T * self.F * 4, dtype=torch.float32, device="cuda")
+        _check(load_library().wob_cv_get_nodes(self._h, _ptr(c), _ptr(f), _stream(None)))
+        return (c.cpu().numpy().reshape(self.T, 7, 4), f.cpu().numpy().reshape(self.T, self.F, 4))
+
+    def set_network(self, params, stream=None):
+        import torch
+        self._params = _dev(params, torch.float32)
+        _check(load_library().wob_cv_set_network(self._h, _ptr(self._params), _stream(stream)))
+
+    def set_node_values(self, coarse, fine, stream=None):
+        import torch
+        c = _dev(coarse, torch.float32)
+        f = _dev(fine, torch.float32)
+        _check(load_library().wob_cv_set_node_values(self._h, _ptr(c), _ptr(f), _stream(stream)))
+        torch.cuda.synchronize()
+
+    def quad_D(self, points, stream=None):
+        import torch
+        pts = _dev(points, torch.float32).reshape(-1, 3)
+        out = torch.empty(pts.shape[0], dtype=torch.float32, device="cuda")
+        _check(load_library().wob_cv_quad_D(self._h, _ptr(pts), pts.shape[0], _ptr(out),
+                                            _stream(stream)))
+        return out
+
+    def quad_H(self, points, prims, fx, phi: int = 1, stream=None):
+        import torch
+        pts = _dev(points, torch.float32).reshape(-1, 3)
+        pr = _dev(prims, torch.int32)
+        f = _dev(fx, torch.float32)
+        out = torch.empty(pts.shape[0], dtype=torch.float32, device="cuda")
+        _check(load_library().wob_cv_quad_H(self._h, phi, _ptr(pts), _ptr(pr), _ptr(f),
+                                            pts.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def solve_range(self, problem: Problem, params, queries, walk_begin: int, walks: int,
+                    max_len: int, sum_, sumsq, seed: int = 0, per_walk=None, dnt=None,
+                    stream=None):
+        import torch
+        pp = _dev(params, torch.float32)
+        q = _dev(queries, torch.float32).reshape(-1, 3)
+        pc = problem._c()
+        _check(load_library().wob_cv_solve(ctypes.byref(pc), self._h, _ptr(pp), _ptr(q),
+                                           q.shape[0], walk_begin, walks, max_len, seed,
+                                           _ptr(sum_), _ptr(sumsq), _ptr(per_walk), _ptr(dnt),
+                                           _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.wob_cv_destroy(h)
+            self._h = None
 
 
 def solve_range(problem: Problem, queries, walk_begin: int, walks: int, max_len: int,

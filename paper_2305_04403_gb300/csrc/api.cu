@@ -171,7 +171,8 @@ struct Scratch {
 int solve_common(const wob_problem* prob, const float* queries, const int32_t* query_prim,
                  int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len, uint64_t seed,
                  double* est, double* var, double* sum, double* sumsq,
-                 const wob_debug_out* dbg, wob_stats* stats, cudaStream_t s)
+                 const wob_debug_out* dbg, wob_stats* stats, cudaStream_t s,
+                 bool density = false)
 {
     WOB_TRY(check_problem(prob));
     WOB_TRY(check_sizes(Q, walk_begin, walks, max_len));
@@ -180,7 +181,11 @@ int solve_common(const wob_problem* prob, const float* queries, const int32_t* q
         set_error("queries is NULL");
         return WOB_ERR_INVALID_ARG;
     }
-    if (prob->kind == WOB_DIRICHLET_DL && query_prim) {
+    if (density && (prob->kind != WOB_DIRICHLET_DL || !query_prim)) {
+        set_error("density walks need WOB_DIRICHLET_DL and query_prim");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (!density && prob->kind == WOB_DIRICHLET_DL && query_prim) {
         set_error("query_prim must be NULL for WOB_DIRICHLET_DL (the solution on the "
                   "boundary is the Dirichlet data)");
         return WOB_ERR_UNSUPPORTED;
@@ -358,6 +363,19 @@ int wob_solve(const wob_problem* prob, const float* queries, const int32_t* quer
                         nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
 }
 
+int wob_solve_density(const wob_problem* prob, const float* points, const int32_t* prims,
+                      int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double* est,
+                      double* var, void* stream)
+{
+    clear_error();
+    if (walks < 2 || (Q > 0 && (!est || !var || !prims))) {
+        set_error("wob_solve_density: walks < 2 or NULL est/var/prims");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return solve_common(prob, points, prims, Q, 0, walks, max_len, seed, est, var, nullptr,
+                        nullptr, nullptr, nullptr, (cudaStream_t)stream, true);
+}
+
 int wob_solve_range(const wob_problem* prob, const float* queries, const int32_t* query_prim,
                     int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len,
                     uint64_t seed, double* sum, double* sumsq, void* stream)
@@ -384,8 +402,9 @@ int wob_solve_debug(const wob_problem* prob, const float* queries, const int32_t
         set_error("walks < 2 or est/var NULL");
         return WOB_ERR_INVALID_ARG;
     }
+    const bool density = prob && prob->kind == WOB_DIRICHLET_DL && query_prim;
     return solve_common(prob, queries, query_prim, Q, 0, walks, max_len, seed, est, var,
-                        nullptr, nullptr, dbg, nullptr, (cudaStream_t)stream);
+                        nullptr, nullptr, dbg, nullptr, (cudaStream_t)stream, density);
 }
 
 int wob_solve_counted(const wob_problem* prob, const float* queries, const int32_t* query_prim,

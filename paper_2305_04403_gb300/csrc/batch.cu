@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128, 8)
                 int wflag = 0;
                 per_walk[P.walk_base + local] =
                     dl_walk<false, false>(G, P.data, (double)P.phi, P.M, key, (uint32_t)qi, w, x,
-                                          ws, stack, hits, err, wflag, nullptr, c);
+                                          -1, ws, stack, hits, err, wflag, nullptr, c);
             }
         }
     }

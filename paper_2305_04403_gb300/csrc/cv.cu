@@ -1,0 +1,612 @@
+// cv.cu -- the learned control variate: quadrature of its double-layer
+// integrals and the residual walks.
+//
+// With nu = nu_t + rho (nu_t the network), rho solves rho = H rho + r with
+//   r = 2 phi g - nu_t + H nu_t,   and   u(x0) = D nu_t(x0) + D rho(x0),
+// where (H f)(x) = 2 phi int dG/dn_y f dA (Table 1, Dirichlet source density)
+// and (D f)(x0) = -int dG/dn_y f dA (Eq. indirect_double_domain).  D nu_t and
+// H nu_t are computed by quadrature (Radon's 7-point degree-5 rule on every
+// triangle; triangles whose centroid lies closer than `near` times their
+// longest edge to the target are split into 4^level sub-triangles with the
+// same rule); H uses H[nu_t - nu_t(x)](x) - phi nu_t(x) (H[1] = -phi by
+// Gauss) and skips the target's own flat triangle.  The walk is the
+// double-layer recursion with r in place of 2 phi g.
+//
+// Residual walks run as a small wavefront per step: traverse + FP64 refine
+// (one thread per walk), the network at every new vertex (batched on the
+// tensor cores), then quadrature + accumulation (one thread per walk; the
+// far-field loop over triangles is the same for every lane of a warp, so its
+// node loads are broadcasts).
+#include <array>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "wob_device.cuh"
+#include "wob_host.h"
+
+namespace wob {
+
+namespace {
+
+constexpr int kCoarse = 7;
+constexpr int kMaxFine = 7 * 64;  // level <= 3
+constexpr float kInvFourPi = 0.0795774715459476678f;
+
+__constant__ float c_coarse_b[kCoarse * 3];
+__constant__ float c_coarse_w[kCoarse];
+__constant__ float c_fine_b[kMaxFine * 3];
+__constant__ float c_fine_w[kMaxFine];
+
+struct CvGeom {
+    int T;
+    int F;                       // fine nodes per triangle
+    const float4* tri_c;         // centroid, near radius (near x longest edge)
+    const float4* tri_n;         // unit normal, circumradius about the centroid
+    const float4* coarse;        // T x 7: position, weight
+    const float4* fine;          // T x F
+    const float* coarse_val;     // network values at the nodes
+    const float* fine_val;
+    const int* cand_off;         // per triangle: candidate near triangles
+    const int* cand;
+};
+
+// Radon's rule (degree 5) in barycentric coordinates and its
+// 4^level-subdivided version, computed once in double.
+void rule_tables(int level, std::vector<float>& cb, std::vector<float>& cw,
+                 std::vector<float>& fb, std::vector<float>& fw)
+{
+    const double s15 = std::sqrt(15.0);
+    const double a1 = (6.0 - s15) / 21.0, b1 = (9.0 + 2.0 * s15) / 21.0;
+    const double a2 = (6.0 + s15) / 21.0, b2 = (9.0 - 2.0 * s15) / 21.0;
+    const double w1 = (155.0 - s15) / 1200.0, w2 = (155.0 + s15) / 1200.0;
+    const double P[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {b1, a1, a1}, {a1, b1, a1}, {a1, a1, b1},
+                            {b2, a2, a2}, {a2, b2, a2}, {a2, a2, b2}};
+    const double W[7] = {9.0 / 40.0, w1, w1, w1, w2, w2, w2};
+    cb.clear();
+    cw.clear();
+    for (int q = 0; q < 7; ++q) {
+        for (int c = 0; c < 3; ++c) cb.push_back((float)P[q][c]);
+        cw.push_back((float)W[q]);
+    }
+    // sub-triangles as barycentric corner triples
+    std::vector<std::array<std::array<double, 3>, 3>> tris;
+    tris.push_back({{{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}});
+    for (int l = 0; l < level; ++l) {
+        std::vector<std::array<std::array<double, 3>, 3>> nxt;
+        for (auto& T : tris) {
+            std::array<double, 3> ab, bc, ca;
+            for (int c = 0; c < 3; ++c) {
+                ab[c] = 0.5 * (T[0][c] + T[1][c]);
+                bc[c] = 0.5 * (T[1][c] + T[2][c]);
+                ca[c] = 0.5 * (T[2][c] + T[0][c]);
+            }
+            nxt.push_back({{T[0], ab, ca}});
+            nxt.push_back({{T[1], bc, ab}});
+            nxt.push_back({{T[2], ca, bc}});
+            nxt.push_back({{ab, bc, ca}});
+        }
+        tris = nxt;
+    }
+    fb.clear();
+    fw.clear();
+    for (auto& T : tris)
+        for (int q = 0; q < 7; ++q) {
+            for (int c = 0; c < 3; ++c)
+                fb.push_back((float)(P[q][0] * T[0][c] + P[q][1] * T[1][c] + P[q][2] * T[2][c]));
+            fw.push_back((float)(W[q] / tris.size()));
+        }
+}
+
+__global__ void k_cv_nodes(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                           int T, int F, float near, float4* __restrict__ tri_c,
+                           float4* __restrict__ tri_n, float4* __restrict__ coarse,
+                           float4* __restrict__ fine)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
+        double v[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) v[k][c] = verts[3 * (int64_t)tris[3 * j + k] + c];
+        double e1[3], e2[3], e3[3], cen[3];
+        for (int c = 0; c < 3; ++c) {
+            e1[c] = v[1][c] - v[0][c];
+            e2[c] = v[2][c] - v[0][c];
+            e3[c] = v[2][c] - v[1][c];
+            cen[c] = (v[0][c] + v[1][c] + v[2][c]) / 3.0;
+        }
+        const double N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                             e1[0] * e2[1] - e1[1] * e2[0]};
+        const double nl = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        const double area = 0.5 * nl;
+        auto len = [](const double* e) { return sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]); };
+        const double h = fmax(len(e1), fmax(len(e2), len(e3)));
+        double R = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double d[3] = {v[k][0] - cen[0], v[k][1] - cen[1], v[k][2] - cen[2]};
+            R = fmax(R, len(d));
+        }
+        tri_c[j] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(near * h));
+        tri_n[j] = make_float4((float)(N[0] / nl), (float)(N[1] / nl), (float)(N[2] / nl), (float)R);
+        for (int q = 0; q < kCoarse; ++q) {
+            double p[3];
+            for (int c = 0; c < 3; ++c)
+                p[c] = c_coarse_b[3 * q] * v[0][c] + c_coarse_b[3 * q + 1] * v[1][c] +
+                       c_coarse_b[3 * q + 2] * v[2][c];
+            coarse[kCoarse * j + q] = make_float4((float)p[0], (float)p[1], (float)p[2],
+                                                  (float)(c_coarse_w[q] * area));
+        }
+        for (int q = 0; q < F; ++q) {
+            double p[3];
+            for (int c = 0; c < 3; ++c)
+                p[c] = c_fine_b[3 * q] * v[0][c] + c_fine_b[3 * q + 1] * v[1][c] +
+                       c_fine_b[3 * q + 2] * v[2][c];
+            fine[(int64_t)F * j + q] = make_float4((float)p[0], (float)p[1], (float)p[2],
+                                                   (float)(c_fine_w[q] * area));
+        }
+    }
+}
+
+// Candidates of triangle p: every j != p that can be near some point of p:
+// |c_j - c_p| < near_j + R_p.  Pass 0 counts, pass 1 fills.
+__global__ void k_cv_candidates(int T, const float4* __restrict__ tri_c,
+                                const float4* __restrict__ tri_n, const int* __restrict__ off,
+                                int* __restrict__ count, int* __restrict__ cand, int pass)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
+        const float4 cp = tri_c[p];
+        const float Rp = tri_n[p].w;
+        int n = 0;
+        for (int j = 0; j < T; ++j) {
+            if (j == p) continue;
+            const float4 cj = tri_c[j];
+            const float dx = cj.x - cp.x, dy = cj.y - cp.y, dz = cj.z - cp.z;
+            const float lim = cj.w + Rp;
+            if (dx * dx + dy * dy + dz * dz < lim * lim) {
+                if (pass == 1) cand[(p == 0 ? 0 : off[p - 1]) + n] = j;
+                ++n;
+            }
+        }
+        if (pass == 0) count[p] = n;
+    }
+}
+
+__device__ __forceinline__ float node_term(float4 nd, float v, float3 n, float3 x)
+{
+    const float rx = nd.x - x.x, ry = nd.y - x.y, rz = nd.z - x.z;
+    const float r2 = rx * rx + ry * ry + rz * rz;
+    const float rinv = rsqrtf(r2);
+    return nd.w * (rx * n.x + ry * n.y + rz * n.z) * (rinv * rinv * rinv) * kInvFourPi * v;
+}
+
+__device__ __forceinline__ bool is_near(float4 tc, float3 x)
+{
+    const float dx = tc.x - x.x, dy = tc.y - x.y, dz = tc.z - x.z;
+    return dx * dx + dy * dy + dz * dz < tc.w * tc.w;
+}
+
+// sum over quadrature nodes of w (r . n)/(4 pi r^3) (f(y) - fx), r = y - x,
+// i.e. -int dG/dn_y (f - fx) dA, skipping triangle `own` (-1: none).
+// Near triangles (fine nodes): per lane from the candidate list of `own`
+// when own >= 0, otherwise decided per triangle for the whole warp.
+__device__ float quad_sum(const CvGeom& c, float3 x, int own, float fx)
+{
+    float tot = 0.f;
+    for (int j = 0; j < c.T; ++j) {
+        const float4 tc = __ldg(c.tri_c + j);
+        const float4 tn4 = __ldg(c.tri_n + j);
+        const float3 n = make_float3(tn4.x, tn4.y, tn4.z);
+        const bool near_me = is_near(tc, x);
+        const bool skip = (j == own) || near_me;
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < kCoarse; ++q)
+            part += node_term(__ldg(c.coarse + kCoarse * j + q),
+                              __ldg(c.coarse_val + kCoarse * j + q) - fx, n, x);
+        tot += skip ? 0.f : part;
+        if (own < 0 && __any_sync(0xFFFFFFFFu, near_me)) {
+            float fpart = 0.f;
+            for (int q = 0; q < c.F; ++q)
+                fpart += node_term(__ldg(c.fine + (int64_t)c.F * j + q),
+                                   __ldg(c.fine_val + (int64_t)c.F * j + q) - fx, n, x);
+            tot += near_me ? fpart : 0.f;
+        }
+    }
+    if (own >= 0) {
+        for (int ci = own == 0 ? 0 : c.cand_off[own - 1]; ci < c.cand_off[own]; ++ci) {
+            const int j = c.cand[ci];
+            const float4 tc = __ldg(c.tri_c + j);
+            if (!is_near(tc, x)) continue;
+            const float4 tn4 = __ldg(c.tri_n + j);
+            const float3 n = make_float3(tn4.x, tn4.y, tn4.z);
+            for (int q = 0; q < c.F; ++q)
+                tot += node_term(__ldg(c.fine + (int64_t)c.F * j + q),
+                                 __ldg(c.fine_val + (int64_t)c.F * j + q) - fx, n, x);
+        }
+    }
+    return tot;
+}
+
+// (D f)(x0) at points off the surface.  Every lane of a warp runs the
+// triangle loop (the near-field branch is warp-uniform).
+__global__ void k_cv_quad_D(CvGeom c, const float* __restrict__ x, int64_t n, float* out)
+{
+    const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x + 31) / 32;
+    const int64_t rounds = (n + 31) / 32;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int64_t r = gw; r < rounds; r += warps_total) {
+        const int64_t i = r * 32 + (threadIdx.x & 31);
+        const bool ok = i < n;
+        const float3 p = ok ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2])
+                            : make_float3(0.f, 0.f, 0.f);
+        const float v = quad_sum(c, p, -1, 0.f);
+        if (ok) out[i] = v;
+    }
+}
+
+// (H f)(x) at points on triangles prims (original ids): 2 phi int dG/dn_y f
+// = -2 phi quad_sum(f - f(x)) - phi f(x).
+__global__ void k_cv_quad_H(CvGeom c, int phi, const float* __restrict__ x,
+                            const int32_t* __restrict__ prims, const float* __restrict__ fx,
+                            int64_t n, float* out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int own = prims[i];
+        if (own < 0 || own >= c.T) {  // not a triangle of this mesh
+            out[i] = __int_as_float(0x7FC00000);
+            continue;
+        }
+        const float3 p = make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]);
+        const float s = quad_sum(c, p, own, fx[i]);
+        out[i] = -2.f * (float)phi * s - (float)phi * fx[i];
+    }
+}
+
+// ------------------------------------------------------------ residual walks
+struct CvWalk {
+    double* x;    // 3 x W
+    double* S;    // walk sums = per-walk values
+    double* P;
+    int* self;    // leaf position of the current vertex (-1: off the surface)
+    int* alive;   // 0 once a line missed
+    float* vpos;  // 3 x W (contiguous per walk: x, y, z) for the network
+    float* nut;   // network value at the current vertex
+    int64_t W;
+};
+
+__global__ void k_cvw_init(WalkParams p, CvWalk st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.W;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = i / p.N;
+        st.x[i] = p.queries[3 * qi];
+        st.x[st.W + i] = p.queries[3 * qi + 1];
+        st.x[2 * st.W + i] = p.queries[3 * qi + 2];
+        st.S[i] = 0.0;
+        st.P[i] = 1.0;
+        st.self[i] = -1;
+        st.alive[i] = 1;
+    }
+}
+
+// Line of step k from the current vertex: traversal, pick, FP64 refine and
+// the weight (first step (m/2)s, later -phi m s).
+__global__ void __launch_bounds__(128, 8) k_cvw_trace(WalkParams p, CvWalk st, int k)
+{
+    const StreamKey key{p.key0, p.key1};
+    int stack[kStackSize];
+    int hits[kMaxHits];
+    int err = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.W;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!st.alive[i]) continue;
+        const int64_t qi = i / p.N;
+        const uint32_t q = p.q_base + (uint32_t)qi;
+        const uint32_t w = (uint32_t)(p.walk_begin + (i - qi * p.N));
+        const double3 x = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
+        const int self = st.self[i];
+        const double3 d = line_axis(key, q, w, (uint32_t)k);
+        const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
+                                   make_float3((float)d.x, (float)d.y, (float)d.z));
+        const float Tthr = p.edge_thr_L * fabsf(L.Sz);
+        Trav t;
+        trav_init(t, p.root);
+        uint32_t nn = 0, nt = 0;
+        while (t.ref != kNoRef) {
+            descend<false>(p.nodes, L, t, stack, nn, err, p.iter_limit);
+            if (t.ref == kNoRef) break;
+            test_leaf<false, false>(p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL, p.graze,
+                                    self, t, hits, stack, key, q, w, (uint32_t)k, nt);
+        }
+        if (t.m == 0) {
+            st.alive[i] = 0;
+            continue;
+        }
+        const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
+        const Refined r = refine_hit(p.tv, pos, x, d);
+        const double ms = (double)t.m * (double)r.s;
+        st.P[i] = (k == 0) ? 0.5 * ms : st.P[i] * (-(double)p.phi * ms);
+        st.x[i] = r.y.x;
+        st.x[st.W + i] = r.y.y;
+        st.x[2 * st.W + i] = r.y.z;
+        st.vpos[3 * i] = (float)r.y.x;
+        st.vpos[3 * i + 1] = (float)r.y.y;
+        st.vpos[3 * i + 2] = (float)r.y.z;
+        st.self[i] = pos;
+    }
+    if (err) atomicOr(p.error_word, err);
+}
+
+// Source r = 2 phi g - nu_t + H nu_t at the vertex reached at step k,
+// halved on the last vertex (Sec. 4.1.2), times the weight product.
+__global__ void k_cvw_accum(WalkParams p, CvWalk st, CvGeom c, int k)
+{
+    const double phi = (double)p.phi;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.W;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!st.alive[i]) continue;
+        const int pos = st.self[i];
+        const float3 v = make_float3(st.vpos[3 * i], st.vpos[3 * i + 1], st.vpos[3 * i + 2]);
+        const float fx = st.nut[i];
+        const int own = (int)prim_of(p.tv, pos);
+        const float h = -2.f * (float)p.phi * quad_sum(c, v, own, fx) - (float)p.phi * fx;
+        const double3 y = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
+        const double g = (double)dl_data(p.data, p.tv, pos, y);
+        const double r = 2.0 * phi * g - (double)fx + (double)h;
+        const double cw = (k == p.M - 1) ? 0.5 : 1.0;
+        st.S[i] = fma(st.P[i] * cw, r, st.S[i]);
+    }
+}
+
+}  // namespace
+}  // namespace wob
+
+using namespace wob;
+
+struct wob_cv_s {
+    const MeshDev* mesh = nullptr;
+    int T = 0, F = 0, level = 2;
+    float near = 2.f;
+    float4 *tri_c = nullptr, *tri_n = nullptr, *coarse = nullptr, *fine = nullptr;
+    float *coarse_val = nullptr, *fine_val = nullptr;
+    int *cand_off = nullptr, *cand = nullptr;
+    int64_t n_cand = 0;
+    CvGeom geom() const
+    {
+        return CvGeom{T, F, tri_c, tri_n, coarse, fine, coarse_val, fine_val, cand_off, cand};
+    }
+};
+
+namespace {
+
+void free_cv(wob_cv_s* c)
+{
+    for (void* p : {(void*)c->tri_c, (void*)c->tri_n, (void*)c->coarse, (void*)c->fine,
+                    (void*)c->coarse_val, (void*)c->fine_val, (void*)c->cand_off, (void*)c->cand})
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int wob_cv_create(wob_mesh m, int32_t level, float near, void* stream, wob_cv* out)
+{
+    clear_error();
+    if (!m || !out || level < 0 || level > 3 || !(near > 0.f)) {
+        set_error("wob_cv_create: invalid arguments (level 0..3, near > 0)");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (m->d.T > (1 << 20)) {
+        set_error("wob_cv_create: the control variate's quadrature supports up to 2^20 triangles");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    wob_cv_s* c = new (std::nothrow) wob_cv_s();
+    if (!c) return WOB_ERR_OOM;
+    c->mesh = &m->d;
+    c->T = (int)m->d.T;
+    c->level = level;
+    c->near = near;
+    c->F = 7 << (2 * level);
+    std::vector<float> cb, cw, fb, fw;
+    rule_tables(level, cb, cw, fb, fw);
+    auto fail = [&](int code, const char* msg) {
+        set_error("wob_cv_create: %s", msg);
+        cudaStreamSynchronize(s);
+        free_cv(c);
+        delete c;
+        return code;
+    };
+    if (cudaMemcpyToSymbolAsync(c_coarse_b, cb.data(), cb.size() * 4, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_coarse_w, cw.data(), cw.size() * 4, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_fine_b, fb.data(), fb.size() * 4, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_fine_w, fw.data(), fw.size() * 4, 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail(WOB_ERR_CUDA, "rule upload failed");
+    const int T = c->T;
+    if (cudaMalloc((void**)&c->tri_c, T * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->tri_n, T * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->coarse, (size_t)T * kCoarse * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->fine, (size_t)T * c->F * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->coarse_val, (size_t)T * kCoarse * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->fine_val, (size_t)T * c->F * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->cand_off, T * sizeof(int)) != cudaSuccess)
+        return fail(WOB_ERR_OOM, "device allocation failed");
+    cudaMemsetAsync(c->coarse_val, 0, (size_t)T * kCoarse * sizeof(float), s);
+    cudaMemsetAsync(c->fine_val, 0, (size_t)T * c->F * sizeof(float), s);
+    const int threads = 128;
+    const int grid = grid_for((const void*)k_cv_nodes, threads, 0, T);
+    k_cv_nodes<<<grid, threads, 0, s>>>(m->d.verts, m->d.tris, T, c->F, near, c->tri_c, c->tri_n,
+                                        c->coarse, c->fine);
+    int* count = nullptr;
+    if (cudaMallocAsync((void**)&count, T * sizeof(int), s) != cudaSuccess)
+        return fail(WOB_ERR_OOM, "device allocation failed");
+    k_cv_candidates<<<grid, threads, 0, s>>>(T, c->tri_c, c->tri_n, nullptr, count, nullptr, 0);
+    int rc = inclusive_scan<int>(count, c->cand_off, T, s);
+    int total = 0;
+    cudaMemcpyAsync(&total, c->cand_off + T - 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(count, s);
+    if (rc != WOB_OK || cudaStreamSynchronize(s) != cudaSuccess) return fail(WOB_ERR_CUDA, "node setup failed");
+    c->n_cand = total;
+    if (cudaMalloc((void**)&c->cand, (size_t)(total > 0 ? total : 1) * sizeof(int)) != cudaSuccess)
+        return fail(WOB_ERR_OOM, "device allocation failed");
+    k_cv_candidates<<<grid, threads, 0, s>>>(T, c->tri_c, c->tri_n, c->cand_off, nullptr, c->cand, 1);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(WOB_ERR_CUDA, "candidate lists failed");
+    *out = c;
+    return WOB_OK;
+}
+
+int wob_cv_set_network(wob_cv c, const float* params, void* stream)
+{
+    clear_error();
+    if (!c || !params) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    WOB_TRY(mlp_forward(params, (const float*)c->coarse, (int64_t)c->T * kCoarse, c->coarse_val, s, 4));
+    WOB_TRY(mlp_forward(params, (const float*)c->fine, (int64_t)c->T * c->F, c->fine_val, s, 4));
+    return WOB_OK;
+}
+
+int wob_cv_set_node_values(wob_cv c, const float* coarse, const float* fine, void* stream)
+{
+    clear_error();
+    if (!c || !coarse || !fine) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    WOB_CUDA_TRY(cudaMemcpyAsync(c->coarse_val, coarse, (size_t)c->T * kCoarse * 4, cudaMemcpyDeviceToDevice, s));
+    WOB_CUDA_TRY(cudaMemcpyAsync(c->fine_val, fine, (size_t)c->T * c->F * 4, cudaMemcpyDeviceToDevice, s));
+    return WOB_OK;
+}
+
+int wob_cv_get_nodes(wob_cv c, float* coarse_out, float* fine_out, void* stream)
+{
+    clear_error();
+    if (!c || !coarse_out || !fine_out) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    WOB_CUDA_TRY(cudaMemcpyAsync(coarse_out, c->coarse, (size_t)c->T * kCoarse * sizeof(float4),
+                                 cudaMemcpyDeviceToDevice, s));
+    WOB_CUDA_TRY(cudaMemcpyAsync(fine_out, c->fine, (size_t)c->T * c->F * sizeof(float4),
+                                 cudaMemcpyDeviceToDevice, s));
+    return WOB_OK;
+}
+
+int wob_cv_quad_D(wob_cv c, const float* points, int64_t n, float* out, void* stream)
+{
+    clear_error();
+    if (!c || n < 0 || (n > 0 && (!points || !out))) {
+        set_error("wob_cv_quad_D: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (n == 0) return WOB_OK;
+    const int grid = grid_for((const void*)k_cv_quad_D, 128, 0, n);
+    k_cv_quad_D<<<grid, 128, 0, (cudaStream_t)stream>>>(c->geom(), points, n, out);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int wob_cv_quad_H(wob_cv c, int32_t phi, const float* points, const int32_t* prims,
+                  const float* fx, int64_t n, float* out, void* stream)
+{
+    clear_error();
+    if (!c || (phi != 1 && phi != -1) || n < 0 || (n > 0 && (!points || !prims || !fx || !out))) {
+        set_error("wob_cv_quad_H: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (n == 0) return WOB_OK;
+    const int grid = grid_for((const void*)k_cv_quad_H, 128, 0, n);
+    k_cv_quad_H<<<grid, 128, 0, (cudaStream_t)stream>>>(c->geom(), phi, points, prims, fx, n, out);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const float* queries,
+                 int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len, uint64_t seed,
+                 double* sum, double* sumsq, double* per_walk, float* dnt, void* stream)
+{
+    clear_error();
+    if (!c || !params || (Q > 0 && (!queries || !sum || !sumsq))) {
+        set_error("wob_cv_solve: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    WOB_TRY(check_problem(prob));
+    WOB_TRY(check_sizes(Q, walk_begin, walks, max_len));
+    if (prob->kind != WOB_DIRICHLET_DL || prob->bvh->d.mesh != c->mesh) {
+        set_error("wob_cv_solve: needs WOB_DIRICHLET_DL on the control variate's mesh");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    if (Q == 0) return WOB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    WalkParams p;
+    fill_params(p, prob, queries, nullptr, Q, walk_begin, walks, max_len, seed);
+    CvWalk st;
+    st.W = Q * (int64_t)walks;
+    const size_t W = (size_t)st.W;
+    char* buf = nullptr;
+    const size_t bytes = W * (8 * 5 + 4 * 2 + 4 * 4) + 256;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
+    st.x = (double*)buf;
+    st.S = st.x + 3 * W;
+    st.P = st.S + W;
+    st.self = (int*)(st.P + W);
+    st.alive = st.self + W;
+    st.vpos = (float*)(st.alive + W);
+    st.nut = st.vpos + 3 * W;
+    int* err = (int*)(st.nut + W);
+    int rc = WOB_OK;
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    p.error_word = err;
+    const CvGeom g = c->geom();
+    const int threads = 128;
+    k_cvw_init<<<grid_for((const void*)k_cvw_init, threads, 0, st.W), threads, 0, s>>>(p, st);
+    const int g_trace = grid_for((const void*)k_cvw_trace, threads, 0, st.W);
+    const int g_acc = grid_for((const void*)k_cvw_accum, threads, 0, st.W);
+    for (int k = 0; k < max_len && rc == WOB_OK; ++k) {
+        k_cvw_trace<<<g_trace, threads, 0, s>>>(p, st, k);
+        rc = mlp_forward(params, st.vpos, st.W, st.nut, s, 3);
+        if (rc == WOB_OK) k_cvw_accum<<<g_acc, threads, 0, s>>>(p, st, g, k);
+    }
+    if (rc == WOB_OK && cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+    if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s);
+    if (rc == WOB_OK && per_walk)
+        if (cudaMemcpyAsync(per_walk, st.S, W * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            rc = WOB_ERR_CUDA;
+    if (rc == WOB_OK && dnt) {
+        const int grid = grid_for((const void*)k_cv_quad_D, 128, 0, Q);
+        k_cv_quad_D<<<grid, 128, 0, s>>>(g, queries, Q, dnt);
+        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+    }
+    cudaFreeAsync(buf, s);
+    if (rc != WOB_OK) set_error("wob_cv_solve failed");
+    return rc;
+}
+
+int wob_cv_get_info(wob_cv c, int32_t* T, int32_t* F, int64_t* candidates)
+{
+    clear_error();
+    if (!c) {
+        set_error("NULL argument");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (T) *T = c->T;
+    if (F) *F = c->F;
+    if (candidates) *candidates = c->n_cand;
+    return WOB_OK;
+}
+
+void wob_cv_destroy(wob_cv c)
+{
+    if (!c) return;
+    free_cv(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -77,7 +77,7 @@ __global__ void k_vertex_bounds(const float* __restrict__ verts, int64_t V,
 // longest-edge reductions, index and degeneracy checks.
 __global__ void k_triangles(const float* __restrict__ verts, int64_t V,
                             const int32_t* __restrict__ tris, int64_t T,
-                            double4* __restrict__ tri_n, double* __restrict__ area,
+                            NormalArea* __restrict__ tri_n, double* __restrict__ area,
                             double* __restrict__ volume, unsigned int* __restrict__ max_edge,
                             int* __restrict__ err)
 {
@@ -88,7 +88,7 @@ __global__ void k_triangles(const float* __restrict__ verts, int64_t V,
         const int32_t i0 = tris[3 * j], i1 = tris[3 * j + 1], i2 = tris[3 * j + 2];
         if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= V || i1 >= V || i2 >= V) {
             atomicOr(err, kErrIndex);
-            tri_n[j] = make_double4(0.0, 0.0, 0.0, 0.0);
+            tri_n[j] = NormalArea{0.0, 0.0, 0.0, 0.0};
             area[j] = 0.0;
             continue;
         }
@@ -102,11 +102,11 @@ __global__ void k_triangles(const float* __restrict__ verts, int64_t V,
         const double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         if (!(nl > 0.0) || !isfinite(nl)) {
             atomicOr(err, kErrZeroArea);
-            tri_n[j] = make_double4(0.0, 0.0, 0.0, 0.0);
+            tri_n[j] = NormalArea{0.0, 0.0, 0.0, 0.0};
             area[j] = 0.0;
             continue;
         }
-        tri_n[j] = make_double4(n[0] / nl, n[1] / nl, n[2] / nl, 0.5 * nl);
+        tri_n[j] = NormalArea{n[0] / nl, n[1] / nl, n[2] / nl, 0.5 * nl};
         area[j] = 0.5 * nl;
         // signed volume: a . (b x c) / 6
         vol += (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
@@ -235,7 +235,7 @@ int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t 
     m.T = T;
     WOB_CUDA_TRY(cudaMalloc((void**)&m.verts, V * 3 * sizeof(float)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.tris, T * 3 * sizeof(int32_t)));
-    WOB_CUDA_TRY(cudaMalloc((void**)&m.tri_n, T * sizeof(double4)));
+    WOB_CUDA_TRY(cudaMalloc((void**)&m.tri_n, T * sizeof(NormalArea)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.cdf, T * sizeof(double)));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     WOB_CUDA_TRY(cudaMemcpyAsync(m.verts, verts, V * 3 * sizeof(float), kind, s));

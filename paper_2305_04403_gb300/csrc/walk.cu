@@ -63,8 +63,13 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
         const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
         const double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
         int wflag = 0;
-        p.per_walk[idx] = dl_walk<COUNT, DEBUG>(G, p.data, (double)p.phi, p.M, key, q, w, x, ws,
-                                                stack, hits, err, wflag,
+        int start = -1;
+        if (p.query_prim) {  // density walks from boundary points
+            const int32_t prim = p.query_prim[qi];
+            start = (prim >= 0 && prim < p.T) ? p.inv_order[prim] : -1;
+        }
+        p.per_walk[idx] = dl_walk<COUNT, DEBUG>(G, p.data, (double)p.phi, p.M, key, q, w, x, start,
+                                                ws, stack, hits, err, wflag,
                                                 DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c);
         if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
     }

@@ -468,12 +468,16 @@ struct WalkSlot {
 // 4.4.1): per line, draw the axis, traverse (descend to a leaf, test it,
 // repeat), pick the hit (keys only when m > 1), refine it in FP64 and
 // accumulate.  Returns the walk value; `line_m` (optional) receives the hit
-// count of each line, -1 for lines not traced.
+// count of each line, -1 for lines not traced.  start_pos >= 0: x0 lies on
+// that triangle (leaf position) and the walk estimates the density nu(x0)
+// (Eq. indirect_double_boundary_reordered2): x0 is vertex 1 with weight 1
+// and lines 1 .. M-1 follow.
 template <bool COUNT, bool DEBUG>
 __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, double phi, int M,
                                           StreamKey key, uint32_t q, uint32_t w, double3 x0,
-                                          const WalkSlot& ws, int* stack, int* hits, int& err,
-                                          int& wflag, int32_t* line_m, WalkCount& c)
+                                          int start_pos, const WalkSlot& ws, int* stack,
+                                          int* hits, int& err, int& wflag, int32_t* line_m,
+                                          WalkCount& c)
 {
     enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP };
     ws.set(X0, x0.x);
@@ -482,6 +486,13 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
     ws.set(SS, 0.0);
     ws.set(PP, 1.0);
     int self = -1, k = 0;
+    if (start_pos >= 0) {
+        const double g = (double)dl_data(D, G.tv, start_pos, x0);
+        ws.set(SS, ((M == 1) ? phi : 2.0 * phi) * g);
+        self = start_pos;
+        k = 1;
+        if (DEBUG && line_m) line_m[0] = -1;
+    }
     for (; k < M; ++k) {
         LinePre L;
         {

@@ -67,4 +67,11 @@ int launch_line_axes(uint32_t key0, uint32_t key1, const uint32_t* qws, int64_t 
 int launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                   cudaStream_t s);
 
+// mlp.cu: the control variate's network
+int mlp_forward(const float* params, const float* x, int64_t n, float* out, cudaStream_t s,
+                int stride);  // point r at x[stride * r .. + 2]
+int mlp_train_step(float* params, float* m, float* v, const float* x, const float* target,
+                   int64_t n, float lr, int step, float* grad_out, float* loss_out,
+                   cudaStream_t s);
+
 }  // namespace wob

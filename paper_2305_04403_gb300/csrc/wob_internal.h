@@ -19,10 +19,15 @@ constexpr float kDefaultTau = 2e-6f;
 constexpr float kGraze = 1e-4f;
 constexpr int kMaxLen = 4096;
 
+// Per-triangle unit normal and area, FP64 (32 bytes, read as two 16-byte loads).
+struct alignas(32) NormalArea {
+    double nx, ny, nz, area;
+};
+
 struct MeshDev {
     float* verts = nullptr;   // V x 3
     int32_t* tris = nullptr;  // T x 3
-    double4* tri_n = nullptr; // unit normal (FP64), area
+    NormalArea* tri_n = nullptr;  // unit normal (FP64), area
     double* cdf = nullptr;    // inclusive prefix sums of areas
     int64_t V = 0, T = 0;
     double lo[3], hi[3];
@@ -62,7 +67,7 @@ struct WalkParams {
     int iter_limit;  // traversal loop bound (4 x nodes + 64)
     const float* verts;
     const int32_t* tris;
-    const double4* tri_n;
+    const NormalArea* tri_n;
     const double* cdf;
     int64_t T;
     double area;

@@ -1,0 +1,200 @@
+"""GPU parity for the learned control variate: the BF16 tensor-core network
+against the oracle's FP64 network (same weights), density walks, the
+quadratures of D and H, and the residual walks.
+
+Bars: network outputs and gradients within 2e-2 (relative, BF16 operands);
+quadratures within 5e-5 (FP32 sums against FP64); residual walks with a zero
+network equal plain walks (1e-12) and with a constant network reproduce the
+plain walks (quadrature error); against the oracle's residual walks with the
+same random network, per walk within 3e-2 * M * max|nu_t| (BF16 network).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import cv as C
+from paper_2305_04403_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wob():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as w
+    return w
+
+
+def _params32(seed=2):
+    flat = C.flatten(C.mlp_init(seed)).astype(np.float32)
+    return flat, C.unflatten(flat.astype(np.float64))
+
+
+def _sphere_points(n, seed):
+    rng = np.random.default_rng(seed)
+    y = rng.standard_normal((n, 3))
+    return (y / np.linalg.norm(y, axis=1, keepdims=True)).astype(np.float32)
+
+
+def test_mlp_forward_matches_oracle(wob):
+    flat, params = _params32()
+    assert wob.mlp_num_params() == flat.size
+    y = _sphere_points(3000, 1)
+    got = wob.mlp_forward(flat, y).cpu().numpy()
+    ref, _ = C.mlp_forward(params, y.astype(np.float64))
+    assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), np.abs(got - ref).max()
+    # ragged tail: sizes that are not multiples of the 16-row tile
+    for n in (1, 15, 17, 33):
+        g = wob.mlp_forward(flat, y[:n]).cpu().numpy()
+        assert np.allclose(g, got[:n], rtol=0, atol=1e-6)
+
+
+def test_mlp_gradients_match_oracle(wob):
+    flat, params = _params32()
+    rng = np.random.default_rng(3)
+    n = 200
+    y = _sphere_points(n, 4)
+    target = rng.standard_normal(n).astype(np.float32)
+    p = torch.from_numpy(flat).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    grad = torch.empty_like(p)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    wob.mlp_train_step(p, m, v, torch.from_numpy(y).cuda(), torch.from_numpy(target).cuda(),
+                       0.0, 1, grad=grad, loss=loss)
+    g = grad.cpu().numpy()
+    ref_loss, ref = C.mse_grad(params, y.astype(np.float64), target.astype(np.float64))
+    assert abs(loss.item() - ref_loss) <= 2e-2 * ref_loss
+    o = 0
+    for fan_in, fan_out in C.LAYERS:
+        for size in (fan_in * fan_out, fan_out):
+            a, b = g[o:o + size], ref[o:o + size]
+            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-7, (o, size)
+            o += size
+    assert torch.equal(p, torch.from_numpy(flat).cuda())  # lr = 0: no update
+
+
+def test_mlp_training_reduces_loss(wob):
+    flat, _ = _params32()
+    y = _sphere_points(8192, 5)
+    target = (1.5 * y[:, 2] + 0.3 * y[:, 0] * y[:, 1]).astype(np.float32)
+    p = torch.from_numpy(flat).cuda()
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    yd, td = torch.from_numpy(y).cuda(), torch.from_numpy(target).cuda()
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    wob.mlp_train_step(p, m, v, yd, td, 0.0, 1, loss=loss)
+    l0 = loss.item()
+    for step in range(1, 401):
+        sl = slice((step * 1024) % 8192, (step * 1024) % 8192 + 1024)
+        wob.mlp_train_step(p, m, v, yd[sl], td[sl], 1e-3, step)
+    wob.mlp_train_step(p, m, v, yd, td, 0.0, 1, loss=loss)
+    assert loss.item() < 0.05 * l0, (l0, loss.item())
+
+
+def test_density_walks_parity(wob):
+    v, f, sh = I.star_mesh(4, 0.3, 6, 3, 0.5)
+    p, prim = I.boundary_points(v, f, 40, 8)
+    poly = (0.1, 0.3, -0.2, 0.5, 1.0, -1.0, 0.0, 0.4, 0.0, 0.0)
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh)
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=poly, tau=O.TAU)
+    g = {k: t.cpu().numpy() for k, t in
+         wob.solve_debug(prob, p, 48, 6, seed=2, query_prim=prim).items()}
+    r = O.dl_walks(v, f, p, 48, 6, seed=2, poly=poly, query_prim=prim, want_lines=True)
+    ok = (g["flag"] == 0) & (r["flag"] == 0)
+    assert ok.mean() > 0.8
+    err = np.abs(g["per_walk"] - r["per_walk"])
+    assert np.all(err[ok] <= 1e-5 * r["abs_terms"][ok] + 1e-12)
+    assert np.array_equal(g["line_m"][ok], r["line_m"][ok])
+    e2, _ = wob.solve_density(prob, p, prim, 48, 6, seed=2)
+    assert torch.equal(e2.cpu(), torch.from_numpy(g["est"]))
+
+
+@pytest.fixture(scope="module")
+def sphere_cv(wob):
+    v, f = I.icosphere(3)
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh)
+    cvo = wob.ControlVariate(mesh, level=2, near=2.0)
+    nodes = C.Nodes(v, f, level=2)
+    return v, f, mesh, bvh, cvo, nodes
+
+
+def test_quadrature_parity(wob, sphere_cv):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    fz = lambda q: q[..., 2] + 0.3 * q[..., 0] * q[..., 1] - 0.2
+    c4, f4 = cvo.nodes()
+    cvo.set_node_values(fz(c4[..., :3].astype(np.float64)).astype(np.float32),
+                        fz(f4[..., :3].astype(np.float64)).astype(np.float32))
+    # node positions and weights agree with the oracle's
+    assert np.allclose(c4[..., :3], nodes.coarse_pos, atol=1e-6)
+    assert np.allclose(c4[..., 3], nodes.coarse_w, rtol=1e-5)
+    vals = nodes.values(fz)
+    q = I.ball_queries(64, 0.9, 3)
+    gD = cvo.quad_D(q).cpu().numpy()
+    rD = np.array([C.quad_D(nodes, vals, x.astype(np.float64), near=2.0) for x in q])
+    assert np.abs(gD - rD).max() < 5e-5, np.abs(gD - rD).max()
+    p, prim = I.boundary_points(v, f, 64, 4)
+    fx = fz(p.astype(np.float64)).astype(np.float32)
+    for phi in (1, -1):
+        gH = cvo.quad_H(p, prim, fx, phi=phi).cpu().numpy()
+        rH = np.array([C.quad_H(nodes, vals, p[j].astype(np.float64), prim[j], float(fx[j]), phi,
+                                near=2.0) for j in range(64)])
+        assert np.abs(gH - rH).max() < 5e-5, np.abs(gH - rH).max()
+
+
+def _cv_run(wob, cvo, prob, params, q, walks, M, seed):
+    Q = len(q)
+    s = torch.zeros(Q, dtype=torch.float64, device="cuda")
+    ss = torch.zeros_like(s)
+    pw = torch.empty((Q, walks), dtype=torch.float64, device="cuda")
+    dnt = torch.empty(Q, dtype=torch.float32, device="cuda")
+    cvo.set_network(params)
+    cvo.solve_range(prob, params, q, 0, walks, M, s, ss, seed=seed, per_walk=pw, dnt=dnt)
+    return pw.cpu().numpy(), dnt.cpu().numpy(), s.cpu().numpy()
+
+
+def test_cv_zero_network_is_plain_wob(wob, sphere_cv):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    q = I.ball_queries(32, 0.85, 6)
+    zero = np.zeros(wob.mlp_num_params(), np.float32)
+    pw, dnt, s = _cv_run(wob, cvo, prob, zero, q, 48, 5, 7)
+    plain = wob.solve_debug(prob, q, 48, 5, seed=7, want_lines=False)["per_walk"].cpu().numpy()
+    assert np.all(dnt == 0.0)
+    assert np.allclose(pw, plain, rtol=0, atol=1e-12 * np.abs(plain).max())
+    assert np.allclose(s, pw.sum(1), rtol=1e-12)
+
+
+def test_cv_constant_network_reproduces_plain_walks(wob, sphere_cv):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    q = I.ball_queries(32, 0.85, 8)
+    c = 0.7
+    const = np.zeros(wob.mlp_num_params(), np.float32)
+    const[-1] = c
+    pw, dnt, _ = _cv_run(wob, cvo, prob, const, q, 48, 4, 9)
+    plain = wob.solve_debug(prob, q, 48, 4, seed=9, want_lines=False)["per_walk"].cpu().numpy()
+    assert np.allclose(dnt, c, atol=5e-5 * c)
+    assert np.allclose(pw + dnt[:, None], plain, rtol=0, atol=1e-4 * c)
+
+
+def test_cv_random_network_vs_oracle(wob, sphere_cv):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1, tau=O.TAU)
+    flat, params = _params32(5)
+    q = I.ball_queries(6, 0.8, 10)
+    M, N = 3, 16
+    pw, dnt, _ = _cv_run(wob, cvo, prob, flat, q, N, M, 11)
+    vals = nodes.values(lambda p: C.mlp_forward(params, p)[0])
+    S, flag, Dnt = C.cv_walks(v, f, q, N, M, params, nodes, vals, I.POLY_CONFIG1, seed=11,
+                             near=2.0)
+    scale = np.abs(np.concatenate(vals[0:1], axis=None)).max()
+    ok = ~flag
+    assert ok.mean() > 0.8
+    assert np.abs(dnt - Dnt).max() <= 3e-2 * scale
+    assert np.all(np.abs(pw - S)[ok] <= 3e-2 * M * scale), np.abs(pw - S)[ok].max() / scale
