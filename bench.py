@@ -304,6 +304,181 @@ def run_batched(args):
     }
 
 
+def run_cv(args):
+    """Learned control variate vs plain WoB: time to RMSE 1e-3 against the
+    exact solution on the icosphere-L3 mesh (1,280 triangles) with
+    g = x^2 - y^2 + 0.5 z evaluated at the hits (the polyhedral problem's
+    exact solution is then the polynomial itself), 65,536 queries uniform in
+    the ball of radius 0.9 (seed 1).
+
+    CV: the network is initialised on the device (seed 2) and trained by
+    wob_cv_train on 1M area-uniform boundary points (seed 3) with targets
+    from 64 density walks of length 4; then residual walks of length
+    --cv-len are added in batches of --cv-batch walks until the RMSE of
+    D nu_t + mean(residual walks) is <= 1e-3 (measured, CUDA events; the
+    RMSE check after each batch is inside the timed region).  Training
+    time is reported separately.
+
+    Plain WoB, M in {4, 5, 6, 8}: reaching 1e-3 takes 10^6-10^7 walks per
+    query (minutes to an hour), so the time is projected from measured
+    quantities: walks per second and mean per-walk variance sigma^2 on all
+    queries (512 walks), and the squared truncation bias b^2 estimated on
+    the first 256 queries with --bias-walks walks (mean squared error minus
+    the noise term).  RMSE(N)^2 = b^2 + sigma^2 / N gives the walks needed.
+    The best M is then run directly for --plain-cap seconds and its RMSE
+    compared with the projection."""
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    from paper_2305_04403_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    target = 1e-3
+    v, f = I.icosphere(3)
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    prob = wob.Problem(bvh, kind=wob.DIRICHLET_DL, side=1, data_mode=wob.DATA_POLY,
+                       poly=I.POLY_CONFIG1, problem=0)
+    Q = 65536
+    qh = I.ball_queries(Q, 0.9, 1)
+    q = torch.from_numpy(qh).cuda()
+    exact = torch.from_numpy(I.poly_eval(I.POLY_CONFIG1, qh.astype(np.float64))).cuda()
+    stream = torch.cuda.current_stream()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def rmse(est):
+        return float(torch.sqrt(torch.mean((est - exact) ** 2)).item())
+
+    def lap(start):
+        e = ev()
+        e.synchronize()
+        return start.elapsed_time(e) / 1e3
+
+    cvo = wob.ControlVariate(mesh, level=2, near=2.0)
+    launches = 0
+    # warm-up at the timed sizes: kernels loaded, memory pools grown
+    for _ in range(args.warmup):
+        p = wob.mlp_init(2)
+        m, vv = torch.zeros_like(p), torch.zeros_like(p)
+        cvo.train(prob, p, m, vv, points=1 << 20, walks=64, max_len=4, epochs=1)
+        s_ = torch.zeros(Q, dtype=torch.float64, device="cuda")
+        d_ = torch.empty(Q, dtype=torch.float32, device="cuda")
+        cvo.solve_range(prob, p, q, 0, args.cv_batch, args.cv_len, s_, torch.zeros_like(s_),
+                        dnt=d_)
+        rmse(d_.double() + s_ / args.cv_batch)
+        wob.solve_range(prob, q, 0, 512, 4, s_, torch.zeros_like(s_))
+        rmse(s_ / 512)
+        lap(ev())
+    torch.cuda.synchronize()
+
+    with Clocks(0) as clk:
+        # ---- CV: train, then progressive residual walks
+        p = wob.mlp_init(2)
+        m, vv = torch.zeros_like(p), torch.zeros_like(p)
+        steps_per_epoch = -(-(1 << 20) // 4096)
+        t0 = ev()
+        loss = cvo.train(prob, p, m, vv, points=1 << 20, walks=64, max_len=4, point_seed=3,
+                         walk_seed=0, epochs=args.cv_epochs, batch=4096, lr=1e-3,
+                         lr_end=1e-4, tail_epochs=args.cv_tail)
+        t1 = ev()
+        torch.cuda.synchronize()
+        train_s = t0.elapsed_time(t1) / 1e3
+        launches += 6 + args.cv_epochs * steps_per_epoch * 3 + 2
+        s_ = torch.zeros(Q, dtype=torch.float64, device="cuda")
+        ss = torch.zeros_like(s_)
+        dnt = torch.empty(Q, dtype=torch.float32, device="cuda")
+        curve, n_cv = [], 0
+        t0 = ev()
+        while True:
+            cvo.solve_range(prob, p, q, n_cv, args.cv_batch, args.cv_len, s_, ss, seed=SEED,
+                            dnt=dnt if n_cv == 0 else None)
+            launches += 2 + 3 * args.cv_len + (1 if n_cv == 0 else 0)
+            n_cv += args.cv_batch
+            e = rmse(dnt.double() + s_ / n_cv)
+            curve.append([lap(t0), n_cv, e])
+            if e <= target or n_cv >= args.cv_max_walks:
+                break
+        cv_s = curve[-1][0]
+        cv_var = float(((ss - s_ * s_ / n_cv) / (n_cv - 1)).mean().item())
+
+        # ---- plain WoB: rate and variance on all queries, bias on a subset
+        plain = {}
+        nb = 256
+        for M in (4, 5, 6, 8):
+            s_.zero_()
+            ss.zero_()
+            a = ev()
+            wob.solve_range(prob, q, 0, 512, M, s_, ss, seed=SEED)
+            b = ev()
+            torch.cuda.synchronize()
+            t_walk = a.elapsed_time(b) / 1e3 / 512          # seconds per walk of every query
+            var = float(((ss - s_ * s_ / 512) / 511).mean().item())
+            sb = torch.zeros(nb, dtype=torch.float64, device="cuda")
+            sbb = torch.zeros_like(sb)
+            chunk = 1 << 18
+            for k in range(args.bias_walks // chunk):
+                wob.solve_range(prob, q[:nb], k * chunk, chunk, M, sb, sbb, seed=SEED + 1)
+            nbw = (args.bias_walks // chunk) * chunk
+            mse = float(torch.mean((sb / nbw - exact[:nb]) ** 2).item())
+            vb = float(((sbb - sb * sb / nbw) / (nbw - 1)).mean().item())
+            bias2 = mse - vb / nbw
+            launches += 2 + 2 * (args.bias_walks // chunk)
+            need = var / (target ** 2 - bias2) if bias2 < target ** 2 else None
+            plain[str(M)] = {"seconds_per_walk": t_walk, "per_walk_var": var,
+                             "bias_rms": float(np.sqrt(max(bias2, 0.0))),
+                             "bias2_estimate": bias2, "bias_walks": nbw,
+                             "walks_needed": need,
+                             "time_to_rmse_s": need * t_walk if need else None}
+        ok = {k: r for k, r in plain.items() if r["time_to_rmse_s"]}
+        best = min(ok, key=lambda k: ok[k]["time_to_rmse_s"])
+        # direct run of the best M for a bounded time: RMSE vs the model
+        Mb = int(best)
+        s_.zero_()
+        ss.zero_()
+        n_pl, chunk = 0, 2048
+        t0 = ev()
+        while True:
+            wob.solve_range(prob, q, n_pl, chunk, Mb, s_, ss, seed=SEED + 2)
+            n_pl += chunk
+            launches += 2
+            el = lap(t0)
+            if el >= args.plain_cap:
+                break
+        e_pl = rmse(s_ / n_pl)
+        pred = float(np.sqrt(max(plain[best]["bias2_estimate"], 0.0)
+                             + plain[best]["per_walk_var"] / n_pl))
+        torch.cuda.synchronize()
+
+    best_t = plain[best]["time_to_rmse_s"]
+    return {
+        "metric": "time-to-RMSE 1e-3, learned control variate vs plain WoB",
+        "value": cv_s, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * cv_s, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 network / f32 quadrature / f64 accumulation",
+        "data": "synthetic (icosphere, seeded ball queries)",
+        "config": {"workload": "icosphere L3 (1,280 tris), g = x^2 - y^2 + 0.5 z at the hits, "
+                               "Q = 65,536 in the r <= 0.9 ball; CV trained on 1M boundary "
+                               "densities (64 walks, M = 4)",
+                   "cv_len": args.cv_len, "cv_batch": args.cv_batch,
+                   "cv_epochs": args.cv_epochs, "cv_lr": f"1e-3, last {args.cv_tail} epochs 1e-4",
+                   "quadrature": "Radon 7-point, level-2 near "
+                   "field within 2 edge lengths"},
+        "cv": {"train_s": train_s, "solve_s": cv_s, "walks": n_cv, "rmse": curve[-1][2],
+               "per_walk_var": cv_var, "final_train_loss": float(loss[-1].mean().item()),
+               "curve": curve},
+        "plain": plain,
+        "best_plain": {"M": Mb, "time_to_rmse_s": best_t, "projected": True,
+                       "direct_check": {"walks": n_pl, "seconds": el, "rmse": e_pl,
+                                        "model_rmse": pred}},
+        "speedup_solve": best_t / cv_s, "speedup_incl_training": best_t / (cv_s + train_s),
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+
+
 def cpu_baseline(v, f, q, nq: int) -> dict:
     """The oracle as it stands, on the host cores, on a bounded sample."""
     import oracle as O
@@ -360,13 +535,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
-    ap.add_argument("--workload", default="star", choices=["star", "batched"])
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "cv"])
+    ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
+    ap.add_argument("--cv-batch", type=int, default=64)
+    ap.add_argument("--cv-epochs", type=int, default=23)
+    ap.add_argument("--cv-tail", type=int, default=3, help="final epochs at lr 1e-4")
+    ap.add_argument("--cv-max-walks", type=int, default=1 << 16)
+    ap.add_argument("--bias-walks", type=int, default=1 << 22)
+    ap.add_argument("--plain-cap", type=float, default=20.0)
     ap.add_argument("--problems", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         line = run_reference(args)
     elif args.workload == "batched":
         line = run_batched(args)
+    elif args.workload == "cv":
+        line = run_cv(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -289,6 +289,11 @@ void wob_batch_destroy(wob_batch b);
  * tensor-core arithmetic with FP32 accumulation.
  */
 int wob_mlp_num_params(void); /* 18753 */
+/* He-uniform initial parameters (device, n_params floats): weight i (flat
+ * index) of a layer with fan-in f is sqrt(6 / f) (2 u - 1), u = (x >> 8) 2^-24
+ * for x the first word of the Philox4x32-10 block with counter (i, 0,
+ * 3 << 12, 0) and key (seed, seed >> 32); biases 0. */
+int wob_mlp_init(float *params, uint64_t seed, void *stream);
 /* out[i] = network(x[i]), x device n x 3, out device n. */
 int wob_mlp_forward(const float *params, const float *x, int64_t n, float *out, void *stream);
 /* One step on the mean squared error of (network(x), target) over the n
@@ -327,6 +332,48 @@ int wob_cv_solve(const wob_problem *prob, wob_cv c, const float *params, const f
                  int64_t Q, int64_t walk_begin, int32_t walks, int32_t max_len, uint64_t seed,
                  double *sum, double *sumsq, double *per_walk, float *dnt, void *stream);
 void wob_cv_destroy(wob_cv c);
+
+/*
+ * Area-uniform points on the mesh (device outputs: points n x 3 float,
+ * prims n original triangle ids).  Point i is the area sample of the
+ * counter-based stream (query i, walk 0, step 0) under key (seed ^ problem,
+ * seed >> 32): triangle by inverse CDF of the areas, then the square-root
+ * warp b = (1 - sqrt(u1), sqrt(u1)(1 - u2), sqrt(u1) u2) -- the draw the
+ * single-layer walks make (Sec. 4.3 with uniform area sampling).  0 <= n < 2^31.
+ */
+int wob_sample_boundary(wob_mesh m, int64_t n, uint64_t seed, uint32_t problem, float *points,
+                        int32_t *prims, void *stream);
+
+/*
+ * Train the control variate's network nu_t on density estimates, then set
+ * c's node values from it.  Training set: `points` area-uniform boundary
+ * points (wob_sample_boundary with point_seed and prob->problem); target at
+ * each = mean of `walks` density walks of length max_len (wob_solve_density
+ * with walk_seed).  Then `epochs` passes of Adam (lr) over minibatches of
+ * `batch` consecutive points (the points are independent draws, so fixed
+ * order is a valid stochastic gradient) at rate lr, the last tail_epochs of
+ * them at lr_end; the Adam step counter starts at step0 + 1.  params / adam_m / adam_v (device, n_params floats each) are
+ * updated in place; loss_out (device, optional) receives the minibatch MSE
+ * of every step, epochs x ceil(points / batch) floats.  The library
+ * allocates points x 36 bytes of scratch on `stream` and frees it before
+ * returning.  prob: WOB_DIRICHLET_DL on c's mesh.
+ */
+typedef struct {
+    int64_t points;      /* training points (1 .. 2^31 - 1) */
+    int32_t walks;       /* density walks per point (>= 2) */
+    int32_t max_len;     /* their path length M */
+    uint64_t point_seed; /* seed of the training points */
+    uint64_t walk_seed;  /* seed of the density walks */
+    int32_t epochs;      /* >= 0 */
+    int32_t batch;       /* minibatch size, 1 .. 2^22 */
+    float lr;            /* Adam learning rate, >= 0 */
+    float lr_end;        /* rate of the last tail_epochs epochs, >= 0 */
+    int32_t tail_epochs; /* 0: lr throughout */
+    int32_t step0;       /* Adam steps already taken with adam_m / adam_v */
+} wob_cv_train_params;
+
+int wob_cv_train(const wob_problem *prob, wob_cv c, const wob_cv_train_params *tp,
+                 float *params, float *adam_m, float *adam_v, float *loss_out, void *stream);
 
 /*
  * wob_solve for callers that cannot allocate device memory.  The paper has no

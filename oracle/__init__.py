@@ -78,6 +78,8 @@ def _load():
             lib.oracle_uniforms.argtypes = [U64, U32, P, I64, P, P]
             lib.oracle_mesh_stats.argtypes = [P, I64, P, I64, P]
             lib.oracle_mesh_stats.restype = ctypes.c_int
+            lib.oracle_area_points.argtypes = [P, I64, P, I64, I64, U64, U32, P, P]
+            lib.oracle_area_points.restype = ctypes.c_int
             lib.oracle_trace_lines.argtypes = [P, I64, P, I64, P, P, P, P, I64, U64, U32, D, D,
                                                P, P, P, P, P, P, P, ctypes.c_int]
             lib.oracle_trace_lines.restype = ctypes.c_int
@@ -153,6 +155,20 @@ def mesh_stats(verts, tris) -> dict:
     if rc != 0:
         raise RuntimeError("oracle_mesh_stats failed")
     return dict(L=out[0], area=out[1], volume=out[2], min_area=out[3], max_edge=out[4])
+
+
+def area_points(verts, tris, n: int, seed: int = 0, problem: int = 0):
+    """n area-uniform boundary points (float64 positions, triangle ids):
+    point i is the area sample of the stream (i, 0, 0)."""
+    v = _c(verts, np.float32)
+    t = _c(tris, np.int32)
+    pts = np.empty((n, 3), np.float64)
+    prims = np.empty(n, np.int32)
+    rc = _load().oracle_area_points(_p(v), v.shape[0], _p(t), t.shape[0], n, ctypes.c_uint64(seed),
+                                    ctypes.c_uint32(problem), _p(pts), _p(prims))
+    if rc != 0:
+        raise RuntimeError("oracle_area_points failed")
+    return pts, prims
 
 
 def trace_lines(verts, tris, origins, dirs, exclude=None, keys=None, seed: int = 0,

@@ -63,6 +63,28 @@ def mlp_init(seed: int = 2) -> list:
     return params
 
 
+def mlp_init_counter(seed: int = 2) -> np.ndarray:
+    """He-uniform parameters (flat, float32) from the counter-based stream:
+    weight i (flat index) of a layer with fan-in f is sqrt(6/f) (2u - 1),
+    u = (x >> 8) 2^-24 for x the first word of Philox4x32-10 at counter
+    (i, 0, 3 << 12, 0), key (seed_lo, seed_hi); biases 0."""
+    n = N_PARAMS
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 2] = 3 << 12
+    key = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32), (n, 1))
+    x = O.philox4x32_10(ctr, key)[:, 0]
+    u = (x >> 8).astype(np.float64) * 2.0 ** -24
+    flat = np.zeros(n, np.float32)
+    o = 0
+    for fan_in, fan_out in LAYERS:
+        lim = np.float32(math.sqrt(6.0 / fan_in))
+        sl = slice(o, o + fan_in * fan_out)
+        flat[sl] = lim * (np.float32(2.0) * u[sl].astype(np.float32) - np.float32(1.0))
+        o += fan_in * fan_out + fan_out
+    return flat
+
+
 def flatten(params) -> np.ndarray:
     return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params])
 

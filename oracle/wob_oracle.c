@@ -585,6 +585,24 @@ int oracle_mesh_stats(const float *verts, int64_t V, const int32_t *tris, int64_
     return 0;
 }
 
+/* n area-uniform boundary points: point i is the area sample of the stream
+ * (query i, walk 0, step 0), as drawn at the vertices of the single-layer
+ * walks (Sec. 4.3 with uniform area sampling). */
+int oracle_area_points(const float *verts, int64_t V, const int32_t *tris, int64_t T, int64_t n,
+                       uint64_t seed, uint32_t problem, double *points, int32_t *prims)
+{
+    mesh_t M;
+    if (mesh_init(&M, verts, V, tris, T, 1)) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t j;
+        double b[3];
+        area_sample(&M, seed, problem, (uint32_t)i, 0u, 0u, &j, points + 3 * i, b);
+        prims[i] = (int32_t)j;
+    }
+    mesh_free(&M);
+    return 0;
+}
+
 /* Trace n explicit lines (origin o, axis d).  keys: n x 3 (query, walk,
  * step) address the hit-selection keys.  hits_prim / hits_s (n x max_hits,
  * optional) list every hit. */

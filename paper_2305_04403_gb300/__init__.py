@@ -80,6 +80,14 @@ class _DebugOut(ctypes.Structure):
                 ("line_m", ctypes.c_void_p)]
 
 
+class _CvTrainParams(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_int64), ("walks", ctypes.c_int32),
+                ("max_len", ctypes.c_int32), ("point_seed", ctypes.c_uint64),
+                ("walk_seed", ctypes.c_uint64), ("epochs", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("lr_end", ctypes.c_float),
+                ("tail_epochs", ctypes.c_int32), ("step0", ctypes.c_int32)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("lines", ctypes.c_int64), ("node_visits", ctypes.c_int64),
                 ("tri_tests", ctypes.c_int64), ("hits", ctypes.c_int64),
@@ -132,6 +140,7 @@ def load_library() -> ctypes.CDLL:
             "wob_solve_density": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
                                   ctypes.c_int),
             "wob_mlp_num_params": ([], ctypes.c_int),
+            "wob_mlp_init": ([P, U64, P], ctypes.c_int),
             "wob_mlp_forward": ([P, P, I64, P, P], ctypes.c_int),
             "wob_mlp_train_step": ([P, P, P, P, P, I64, F, I32, P, P, P], ctypes.c_int),
             "wob_cv_create": ([P, I32, F, P, ctypes.POINTER(P)], ctypes.c_int),
@@ -145,6 +154,9 @@ def load_library() -> ctypes.CDLL:
             "wob_cv_solve": ([ctypes.POINTER(_Problem), P, P, P, I64, I64, I32, I32, U64, P, P, P,
                               P, P], ctypes.c_int),
             "wob_cv_destroy": ([P], None),
+            "wob_sample_boundary": ([P, I64, U64, U32, P, P, P], ctypes.c_int),
+            "wob_cv_train": ([ctypes.POINTER(_Problem), P, ctypes.POINTER(_CvTrainParams), P, P, P,
+                              P, P], ctypes.c_int),
             "wob_batch_create": ([P, I32, P, P, P, P, P, P, ctypes.POINTER(_BatchParams), P,
                                   ctypes.POINTER(P)], ctypes.c_int),
             "wob_batch_run": ([P, U64, P], ctypes.c_int),
@@ -395,8 +407,26 @@ def solve_density(problem: Problem, points, prims, walks: int, max_len: int, see
     return est, var
 
 
+def sample_boundary(mesh: Mesh, n: int, seed: int = 0, problem: int = 0, stream=None):
+    """wob_sample_boundary: (points (n, 3) float32, prims (n,) int32) on the device."""
+    import torch
+    pts = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    prims = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(load_library().wob_sample_boundary(mesh.handle, n, seed, problem, _ptr(pts),
+                                              _ptr(prims), _stream(stream)))
+    return pts, prims
+
+
 def mlp_num_params() -> int:
     return load_library().wob_mlp_num_params()
+
+
+def mlp_init(seed: int = 2, stream=None):
+    """wob_mlp_init: He-uniform parameters (CUDA float32, n_params)."""
+    import torch
+    p = torch.empty(mlp_num_params(), dtype=torch.float32, device="cuda")
+    _check(load_library().wob_mlp_init(_ptr(p), seed, _stream(stream)))
+    return p
 
 
 def mlp_forward(params, x, stream=None):
@@ -481,6 +511,25 @@ class ControlVariate:
                                            q.shape[0], walk_begin, walks, max_len, seed,
                                            _ptr(sum_), _ptr(sumsq), _ptr(per_walk), _ptr(dnt),
                                            _stream(stream)))
+
+    def train(self, problem: Problem, params, adam_m, adam_v, points: int = 1 << 20,
+              walks: int = 64, max_len: int = 4, point_seed: int = 3, walk_seed: int = 0,
+              epochs: int = 1, batch: int = 4096, lr: float = 1e-3, lr_end: float = 1e-4,
+              tail_epochs: int = 0, step0: int = 0, want_loss: bool = True, stream=None):
+        """wob_cv_train: params / adam_m / adam_v (CUDA float32) updated in
+        place; returns the per-step minibatch losses (epochs x steps)."""
+        import torch
+        steps = -(-points // min(batch, points))
+        loss = (torch.empty((epochs, steps), dtype=torch.float32, device="cuda")
+                if want_loss else None)
+        tp = _CvTrainParams(points, walks, max_len, point_seed, walk_seed, epochs, batch, lr, lr_end,
+                            tail_epochs, step0)
+        pc = problem._c()
+        _check(load_library().wob_cv_train(ctypes.byref(pc), self._h, ctypes.byref(tp),
+                                           _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(loss),
+                                           _stream(stream)))
+        self._params = params
+        return loss
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -18,6 +18,7 @@
 // far-field loop over triangles is the same for every lane of a warp, so its
 // node loads are broadcasts).
 #include <array>
+#include <climits>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -42,11 +43,10 @@ struct CvGeom {
     int T;
     int F;                       // fine nodes per triangle
     const float4* tri_c;         // centroid, near radius (near x longest edge)
-    const float4* tri_n;         // unit normal, circumradius about the centroid
-    const float4* coarse;        // T x 7: position, weight
-    const float4* fine;          // T x F
-    const float* coarse_val;     // network values at the nodes
-    const float* fine_val;
+    const float4* tri_p;         // unit normal n, plane offset n . y of the triangle
+    const float* tri_a;          // area
+    const float4* coarse_pk;     // T x 7: position, weight x node value
+    const float4* fine_pk;       // T x F
     const int* cand_off;         // per triangle: candidate near triangles
     const int* cand;
 };
@@ -100,7 +100,8 @@ void rule_tables(int level, std::vector<float>& cb, std::vector<float>& cw,
 
 __global__ void k_cv_nodes(const float* __restrict__ verts, const int32_t* __restrict__ tris,
                            int T, int F, float near, float4* __restrict__ tri_c,
-                           float4* __restrict__ tri_n, float4* __restrict__ coarse,
+                           float4* __restrict__ tri_p, float* __restrict__ tri_R,
+                           float* __restrict__ tri_a, float4* __restrict__ coarse,
                            float4* __restrict__ fine)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
@@ -118,6 +119,7 @@ __global__ void k_cv_nodes(const float* __restrict__ verts, const int32_t* __res
                              e1[0] * e2[1] - e1[1] * e2[0]};
         const double nl = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
         const double area = 0.5 * nl;
+        const double n[3] = {N[0] / nl, N[1] / nl, N[2] / nl};
         auto len = [](const double* e) { return sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]); };
         const double h = fmax(len(e1), fmax(len(e2), len(e3)));
         double R = 0.0;
@@ -126,7 +128,10 @@ __global__ void k_cv_nodes(const float* __restrict__ verts, const int32_t* __res
             R = fmax(R, len(d));
         }
         tri_c[j] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(near * h));
-        tri_n[j] = make_float4((float)(N[0] / nl), (float)(N[1] / nl), (float)(N[2] / nl), (float)R);
+        tri_p[j] = make_float4((float)n[0], (float)n[1], (float)n[2],
+                               (float)(n[0] * cen[0] + n[1] * cen[1] + n[2] * cen[2]));
+        tri_R[j] = (float)R;
+        tri_a[j] = (float)area;
         for (int q = 0; q < kCoarse; ++q) {
             double p[3];
             for (int c = 0; c < 3; ++c)
@@ -146,15 +151,26 @@ __global__ void k_cv_nodes(const float* __restrict__ verts, const int32_t* __res
     }
 }
 
+// Packed nodes for the sums: position and weight x value.
+__global__ void k_cv_pack(const float4* __restrict__ nodes, const float* __restrict__ val,
+                          int64_t n, float4* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = nodes[i];
+        out[i] = make_float4(a.x, a.y, a.z, a.w * val[i]);
+    }
+}
+
 // Candidates of triangle p: every j != p that can be near some point of p:
 // |c_j - c_p| < near_j + R_p.  Pass 0 counts, pass 1 fills.
 __global__ void k_cv_candidates(int T, const float4* __restrict__ tri_c,
-                                const float4* __restrict__ tri_n, const int* __restrict__ off,
+                                const float* __restrict__ tri_R, const int* __restrict__ off,
                                 int* __restrict__ count, int* __restrict__ cand, int pass)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
         const float4 cp = tri_c[p];
-        const float Rp = tri_n[p].w;
+        const float Rp = tri_R[p];
         int n = 0;
         for (int j = 0; j < T; ++j) {
             if (j == p) continue;
@@ -170,95 +186,139 @@ __global__ void k_cv_candidates(int T, const float4* __restrict__ tri_c,
     }
 }
 
-__device__ __forceinline__ float node_term(float4 nd, float v, float3 n, float3 x)
-{
-    const float rx = nd.x - x.x, ry = nd.y - x.y, rz = nd.z - x.z;
-    const float r2 = rx * rx + ry * ry + rz * rz;
-    const float rinv = rsqrtf(r2);
-    return nd.w * (rx * n.x + ry * n.y + rz * n.z) * (rinv * rinv * rinv) * kInvFourPi * v;
-}
-
 __device__ __forceinline__ bool is_near(float4 tc, float3 x)
 {
     const float dx = tc.x - x.x, dy = tc.y - x.y, dz = tc.z - x.z;
     return dx * dx + dy * dy + dz * dz < tc.w * tc.w;
 }
 
-// sum over quadrature nodes of w (r . n)/(4 pi r^3) (f(y) - fx), r = y - x,
-// i.e. -int dG/dn_y (f - fx) dA, skipping triangle `own` (-1: none).
-// Near triangles (fine nodes): per lane from the candidate list of `own`
-// when own >= 0, otherwise decided per triangle for the whole warp.
-__device__ float quad_sum(const CvGeom& c, float3 x, int own, float fx)
+// One node: t = 1/r^3, r = |y - x|; s1 += (w f) t, s0 += omega t (omega: the
+// rule weight without the triangle's area).
+__device__ __forceinline__ void node_acc(float4 nd, float omega, float3 x, float& s1, float& s0)
 {
-    float tot = 0.f;
-    for (int j = 0; j < c.T; ++j) {
-        const float4 tc = __ldg(c.tri_c + j);
-        const float4 tn4 = __ldg(c.tri_n + j);
-        const float3 n = make_float3(tn4.x, tn4.y, tn4.z);
-        const bool near_me = is_near(tc, x);
-        const bool skip = (j == own) || near_me;
-        float part = 0.f;
-#pragma unroll
-        for (int q = 0; q < kCoarse; ++q)
-            part += node_term(__ldg(c.coarse + kCoarse * j + q),
-                              __ldg(c.coarse_val + kCoarse * j + q) - fx, n, x);
-        tot += skip ? 0.f : part;
-        if (own < 0 && __any_sync(0xFFFFFFFFu, near_me)) {
-            float fpart = 0.f;
-            for (int q = 0; q < c.F; ++q)
-                fpart += node_term(__ldg(c.fine + (int64_t)c.F * j + q),
-                                   __ldg(c.fine_val + (int64_t)c.F * j + q) - fx, n, x);
-            tot += near_me ? fpart : 0.f;
-        }
-    }
-    if (own >= 0) {
-        for (int ci = own == 0 ? 0 : c.cand_off[own - 1]; ci < c.cand_off[own]; ++ci) {
-            const int j = c.cand[ci];
-            const float4 tc = __ldg(c.tri_c + j);
-            if (!is_near(tc, x)) continue;
-            const float4 tn4 = __ldg(c.tri_n + j);
-            const float3 n = make_float3(tn4.x, tn4.y, tn4.z);
-            for (int q = 0; q < c.F; ++q)
-                tot += node_term(__ldg(c.fine + (int64_t)c.F * j + q),
-                                 __ldg(c.fine_val + (int64_t)c.F * j + q) - fx, n, x);
-        }
-    }
-    return tot;
+    const float rx = nd.x - x.x, ry = nd.y - x.y, rz = nd.z - x.z;
+    const float ri = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+    const float t = ri * ri * ri;
+    s1 = fmaf(nd.w, t, s1);
+    s0 = fmaf(omega, t, s0);
 }
 
-// (D f)(x0) at points off the surface.  Every lane of a warp runs the
-// triangle loop (the near-field branch is warp-uniform).
-__global__ void k_cv_quad_D(CvGeom c, const float* __restrict__ x, int64_t n, float* out)
+// On the flat triangle j every node has the same r . n_j = d_j - x . n_j, so
+//   sum_q w_q (r . n)/r^3 (f_q - fx) = (d_j - x . n_j) (S1 - fx area_j S0),
+// S1 = sum_q (w_q f_q) / r_q^3, S0 = sum_q omega_q / r_q^3 (w_q = area_j omega_q).
+__device__ __forceinline__ float tri_term(float4 tp, float area, float3 x, float fx, float s1,
+                                          float s0)
 {
-    const int64_t warps_total = ((int64_t)gridDim.x * blockDim.x + 31) / 32;
-    const int64_t rounds = (n + 31) / 32;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int64_t r = gw; r < rounds; r += warps_total) {
-        const int64_t i = r * 32 + (threadIdx.x & 31);
+    const float dot = tp.w - fmaf(x.x, tp.x, fmaf(x.y, tp.y, x.z * tp.z));
+    return dot * fmaf(-fx * area, s0, s1);
+}
+
+// Far-field tile: kTileTris triangles (centroid + near radius, plane, area)
+// and their packed coarse nodes, staged in shared memory by the whole block.
+constexpr int kQuadThreads = 256;
+constexpr int kTileTris = 64;
+struct FarTile {
+    float4 tc[kTileTris];
+    float4 tp[kTileTris];
+    float ta[kTileTris];
+    float4 node[kTileTris * kCoarse];
+};
+
+// Fine-node sum of triangle j (its 4^level sub-triangles).
+__device__ __forceinline__ float fine_tri(const CvGeom& c, int j, float3 x, float fx)
+{
+    float s1 = 0.f, s0 = 0.f;
+    const float4* nd = c.fine_pk + (int64_t)c.F * j;
+    for (int q = 0; q < c.F; ++q) node_acc(__ldg(nd + q), c_fine_w[q], x, s1, s0);
+    return tri_term(__ldg(c.tri_p + j), __ldg(c.tri_a + j), x, fx, s1, s0);
+}
+
+// sum over quadrature nodes of w (r . n)/(4 pi r^3) (f(y) - fx), r = y - x,
+// i.e. -int dG/dn_y (f - fx) dA, skipping triangle `own` (-1: none).
+// Called by EVERY thread of the block (the triangle tiles are loaded
+// cooperatively); `own` must be negative for all lanes of a warp or for
+// none.  The far field (coarse nodes of every triangle not near x) is an
+// N-body sum over shared-memory tiles, FP32 within a tile and FP64 across
+// tiles.  Near triangles (fine nodes): per lane from the candidate list of
+// `own` when own >= 0; otherwise decided per triangle for the whole warp.
+__device__ __forceinline__ float quad_sum(const CvGeom& c, FarTile& sm, float3 x, int own,
+                                          float fx)
+{
+    double tot = 0.0;
+    for (int j0 = 0; j0 < c.T; j0 += kTileTris) {
+        const int nt = min(kTileTris, c.T - j0);
+        __syncthreads();  // the previous tile is no longer read
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            sm.tc[i] = __ldg(c.tri_c + j0 + i);
+            sm.tp[i] = __ldg(c.tri_p + j0 + i);
+            sm.ta[i] = __ldg(c.tri_a + j0 + i);
+        }
+        for (int i = threadIdx.x; i < nt * kCoarse; i += blockDim.x)
+            sm.node[i] = __ldg(c.coarse_pk + (int64_t)kCoarse * j0 + i);
+        __syncthreads();
+        float part = 0.f;
+        for (int jj = 0; jj < nt; ++jj) {
+            const int j = j0 + jj;
+            const bool near_me = is_near(sm.tc[jj], x);
+            float s1 = 0.f, s0 = 0.f;
+#pragma unroll
+            for (int q = 0; q < kCoarse; ++q)
+                node_acc(sm.node[kCoarse * jj + q], c_coarse_w[q], x, s1, s0);
+            const float term = tri_term(sm.tp[jj], sm.ta[jj], x, fx, s1, s0);
+            part += (j == own || near_me) ? 0.f : term;
+            if (own < 0 && __any_sync(0xFFFFFFFFu, near_me)) {
+                const float fterm = fine_tri(c, j, x, fx);
+                part += near_me ? fterm : 0.f;
+            }
+        }
+        tot += (double)part;
+    }
+    if (own >= 0) {
+        float near_tot = 0.f;
+        for (int ci = own == 0 ? 0 : c.cand_off[own - 1]; ci < c.cand_off[own]; ++ci) {
+            const int j = c.cand[ci];
+            if (is_near(__ldg(c.tri_c + j), x)) near_tot += fine_tri(c, j, x, fx);
+        }
+        tot += (double)near_tot;
+    }
+    return (float)(tot * (double)kInvFourPi);
+}
+
+// (D f)(x0) at points off the surface: -quad_sum(f) with f(x) = 0.
+__global__ void __launch_bounds__(kQuadThreads, 4) k_cv_quad_D(CvGeom c, const float* __restrict__ x,
+                                                           int64_t n, float* out)
+{
+    __shared__ FarTile sm;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
         const float3 p = ok ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2])
                             : make_float3(0.f, 0.f, 0.f);
-        const float v = quad_sum(c, p, -1, 0.f);
+        const float v = quad_sum(c, sm, p, -1, 0.f);
         if (ok) out[i] = v;
     }
 }
 
 // (H f)(x) at points on triangles prims (original ids): 2 phi int dG/dn_y f
 // = -2 phi quad_sum(f - f(x)) - phi f(x).
-__global__ void k_cv_quad_H(CvGeom c, int phi, const float* __restrict__ x,
-                            const int32_t* __restrict__ prims, const float* __restrict__ fx,
-                            int64_t n, float* out)
+__global__ void __launch_bounds__(kQuadThreads) k_cv_quad_H(CvGeom c, int phi,
+                                                           const float* __restrict__ x,
+                                                           const int32_t* __restrict__ prims,
+                                                           const float* __restrict__ fx,
+                                                           int64_t n, float* out)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int own = prims[i];
-        if (own < 0 || own >= c.T) {  // not a triangle of this mesh
-            out[i] = __int_as_float(0x7FC00000);
-            continue;
-        }
-        const float3 p = make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]);
-        const float s = quad_sum(c, p, own, fx[i]);
-        out[i] = -2.f * (float)phi * s - (float)phi * fx[i];
+    __shared__ FarTile sm;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int own = i < n ? prims[i] : -1;
+        const bool ok = i < n && own >= 0 && own < c.T;  // else: not a triangle of this mesh
+        const float3 p = ok ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2])
+                            : make_float3(0.f, 0.f, 0.f);
+        const float f0 = ok ? fx[i] : 0.f;
+        const float s = quad_sum(c, sm, p, ok ? own : 0, f0);
+        if (i < n) out[i] = ok ? -2.f * (float)phi * s - (float)phi * f0 : __int_as_float(0x7FC00000);
     }
 }
 
@@ -271,7 +331,13 @@ struct CvWalk {
     int* alive;   // 0 once a line missed
     float* vpos;  // 3 x W (contiguous per walk: x, y, z) for the network
     float* nut;   // network value at the current vertex
+    int* own;     // triangle of the current vertex (original id; T once dead)
+    int* perm;    // walks bucketed by `own` (the order k_cvw_accum visits them)
+    int* count;   // T + 1 bucket sizes
+    int* incl;    // their inclusive prefix sums
+    int* cursor;  // scatter cursors
     int64_t W;
+    int T;
 };
 
 __global__ void k_cvw_init(WalkParams p, CvWalk st)
@@ -286,6 +352,10 @@ __global__ void k_cvw_init(WalkParams p, CvWalk st)
         st.P[i] = 1.0;
         st.self[i] = -1;
         st.alive[i] = 1;
+        st.own[i] = st.T;
+        st.vpos[3 * i] = p.queries[3 * qi];
+        st.vpos[3 * i + 1] = p.queries[3 * qi + 1];
+        st.vpos[3 * i + 2] = p.queries[3 * qi + 2];
     }
 }
 
@@ -320,6 +390,7 @@ __global__ void __launch_bounds__(128, 8) k_cvw_trace(WalkParams p, CvWalk st, i
         }
         if (t.m == 0) {
             st.alive[i] = 0;
+            st.own[i] = st.T;
             continue;
         }
         const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
@@ -333,29 +404,115 @@ __global__ void __launch_bounds__(128, 8) k_cvw_trace(WalkParams p, CvWalk st, i
         st.vpos[3 * i + 1] = (float)r.y.y;
         st.vpos[3 * i + 2] = (float)r.y.z;
         st.self[i] = pos;
+        st.own[i] = (int)prim_of(p.tv, pos);
     }
     if (err) atomicOr(p.error_word, err);
 }
 
+// Bucket the walks by the triangle their vertex lies on (a counting sort;
+// dead walks go to bucket T, last).  Walks of one bucket share the near-field
+// candidate list, so a warp of them reads the same fine nodes.
+__global__ void k_cvw_count(CvWalk st)
+{
+    // warp-uniform loop: every lane takes part in the match
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31;
+         base < st.W; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + (threadIdx.x & 31);
+        const int b = i < st.W ? st.own[i] : -1;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+        if (b >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicAdd(st.count + b, __popc(peers));
+    }
+}
+
+__global__ void k_cvw_cursor(CvWalk st)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= st.T; b += gridDim.x * blockDim.x)
+        st.cursor[b] = st.incl[b] - st.count[b];
+}
+
+__global__ void k_cvw_scatter(CvWalk st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.W;
+         i += (int64_t)gridDim.x * blockDim.x)
+        st.perm[atomicAdd(st.cursor + st.own[i], 1)] = (int)i;
+}
+
 // Source r = 2 phi g - nu_t + H nu_t at the vertex reached at step k,
 // halved on the last vertex (Sec. 4.1.2), times the weight product.
-__global__ void k_cvw_accum(WalkParams p, CvWalk st, CvGeom c, int k)
+__global__ void __launch_bounds__(kQuadThreads) k_cvw_accum(WalkParams p, CvWalk st, CvGeom c,
+                                                           int k)
 {
+    __shared__ FarTile sm;
     const double phi = (double)p.phi;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.W;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (!st.alive[i]) continue;
-        const int pos = st.self[i];
-        const float3 v = make_float3(st.vpos[3 * i], st.vpos[3 * i + 1], st.vpos[3 * i + 2]);
-        const float fx = st.nut[i];
-        const int own = (int)prim_of(p.tv, pos);
-        const float h = -2.f * (float)p.phi * quad_sum(c, v, own, fx) - (float)p.phi * fx;
+    const int64_t n_alive = st.T > 0 ? st.incl[st.T - 1] : 0;  // buckets 0..T-1
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_alive;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = base + threadIdx.x < n_alive;
+        const int64_t i = ok ? st.perm[base + threadIdx.x] : 0;
+        const int pos = ok ? st.self[i] : 0;
+        const float3 v = ok ? make_float3(st.vpos[3 * i], st.vpos[3 * i + 1], st.vpos[3 * i + 2])
+                            : make_float3(0.f, 0.f, 0.f);
+        const float fx = ok ? st.nut[i] : 0.f;
+        const int own = ok ? (int)prim_of(p.tv, pos) : 0;
+        const float h = -2.f * (float)p.phi * quad_sum(c, sm, v, own, fx) - (float)p.phi * fx;
+        if (!ok) continue;
         const double3 y = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
         const double g = (double)dl_data(p.data, p.tv, pos, y);
         const double r = 2.0 * phi * g - (double)fx + (double)h;
         const double cw = (k == p.M - 1) ? 0.5 : 1.0;
         st.S[i] = fma(st.P[i] * cw, r, st.S[i]);
     }
+}
+
+// Area-uniform boundary points: point i is the area sample of the stream
+// (query i, walk 0, step 0) -- triangle by inverse CDF of the areas, then a
+// square-root-warped uniform point on it -- the same draw the single-layer
+// walks make at their vertices.
+__global__ void k_sample_boundary(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                                  const double* __restrict__ cdf, int64_t T, double area,
+                                  uint32_t key0, uint32_t key1, int64_t n, float* __restrict__ pts,
+                                  int32_t* __restrict__ prims)
+{
+    const StreamKey key{key0, key1};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const u32x4 u = stream_block(key, (uint32_t)i, 0u, 0u, kPurposeArea, 0u, 0u);
+        const double target = u53(u.x, u.y) * area;
+        int64_t lo = 0, hi = T - 1;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (__ldg(cdf + mid) > target) hi = mid; else lo = mid + 1;
+        }
+        const double su = sqrt(u24(u.z)), u2 = u24(u.w);
+        const double b0 = 1.0 - su, b1 = su * (1.0 - u2), b2 = su * u2;
+        const int32_t* t = tris + 3 * lo;
+        const float* v0 = verts + 3 * (int64_t)__ldg(t);
+        const float* v1 = verts + 3 * (int64_t)__ldg(t + 1);
+        const float* v2 = verts + 3 * (int64_t)__ldg(t + 2);
+        for (int c = 0; c < 3; ++c)
+            pts[3 * i + c] = (float)(b0 * __ldg(v0 + c) + b1 * __ldg(v1 + c) + b2 * __ldg(v2 + c));
+        prims[i] = (int32_t)lo;
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ in, int64_t n, float* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+int sample_boundary(const MeshDev& m, int64_t n, uint64_t seed, uint32_t problem, float* pts,
+                    int32_t* prims, cudaStream_t s)
+{
+    if (n <= 0) return WOB_OK;
+    const int grid = grid_for((const void*)k_sample_boundary, 128, 0, n);
+    k_sample_boundary<<<grid, 128, 0, s>>>(m.verts, m.tris, m.cdf, m.T, m.area,
+                                            (uint32_t)seed ^ problem, (uint32_t)(seed >> 32), n,
+                                            pts, prims);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
 }
 
 }  // namespace
@@ -367,13 +524,14 @@ struct wob_cv_s {
     const MeshDev* mesh = nullptr;
     int T = 0, F = 0, level = 2;
     float near = 2.f;
-    float4 *tri_c = nullptr, *tri_n = nullptr, *coarse = nullptr, *fine = nullptr;
-    float *coarse_val = nullptr, *fine_val = nullptr;
+    float4 *tri_c = nullptr, *tri_p = nullptr, *coarse = nullptr, *fine = nullptr;
+    float4 *coarse_pk = nullptr, *fine_pk = nullptr;
+    float *tri_R = nullptr, *tri_a = nullptr, *coarse_val = nullptr, *fine_val = nullptr;
     int *cand_off = nullptr, *cand = nullptr;
     int64_t n_cand = 0;
     CvGeom geom() const
     {
-        return CvGeom{T, F, tri_c, tri_n, coarse, fine, coarse_val, fine_val, cand_off, cand};
+        return CvGeom{T, F, tri_c, tri_p, tri_a, coarse_pk, fine_pk, cand_off, cand};
     }
 };
 
@@ -381,9 +539,22 @@ namespace {
 
 void free_cv(wob_cv_s* c)
 {
-    for (void* p : {(void*)c->tri_c, (void*)c->tri_n, (void*)c->coarse, (void*)c->fine,
+    for (void* p : {(void*)c->tri_c, (void*)c->tri_p, (void*)c->tri_R, (void*)c->tri_a,
+                    (void*)c->coarse, (void*)c->fine, (void*)c->coarse_pk, (void*)c->fine_pk,
                     (void*)c->coarse_val, (void*)c->fine_val, (void*)c->cand_off, (void*)c->cand})
         if (p) cudaFree(p);
+}
+
+// Packed nodes from the current node values.
+int pack_nodes(wob_cv_s* c, cudaStream_t s)
+{
+    const int64_t nc = (int64_t)c->T * kCoarse, nf = (int64_t)c->T * c->F;
+    k_cv_pack<<<grid_for((const void*)k_cv_pack, 256, 0, nc), 256, 0, s>>>(c->coarse, c->coarse_val,
+                                                                          nc, c->coarse_pk);
+    k_cv_pack<<<grid_for((const void*)k_cv_pack, 256, 0, nf), 256, 0, s>>>(c->fine, c->fine_val, nf,
+                                                                          c->fine_pk);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
 }
 
 }  // namespace
@@ -426,9 +597,13 @@ int wob_cv_create(wob_mesh m, int32_t level, float near, void* stream, wob_cv* o
         return fail(WOB_ERR_CUDA, "rule upload failed");
     const int T = c->T;
     if (cudaMalloc((void**)&c->tri_c, T * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc((void**)&c->tri_n, T * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->tri_p, T * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->tri_R, T * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->tri_a, T * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void**)&c->coarse, (size_t)T * kCoarse * sizeof(float4)) != cudaSuccess ||
         cudaMalloc((void**)&c->fine, (size_t)T * c->F * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->coarse_pk, (size_t)T * kCoarse * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->fine_pk, (size_t)T * c->F * sizeof(float4)) != cudaSuccess ||
         cudaMalloc((void**)&c->coarse_val, (size_t)T * kCoarse * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void**)&c->fine_val, (size_t)T * c->F * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void**)&c->cand_off, T * sizeof(int)) != cudaSuccess)
@@ -437,12 +612,13 @@ int wob_cv_create(wob_mesh m, int32_t level, float near, void* stream, wob_cv* o
     cudaMemsetAsync(c->fine_val, 0, (size_t)T * c->F * sizeof(float), s);
     const int threads = 128;
     const int grid = grid_for((const void*)k_cv_nodes, threads, 0, T);
-    k_cv_nodes<<<grid, threads, 0, s>>>(m->d.verts, m->d.tris, T, c->F, near, c->tri_c, c->tri_n,
-                                        c->coarse, c->fine);
+    k_cv_nodes<<<grid, threads, 0, s>>>(m->d.verts, m->d.tris, T, c->F, near, c->tri_c, c->tri_p,
+                                        c->tri_R, c->tri_a, c->coarse, c->fine);
+    if (pack_nodes(c, s) != WOB_OK) return fail(WOB_ERR_CUDA, "node setup failed");
     int* count = nullptr;
     if (cudaMallocAsync((void**)&count, T * sizeof(int), s) != cudaSuccess)
         return fail(WOB_ERR_OOM, "device allocation failed");
-    k_cv_candidates<<<grid, threads, 0, s>>>(T, c->tri_c, c->tri_n, nullptr, count, nullptr, 0);
+    k_cv_candidates<<<grid, threads, 0, s>>>(T, c->tri_c, c->tri_R, nullptr, count, nullptr, 0);
     int rc = inclusive_scan<int>(count, c->cand_off, T, s);
     int total = 0;
     cudaMemcpyAsync(&total, c->cand_off + T - 1, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -451,7 +627,7 @@ int wob_cv_create(wob_mesh m, int32_t level, float near, void* stream, wob_cv* o
     c->n_cand = total;
     if (cudaMalloc((void**)&c->cand, (size_t)(total > 0 ? total : 1) * sizeof(int)) != cudaSuccess)
         return fail(WOB_ERR_OOM, "device allocation failed");
-    k_cv_candidates<<<grid, threads, 0, s>>>(T, c->tri_c, c->tri_n, c->cand_off, nullptr, c->cand, 1);
+    k_cv_candidates<<<grid, threads, 0, s>>>(T, c->tri_c, c->tri_R, c->cand_off, nullptr, c->cand, 1);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return fail(WOB_ERR_CUDA, "candidate lists failed");
     *out = c;
@@ -468,7 +644,7 @@ int wob_cv_set_network(wob_cv c, const float* params, void* stream)
     cudaStream_t s = (cudaStream_t)stream;
     WOB_TRY(mlp_forward(params, (const float*)c->coarse, (int64_t)c->T * kCoarse, c->coarse_val, s, 4));
     WOB_TRY(mlp_forward(params, (const float*)c->fine, (int64_t)c->T * c->F, c->fine_val, s, 4));
-    return WOB_OK;
+    return pack_nodes(c, s);
 }
 
 int wob_cv_set_node_values(wob_cv c, const float* coarse, const float* fine, void* stream)
@@ -481,7 +657,7 @@ int wob_cv_set_node_values(wob_cv c, const float* coarse, const float* fine, voi
     cudaStream_t s = (cudaStream_t)stream;
     WOB_CUDA_TRY(cudaMemcpyAsync(c->coarse_val, coarse, (size_t)c->T * kCoarse * 4, cudaMemcpyDeviceToDevice, s));
     WOB_CUDA_TRY(cudaMemcpyAsync(c->fine_val, fine, (size_t)c->T * c->F * 4, cudaMemcpyDeviceToDevice, s));
-    return WOB_OK;
+    return pack_nodes(c, s);
 }
 
 int wob_cv_get_nodes(wob_cv c, float* coarse_out, float* fine_out, void* stream)
@@ -507,8 +683,8 @@ int wob_cv_quad_D(wob_cv c, const float* points, int64_t n, float* out, void* st
         return WOB_ERR_INVALID_ARG;
     }
     if (n == 0) return WOB_OK;
-    const int grid = grid_for((const void*)k_cv_quad_D, 128, 0, n);
-    k_cv_quad_D<<<grid, 128, 0, (cudaStream_t)stream>>>(c->geom(), points, n, out);
+    const int grid = grid_for((const void*)k_cv_quad_D, kQuadThreads, 0, n);
+    k_cv_quad_D<<<grid, kQuadThreads, 0, (cudaStream_t)stream>>>(c->geom(), points, n, out);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
@@ -522,8 +698,8 @@ int wob_cv_quad_H(wob_cv c, int32_t phi, const float* points, const int32_t* pri
         return WOB_ERR_INVALID_ARG;
     }
     if (n == 0) return WOB_OK;
-    const int grid = grid_for((const void*)k_cv_quad_H, 128, 0, n);
-    k_cv_quad_H<<<grid, 128, 0, (cudaStream_t)stream>>>(c->geom(), phi, points, prims, fx, n, out);
+    const int grid = grid_for((const void*)k_cv_quad_H, kQuadThreads, 0, n);
+    k_cv_quad_H<<<grid, kQuadThreads, 0, (cudaStream_t)stream>>>(c->geom(), phi, points, prims, fx, n, out);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
@@ -544,14 +720,20 @@ int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const f
         return WOB_ERR_UNSUPPORTED;
     }
     if (Q == 0) return WOB_OK;
+    if (Q * (int64_t)walks > INT32_MAX) {
+        set_error("wob_cv_solve: Q x walks must be below 2^31 per call");
+        return WOB_ERR_UNSUPPORTED;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     WalkParams p;
     fill_params(p, prob, queries, nullptr, Q, walk_begin, walks, max_len, seed);
     CvWalk st;
     st.W = Q * (int64_t)walks;
+    st.T = c->T;
     const size_t W = (size_t)st.W;
+    const size_t nb = (size_t)c->T + 1;
     char* buf = nullptr;
-    const size_t bytes = W * (8 * 5 + 4 * 2 + 4 * 4) + 256;
+    const size_t bytes = W * (8 * 5 + 4 * 2 + 4 * 4 + 4 * 2) + nb * 12 + 256;
     WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
     st.x = (double*)buf;
     st.S = st.x + 3 * W;
@@ -560,7 +742,12 @@ int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const f
     st.alive = st.self + W;
     st.vpos = (float*)(st.alive + W);
     st.nut = st.vpos + 3 * W;
-    int* err = (int*)(st.nut + W);
+    st.own = (int*)(st.nut + W);
+    st.perm = st.own + W;
+    st.count = st.perm + W;
+    st.incl = st.count + nb;
+    st.cursor = st.incl + nb;
+    int* err = st.cursor + nb;
     int rc = WOB_OK;
     cudaMemsetAsync(err, 0, sizeof(int), s);
     p.error_word = err;
@@ -568,11 +755,20 @@ int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const f
     const int threads = 128;
     k_cvw_init<<<grid_for((const void*)k_cvw_init, threads, 0, st.W), threads, 0, s>>>(p, st);
     const int g_trace = grid_for((const void*)k_cvw_trace, threads, 0, st.W);
-    const int g_acc = grid_for((const void*)k_cvw_accum, threads, 0, st.W);
+    const int g_acc = grid_for((const void*)k_cvw_accum, kQuadThreads, 0, st.W);
+    const int g_walk = grid_for((const void*)k_cvw_count, 256, 0, st.W);
+    const int g_buck = grid_for((const void*)k_cvw_cursor, 256, 0, (int64_t)nb);
     for (int k = 0; k < max_len && rc == WOB_OK; ++k) {
         k_cvw_trace<<<g_trace, threads, 0, s>>>(p, st, k);
         rc = mlp_forward(params, st.vpos, st.W, st.nut, s, 3);
-        if (rc == WOB_OK) k_cvw_accum<<<g_acc, threads, 0, s>>>(p, st, g, k);
+        if (rc != WOB_OK) break;
+        cudaMemsetAsync(st.count, 0, nb * sizeof(int), s);
+        k_cvw_count<<<g_walk, 256, 0, s>>>(st);
+        rc = inclusive_scan<int>(st.count, st.incl, (int64_t)nb, s);
+        if (rc != WOB_OK) break;
+        k_cvw_cursor<<<g_buck, 256, 0, s>>>(st);
+        k_cvw_scatter<<<g_walk, 256, 0, s>>>(st);
+        k_cvw_accum<<<g_acc, kQuadThreads, 0, s>>>(p, st, g, k);
     }
     if (rc == WOB_OK && cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
     if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s);
@@ -580,12 +776,79 @@ int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const f
         if (cudaMemcpyAsync(per_walk, st.S, W * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             rc = WOB_ERR_CUDA;
     if (rc == WOB_OK && dnt) {
-        const int grid = grid_for((const void*)k_cv_quad_D, 128, 0, Q);
-        k_cv_quad_D<<<grid, 128, 0, s>>>(g, queries, Q, dnt);
+        const int grid = grid_for((const void*)k_cv_quad_D, kQuadThreads, 0, Q);
+        k_cv_quad_D<<<grid, kQuadThreads, 0, s>>>(g, queries, Q, dnt);
         if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
     }
     cudaFreeAsync(buf, s);
     if (rc != WOB_OK) set_error("wob_cv_solve failed");
+    return rc;
+}
+
+int wob_sample_boundary(wob_mesh m, int64_t n, uint64_t seed, uint32_t problem, float* points,
+                        int32_t* prims, void* stream)
+{
+    clear_error();
+    if (!m || n < 0 || n > INT32_MAX || (n > 0 && (!points || !prims))) {
+        set_error("wob_sample_boundary: invalid arguments (0 <= n < 2^31)");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return sample_boundary(m->d, n, seed, problem, points, prims, (cudaStream_t)stream);
+}
+
+int wob_cv_train(const wob_problem* prob, wob_cv c, const wob_cv_train_params* tp,
+                 float* params, float* adam_m, float* adam_v, float* loss_out, void* stream)
+{
+    clear_error();
+    if (!c || !tp || !params || !adam_m || !adam_v || tp->points < 1 || tp->points > INT32_MAX ||
+        tp->walks < 2 || tp->max_len < 1 || tp->max_len > kMaxLen || tp->epochs < 0 ||
+        tp->batch < 1 || tp->batch > (1 << 22) || !(tp->lr >= 0.f) || !(tp->lr_end >= 0.f) ||
+        tp->tail_epochs < 0 || tp->step0 < 0) {
+        set_error("wob_cv_train: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    WOB_TRY(check_problem(prob));
+    if (prob->kind != WOB_DIRICHLET_DL || prob->bvh->d.mesh != c->mesh) {
+        set_error("wob_cv_train: needs WOB_DIRICHLET_DL on the control variate's mesh");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = tp->points;
+    const int64_t b = tp->batch < n ? tp->batch : n;
+    const int64_t steps = (n + b - 1) / b;
+    const int64_t ws_floats = mlp_train_workspace(b);
+    // one allocation: points (3n f32), prims (n i32), est / var (2n f64), targets (n f32), ws
+    const size_t bytes = (size_t)n * (12 + 4 + 16 + 4) + (size_t)ws_floats * 4 + 256;
+    char* buf = nullptr;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
+    double* est = (double*)buf;
+    double* var = est + n;
+    float* pts = (float*)(var + n);
+    float* targets = pts + 3 * n;
+    int32_t* prims = (int32_t*)(targets + n);
+    float* ws = (float*)(prims + n);
+    int rc = sample_boundary(*c->mesh, n, tp->point_seed, prob->problem, pts, prims, s);
+    if (rc == WOB_OK)
+        rc = wob_solve_density(prob, pts, prims, n, tp->walks, tp->max_len, tp->walk_seed, est, var,
+                               stream);
+    if (rc == WOB_OK) {
+        k_to_float<<<grid_for((const void*)k_to_float, 256, 0, n), 256, 0, s>>>(est, n, targets);
+        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+    }
+    int step = tp->step0;
+    for (int e = 0; e < tp->epochs && rc == WOB_OK; ++e) {
+        // step schedule: the last tail_epochs epochs run at lr_end
+        const float lr = e >= tp->epochs - tp->tail_epochs ? tp->lr_end : tp->lr;
+        for (int64_t j = 0; j < steps && rc == WOB_OK; ++j) {
+            const int64_t r0 = j * b, nb = (r0 + b <= n) ? b : n - r0;
+            const int64_t t = (int64_t)e * steps + j;
+            rc = mlp_train_step_ws(params, adam_m, adam_v, pts + 3 * r0, targets + r0, nb, lr,
+                                   ++step, nullptr, loss_out ? loss_out + t : nullptr, ws, s);
+        }
+    }
+    if (rc == WOB_OK) rc = wob_cv_set_network(c, params, stream);
+    cudaFreeAsync(buf, s);
+    if (rc != WOB_OK && wob_last_error()[0] == 0) set_error("wob_cv_train failed");
     return rc;
 }
 

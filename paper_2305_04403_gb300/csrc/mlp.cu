@@ -15,6 +15,7 @@
 
 #include <cuda_bf16.h>
 
+#include "wob_device.cuh"
 #include "wob_host.h"
 
 namespace wob {
@@ -443,6 +444,27 @@ __global__ void k_mlp_loss(const float* __restrict__ lp, int blocks, float n, fl
     if (threadIdx.x == 0) *out = s / n;
 }
 
+// He-uniform initial weights from the counter-based stream: parameter i
+// (flat index) of a weight matrix with fan-in f is sqrt(6 / f) (2 u - 1),
+// u = u24 of the first word of block (i, 0, 0 | init purpose, 0); biases 0.
+__global__ void k_mlp_init(float* __restrict__ params, uint32_t key0, uint32_t key1)
+{
+    const StreamKey key{key0, key1};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l < 4 && i >= w_off(l + 1)) ++l;
+        const int fan_in = l == 0 ? kFeat : kWidth;
+        const int wend = l < 4 ? b_off(l) : kB5;
+        if (i >= wend) {
+            params[i] = 0.f;
+            continue;
+        }
+        const u32x4 u = stream_block(key, (uint32_t)i, 0u, 0u, kPurposeInit, 0u, 0u);
+        const float lim = sqrtf(6.0f / (float)fan_in);
+        params[i] = lim * (2.0f * u24f(u.x) - 1.0f);
+    }
+}
+
 }  // namespace
 
 int mlp_forward(const float* params, const float* x, int64_t n, float* out, cudaStream_t s,
@@ -461,9 +483,15 @@ int mlp_forward(const float* params, const float* x, int64_t n, float* out, cuda
     return WOB_OK;
 }
 
-int mlp_train_step(float* params, float* m, float* v, const float* x, const float* target,
-                   int64_t n, float lr, int step, float* grad_out, float* loss_out,
-                   cudaStream_t s)
+int64_t mlp_train_workspace(int64_t n)
+{
+    const int64_t blocks = (n + kTrainRows - 1) / kTrainRows;
+    return blocks * (kParams + 1);
+}
+
+int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const float* target,
+                      int64_t n, float lr, int step, float* grad_out, float* loss_out, float* ws,
+                      cudaStream_t s)
 {
     if (n <= 0) return WOB_OK;
     static bool configured = false;
@@ -472,24 +500,30 @@ int mlp_train_step(float* params, float* m, float* v, const float* x, const floa
         configured = true;
     }
     const int blocks = (int)((n + kTrainRows - 1) / kTrainRows);
-    float* partial = nullptr;
-    float* lp = nullptr;
-    WOB_CUDA_TRY(cudaMallocAsync((void**)&partial, (size_t)blocks * kParams * sizeof(float), s));
-    WOB_CUDA_TRY(cudaMallocAsync((void**)&lp, blocks * sizeof(float), s));
+    float* partial = ws;
+    float* lp = ws + (int64_t)blocks * kParams;
     WOB_CUDA_TRY(cudaMemsetAsync(lp, 0, blocks * sizeof(float), s));
     k_mlp_train<<<blocks, 128, kTrainSmem, s>>>(params, x, target, n, partial, lp);
-    int rc = cudaGetLastError() == cudaSuccess ? WOB_OK : WOB_ERR_CUDA;
-    if (rc == WOB_OK) {
-        k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out,
-                                                         lr, 0.9f, 0.999f, 1e-8f, step);
-        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
-    }
-    if (rc == WOB_OK && loss_out) {
+    WOB_CUDA_TRY(cudaGetLastError());
+    k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out, lr,
+                                                     0.9f, 0.999f, 1e-8f, step);
+    WOB_CUDA_TRY(cudaGetLastError());
+    if (loss_out) {
         k_mlp_loss<<<1, 32, 0, s>>>(lp, blocks, (float)n, loss_out);
-        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+        WOB_CUDA_TRY(cudaGetLastError());
     }
-    cudaFreeAsync(partial, s);
-    cudaFreeAsync(lp, s);
+    return WOB_OK;
+}
+
+int mlp_train_step(float* params, float* m, float* v, const float* x, const float* target,
+                   int64_t n, float lr, int step, float* grad_out, float* loss_out,
+                   cudaStream_t s)
+{
+    if (n <= 0) return WOB_OK;
+    float* ws = nullptr;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&ws, (size_t)mlp_train_workspace(n) * sizeof(float), s));
+    const int rc = mlp_train_step_ws(params, m, v, x, target, n, lr, step, grad_out, loss_out, ws, s);
+    cudaFreeAsync(ws, s);
     if (rc != WOB_OK) set_error("MLP training step failed");
     return rc;
 }
@@ -499,6 +533,19 @@ int mlp_train_step(float* params, float* m, float* v, const float* x, const floa
 extern "C" {
 
 int wob_mlp_num_params(void) { return wob::kParams; }
+
+int wob_mlp_init(float* params, uint64_t seed, void* stream)
+{
+    wob::clear_error();
+    if (!params) {
+        wob::set_error("wob_mlp_init: NULL params");
+        return WOB_ERR_INVALID_ARG;
+    }
+    wob::k_mlp_init<<<(wob::kParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        params, (uint32_t)seed, (uint32_t)(seed >> 32));
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
 
 int wob_mlp_forward(const float* params, const float* x, int64_t n, float* out, void* stream)
 {

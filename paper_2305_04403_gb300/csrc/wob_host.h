@@ -73,5 +73,10 @@ int mlp_forward(const float* params, const float* x, int64_t n, float* out, cuda
 int mlp_train_step(float* params, float* m, float* v, const float* x, const float* target,
                    int64_t n, float lr, int step, float* grad_out, float* loss_out,
                    cudaStream_t s);
+// floats of workspace a training step on n samples needs
+int64_t mlp_train_workspace(int64_t n);
+int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const float* target,
+                      int64_t n, float lr, int step, float* grad_out, float* loss_out, float* ws,
+                      cudaStream_t s);
 
 }  // namespace wob

@@ -12,6 +12,7 @@ namespace wob {
 constexpr uint32_t kPurposeDir = 0;   // line axis draws
 constexpr uint32_t kPurposeHit = 1;   // hit-selection keys
 constexpr uint32_t kPurposeArea = 2;  // area-sampled boundary points
+constexpr uint32_t kPurposeInit = 3;  // initial network weights
 constexpr int kStackSize = 64;        // traversal stack entries per line
 constexpr int kNoRef = INT32_MIN;     // empty traversal stack marker
 constexpr int64_t kMaxTriangles = (int64_t(1) << 28) - 2;

@@ -53,6 +53,12 @@ def test_mlp_forward_matches_oracle(wob):
         assert np.allclose(g, got[:n], rtol=0, atol=1e-6)
 
 
+def test_mlp_init_matches_oracle(wob):
+    for seed in (2, (7 << 32) | 5):
+        got = wob.mlp_init(seed).cpu().numpy()
+        assert np.array_equal(got, C.mlp_init_counter(seed))
+
+
 def test_mlp_gradients_match_oracle(wob):
     flat, params = _params32()
     rng = np.random.default_rng(3)
@@ -198,3 +204,62 @@ def test_cv_random_network_vs_oracle(wob, sphere_cv):
     assert ok.mean() > 0.8
     assert np.abs(dnt - Dnt).max() <= 3e-2 * scale
     assert np.all(np.abs(pw - S)[ok] <= 3e-2 * M * scale), np.abs(pw - S)[ok].max() / scale
+
+
+def test_sample_boundary_matches_oracle(wob):
+    v, f, _ = I.star_mesh(3, 0.3, 6, 3, 0.5)
+    mesh = wob.build_mesh(v, f)
+    for n in (1, 1000, 4099):
+        p, pr = wob.sample_boundary(mesh, n, seed=3, problem=5)
+        rp, rpr = O.area_points(v, f, n, seed=3, problem=5)
+        assert np.array_equal(pr.cpu().numpy(), rpr)
+        assert np.abs(p.cpu().numpy() - rp).max() <= 2e-7 * np.abs(rp).max()
+
+
+def _sphere_density_ratio(l, M):
+    """Truncated density series on the unit sphere, mode l: 2 sum_{k<M-1}
+    lam^k + lam^(M-1), lam = -1/(2l+1) (the eigenvalue of H)."""
+    lam = -1.0 / (2 * l + 1)
+    return 2.0 * sum(lam ** k for k in range(M - 1)) + lam ** (M - 1)
+
+
+@pytest.fixture(scope="module")
+def trained(wob, sphere_cv):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    flat, _ = _params32()
+    p = torch.from_numpy(flat).cuda()
+    m, vv = torch.zeros_like(p), torch.zeros_like(p)
+    loss = cvo.train(prob, p, m, vv, points=1 << 20, walks=64, max_len=4, point_seed=3,
+                     walk_seed=0, epochs=5, batch=4096, lr=1e-3)
+    return prob, p, loss.cpu().numpy()
+
+
+def test_cv_training_fits_the_sphere_density(wob, sphere_cv, trained):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob, p, loss = trained
+    assert loss.shape == (5, 256)
+    assert loss[-1].mean() < 0.2 * loss[0, 0], (loss[0, 0], loss[-1].mean())
+    y, _ = O.area_points(v, f, 4000, seed=9)
+    nu = wob.mlp_forward(p, y.astype(np.float32)).cpu().numpy()
+    g1, g2 = 0.5 * y[:, 2], y[:, 0] ** 2 - y[:, 1] ** 2
+    pred = _sphere_density_ratio(1, 4) * g1 + _sphere_density_ratio(2, 4) * g2
+    rel = np.sqrt(np.mean((nu - pred) ** 2) / np.mean(pred ** 2))
+    # observed 0.039 (target noise, 5 epochs, and the polyhedron's own density)
+    assert rel < 0.06, rel
+
+
+def test_cv_estimate_is_unbiased_with_lower_variance(wob, sphere_cv, trained):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob, p, _ = trained
+    q = I.ball_queries(256, 0.9, 1)
+    N, M = 256, 4
+    pw, dnt, _ = _cv_run(wob, cvo, prob, p, q, N, M, 0)
+    est = dnt + pw.mean(1)
+    exact = I.poly_eval(I.POLY_CONFIG1, q.astype(np.float64))
+    se = pw.std(1, ddof=1) / np.sqrt(N)
+    # residual truncation bias is tiny: |r| is a few percent of 2g
+    assert np.all(np.abs(est - exact) <= 5 * se + 2e-3), np.abs(est - exact).max()
+    plain = wob.solve_debug(prob, q, N, M, seed=0, want_lines=False)["per_walk"].cpu().numpy()
+    ratio = pw.var(1, ddof=1).mean() / plain.var(1, ddof=1).mean()
+    assert ratio < 0.05, ratio

@@ -176,3 +176,57 @@ def test_density_walks_match_sphere_series(sphere_nodes, M):
     pred = ratio * p[:, 2].astype(float)
     se = np.sqrt(var / n)
     assert np.all(np.abs(est - pred) <= 5 * se + 5e-3 * abs(ratio)), (est, pred, se)
+
+
+def test_area_points_are_area_uniform():
+    """Training points: on their triangles, triangle frequencies proportional
+    to area (chi-square), barycentric coordinates uniform on the simplex
+    (each has mean 1/3 and P(b0 > 1/2) = 1/4)."""
+    v, f, _ = I.star_mesh(2, 0.3, 6, 3, 0.5)
+    n = 200000
+    p, pr = O.area_points(v, f, n, seed=3)
+    V = v.astype(np.float64)
+    a, b, c = V[f[pr, 0]], V[f[pr, 1]], V[f[pr, 2]]
+    N = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(N, axis=1)
+    assert np.abs(np.einsum("ij,ij->i", p - a, N / (2 * area[:, None]))).max() < 1e-12
+    # barycentrics by solving p = a + s (b - a) + t (c - a)
+    e1, e2, r = b - a, c - a, p - a
+    d11, d12, d22 = (e1 * e1).sum(1), (e1 * e2).sum(1), (e2 * e2).sum(1)
+    r1, r2 = (r * e1).sum(1), (r * e2).sum(1)
+    det = d11 * d22 - d12 * d12
+    s = (d22 * r1 - d12 * r2) / det
+    t = (d11 * r2 - d12 * r1) / det
+    bary = np.stack([1 - s - t, s, t], 1)
+    assert bary.min() > -1e-9
+    se = np.sqrt(1 / 18 / n)                      # sd of one coordinate: 1/sqrt(18)
+    assert np.all(np.abs(bary.mean(0) - 1 / 3) < 5 * se)
+    frac = (bary[:, 0] > 0.5).mean()
+    assert abs(frac - 0.25) < 5 * np.sqrt(0.25 * 0.75 / n)
+    T = len(f)
+    A = 0.5 * np.linalg.norm(np.cross(V[f[:, 1]] - V[f[:, 0]], V[f[:, 2]] - V[f[:, 0]]), axis=1)
+    cnt = np.bincount(pr, minlength=T)
+    expct = n * A / A.sum()
+    chi2 = ((cnt - expct) ** 2 / expct).sum()
+    assert abs(chi2 - (T - 1)) < 5 * np.sqrt(2 * (T - 1)), chi2
+
+
+def test_counter_init_is_he_uniform():
+    """Counter-based initial weights: each weight matrix uniform on
+    [-sqrt(6/fan_in), sqrt(6/fan_in)] (mean 0, variance lim^2/3, in range),
+    biases exactly 0; different seeds give different weights."""
+    flat = C.mlp_init_counter(2)
+    assert flat.dtype == np.float32 and flat.size == C.N_PARAMS
+    o = 0
+    for fan_in, fan_out in C.LAYERS:
+        W = flat[o:o + fan_in * fan_out].astype(np.float64)
+        b = flat[o + fan_in * fan_out:o + fan_in * fan_out + fan_out]
+        lim = math.sqrt(6.0 / fan_in)
+        assert np.all(np.abs(W) <= lim) and np.all(b == 0.0)
+        n = W.size
+        assert abs(W.mean()) < 5 * lim / math.sqrt(3 * n)
+        assert abs(W.var() / (lim * lim / 3.0) - 1.0) < 5 * math.sqrt(0.8 / n)
+        o += fan_in * fan_out + fan_out
+    assert o == C.N_PARAMS
+    other = C.mlp_init_counter(3)
+    assert np.mean(other == flat) < 0.1
