@@ -88,21 +88,52 @@ struct SmemNet {
     float b5;
 };
 
+// One layer's matrix (64 x IN, row-major FP32) into shared memory as BF16.
+// 128 threads; every thread issues all of its float4 loads before any
+// store, so the loads are in flight together.
+template <int IN>
+__device__ __forceinline__ void load_layer(const float* __restrict__ W, __nv_bfloat16* wt,
+                                           __nv_bfloat16* w, bool vec)
+{
+    constexpr int kLdIn = IN == kFeat ? kLd1 : kLd;
+    constexpr int kPer = 64 * IN / 4 / 128;  // float4 per thread
+    static_assert(64 * IN % (4 * 128) == 0, "layer size");
+    float4 r[kPer];
+    if (vec) {
+        const float4* W4 = reinterpret_cast<const float4*>(W);
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) r[u] = __ldg(W4 + threadIdx.x + 128 * u);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const float* p = W + 4 * (threadIdx.x + 128 * u);
+            r[u] = make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = 4 * (threadIdx.x + 128 * u);
+        const int o = i / IN, k = i - o * IN;  // 4 consecutive k of row o
+        const __nv_bfloat16 b[4] = {__float2bfloat16_rn(r[u].x), __float2bfloat16_rn(r[u].y),
+                                    __float2bfloat16_rn(r[u].z), __float2bfloat16_rn(r[u].w)};
+        __nv_bfloat16* d = wt + o * kLdIn + k;
+        *reinterpret_cast<uint2*>(d) =
+            make_uint2((uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16),
+                       (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16));
+        if (w)
+            for (int c = 0; c < 4; ++c) w[(k + c) * kLd + o] = b[c];
+    }
+}
+
+// The network into shared memory (launched with 128 threads).
 __device__ void load_net(const float* __restrict__ params, SmemNet& n, bool with_transposed)
 {
-    for (int l = 0; l < 4; ++l) {
-        const int in = l == 0 ? kFeat : kWidth;
-        const int ld_in = l == 0 ? kLd1 : kLd;
-        const bool tr = with_transposed && l > 0;
-        const float* W = params + w_off(l);
-        for (int i = threadIdx.x; i < 64 * in; i += blockDim.x) {
-            const int o = i / in, k = i - o * in;
-            const __nv_bfloat16 v = __float2bfloat16_rn(W[i]);
-            n.wt[l][o * ld_in + k] = v;
-            if (tr) n.w[l][k * kLd + o] = v;
-        }
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) n.bias[l * 64 + i] = params[b_off(l) + i];
-    }
+    const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
+    load_layer<kFeat>(params + w_off(0), n.wt[0], nullptr, vec);
+    for (int l = 1; l < 4; ++l)
+        load_layer<kWidth>(params + w_off(l), n.wt[l], with_transposed ? n.w[l] : nullptr, vec);
+    for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x)
+        n.bias[i] = params[b_off(i >> 6) + (i & 63)];
     for (int i = threadIdx.x; i < 64; i += blockDim.x) n.w5[i] = params[kW5 + i];
     n.b5 = params[kB5];
     __syncthreads();
@@ -424,6 +455,7 @@ __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m,
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
         float gsum = 0.f;
+#pragma unroll 8
         for (int b = 0; b < blocks; ++b) gsum += partial[(int64_t)b * kParams + i];
         if (grad_out) grad_out[i] = gsum;
         if (lr == 0.f) continue;
