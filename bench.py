@@ -42,6 +42,10 @@ X0 = (3.0, 0.0, 0.0)
 # data term and accumulation), and the bytes fetched per node and triangle.
 OPS_NODE, OPS_TRI, OPS_HIT, OPS_LINE = 34, 41, 100, 235
 BYTES_NODE, BYTES_TRI = 64, 48
+# DRAM bytes (read + write) of one full-size k_dl_walks launch of this
+# workload (29,497 queries, leaves of 2), from ncu dram__bytes_read.sum +
+# dram__bytes_write.sum (profiles/k_dl_walks_star6_full_traffic.md).
+TRAFFIC_FULL = (29497, 2, 41.42e6 + 227.45e6)
 
 
 def _peaks():
@@ -228,7 +232,8 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
                      "unit": "T lane-ops/s", "frac": achieved_ops / alu_peak,
-                     "traffic": None,
+                     "traffic": (TRAFFIC_FULL[2] if (Q, args.leaf) == TRAFFIC_FULL[:2]
+                                 else None),
                      "kernel": "k_dl_walks",
                      "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
                                     f"({which} sm_max_mhz)"},
@@ -339,7 +344,7 @@ def run_cv(args):
     bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
     prob = wob.Problem(bvh, kind=wob.DIRICHLET_DL, side=1, data_mode=wob.DATA_POLY,
                        poly=I.POLY_CONFIG1, problem=0)
-    Q = 65536
+    Q = args.cv_queries
     qh = I.ball_queries(Q, 0.9, 1)
     q = torch.from_numpy(qh).cuda()
     exact = torch.from_numpy(I.poly_eval(I.POLY_CONFIG1, qh.astype(np.float64))).cuda()
@@ -461,7 +466,7 @@ def run_cv(args):
         "vs_baseline": None, "dtype": "bf16 network / f32 quadrature / f64 accumulation",
         "data": "synthetic (icosphere, seeded ball queries)",
         "config": {"workload": "icosphere L3 (1,280 tris), g = x^2 - y^2 + 0.5 z at the hits, "
-                               "Q = 65,536 in the r <= 0.9 ball; CV trained on 1M boundary "
+                               f"Q = {Q} in the r <= 0.9 ball; CV trained on 1M boundary "
                                "densities (64 walks, M = 4)",
                    "cv_len": args.cv_len, "cv_batch": args.cv_batch,
                    "cv_epochs": args.cv_epochs, "cv_lr": f"1e-3, last {args.cv_tail} epochs 1e-4",
@@ -537,6 +542,8 @@ def main():
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
     ap.add_argument("--workload", default="star", choices=["star", "batched", "cv"])
     ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
+    ap.add_argument("--cv-queries", type=int, default=65536,
+                    help="queries of the cv workload (the metric is defined at 65,536)")
     ap.add_argument("--cv-batch", type=int, default=64)
     ap.add_argument("--cv-epochs", type=int, default=23)
     ap.add_argument("--cv-tail", type=int, default=3, help="final epochs at lr 1e-4")
