@@ -36,16 +36,18 @@ WALKS, MAX_LEN, SEED = 1024, 16, 0
 X0 = (3.0, 0.0, 0.0)
 
 # Algorithmic per-event costs: lane operations of the FP32/INT32 pipes counted
-# from the traversal source (per interior node: two 3-slab box tests; per
-# triangle: the sheared edge functions, flags and hit test; per hit: one
-# Philox block and the key comparison; per line: axis, setup, FP64 refinement,
-# data term and accumulation), and the bytes fetched per node and triangle.
-OPS_NODE, OPS_TRI, OPS_HIT, OPS_LINE = 34, 41, 100, 235
-BYTES_NODE, BYTES_TRI = 64, 48
+# from the traversal source (per 8-wide node: header decode and eight 3-slab
+# tests on dequantised child boxes; per triangle: the sheared edge functions,
+# flags and hit test; per hit: one Philox block and the key comparison; per
+# line: axis, setup, FP64 refinement, data term and accumulation), and the
+# bytes fetched per node and triangle.
+OPS_NODE, OPS_TRI, OPS_HIT, OPS_LINE = 320, 41, 100, 235
+BYTES_NODE, BYTES_TRI = 96, 48
 # DRAM bytes (read + write) of one full-size k_dl_walks launch of this
-# workload (29,497 queries, leaves of 2), from ncu dram__bytes_read.sum +
-# dram__bytes_write.sum (profiles/k_dl_walks_star6_full_traffic.md).
-TRAFFIC_FULL = (29497, 2, 41.42e6 + 227.45e6)
+# workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
+# dram__bytes_write.sum (profiles/k_dl_walks_star6_full_traffic.md); None
+# until taken for the current kernel.
+TRAFFIC_FULL = None
 
 
 def _peaks():
@@ -232,8 +234,8 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
                      "unit": "T lane-ops/s", "frac": achieved_ops / alu_peak,
-                     "traffic": (TRAFFIC_FULL[2] if (Q, args.leaf) == TRAFFIC_FULL[:2]
-                                 else None),
+                     "traffic": (TRAFFIC_FULL[2] if TRAFFIC_FULL and
+                                 (Q, args.leaf) == TRAFFIC_FULL[:2] else None),
                      "kernel": "k_dl_walks",
                      "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
                                     f"({which} sm_max_mhz)"},
@@ -535,7 +537,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--leaf", type=int, default=2)
+    ap.add_argument("--leaf", type=int, default=1)
     ap.add_argument("--cpu-queries", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,

@@ -75,16 +75,16 @@ typedef struct {
 } wob_mesh_info;
 
 typedef struct {
-    int32_t leaf_size; /* max triangles per leaf, 1..8 (0 = default 2) */
+    int32_t leaf_size; /* max triangles per leaf, 1..8 (0 = default 1) */
     int32_t reserved[7];
 } wob_bvh_params;
 
 typedef struct {
-    int64_t nodes;   /* reachable interior nodes */
-    int64_t leaves;  /* leaves */
-    int32_t depth;   /* maximum depth (root = 0) */
+    int64_t nodes;   /* 8-wide nodes */
+    int64_t leaves;  /* leaves (triangle groups of at most leaf_size) */
+    int32_t depth;   /* depth of the 8-wide tree (root = 0) */
     int32_t leaf_size;
-    int64_t bytes;   /* device bytes of nodes + leaf triangles */
+    int64_t bytes;   /* device bytes of the wide nodes + leaf triangles */
 } wob_bvh_info;
 
 /*
@@ -154,8 +154,12 @@ void wob_destroy_mesh(wob_mesh m);
  * Build the bounding-volume hierarchy used by the all-hits line queries of
  * ray sampling (Sec. 4.4.1): a linear BVH over Morton-ordered triangle
  * centroids (Karras 2012), bottom-up boxes, leaves of up to leaf_size
- * triangles.  The BVH keeps a reference to the mesh; destroy the BVH first.
- * Synchronises on `stream`.
+ * triangles, then collapsed top-down into 8-wide nodes (each node expands
+ * its largest-area interior child until it has 8 children; child boxes
+ * quantised to 8 bits, rounded outward).  Meshes whose binary tree has
+ * 2^24 or more interior nodes are rejected (WOB_ERR_UNSUPPORTED).  The BVH
+ * keeps a reference to the mesh; destroy the BVH first.  Synchronises on
+ * `stream`.
  */
 int wob_build_bvh(wob_mesh m, const wob_bvh_params *p, void *stream, wob_bvh *out);
 int wob_bvh_get_info(wob_bvh b, wob_bvh_info *out);

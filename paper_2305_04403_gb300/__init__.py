@@ -233,7 +233,7 @@ class Mesh:
 class BVH:
     """Bounding-volume hierarchy over a mesh (wob_build_bvh)."""
 
-    def __init__(self, mesh: Mesh, leaf_size: int = 2, stream=None):
+    def __init__(self, mesh: Mesh, leaf_size: int = 1, stream=None):
         lib = load_library()
         p = _BvhParams()
         p.leaf_size = leaf_size
@@ -263,7 +263,7 @@ def build_mesh(verts, tris, stream=None) -> Mesh:
     return Mesh(verts, tris, stream)
 
 
-def build_bvh(mesh: Mesh, leaf_size: int = 2, stream=None) -> BVH:
+def build_bvh(mesh: Mesh, leaf_size: int = 1, stream=None) -> BVH:
     return BVH(mesh, leaf_size, stream)
 
 

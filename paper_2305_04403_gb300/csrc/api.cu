@@ -97,11 +97,10 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     memset(&p, 0, sizeof(p));
     const BvhDev& b = prob->bvh->d;
     const MeshDev& m = *b.mesh;
-    p.nodes = b.nodes;
+    p.nodes = b.wnodes;
     p.tv = b.tv;
     p.inv_order = b.inv_order;
-    p.root = b.root;
-    p.iter_limit = (int)(4 * b.n_nodes_alloc + 64);
+    p.iter_limit = (int)(4 * b.n_wide + 64);
     p.verts = m.verts;
     p.tris = m.tris;
     p.tri_n = m.tri_n;
@@ -302,7 +301,7 @@ int wob_build_bvh(wob_mesh m, const wob_bvh_params* p, void* stream, wob_bvh* ou
         set_error("NULL argument");
         return WOB_ERR_INVALID_ARG;
     }
-    int leaf = p && p->leaf_size ? p->leaf_size : 2;
+    int leaf = p && p->leaf_size ? p->leaf_size : 1;
     if (leaf < 1 || leaf > 8) {
         set_error("leaf_size %d outside [1, 8]", leaf);
         return WOB_ERR_INVALID_ARG;
@@ -331,11 +330,11 @@ int wob_bvh_get_info(wob_bvh b, wob_bvh_info* out)
         set_error("NULL argument");
         return WOB_ERR_INVALID_ARG;
     }
-    out->nodes = b->d.nodes_reachable;
+    out->nodes = b->d.n_wide;
     out->leaves = b->d.leaves;
-    out->depth = b->d.depth;
+    out->depth = b->d.wide_levels - 1;
     out->leaf_size = b->d.leaf_size;
-    out->bytes = b->d.n_nodes_alloc * 64 + b->d.mesh->T * 48;
+    out->bytes = b->d.n_wide * 96 + b->d.mesh->T * 48;
     return WOB_OK;
 }
 

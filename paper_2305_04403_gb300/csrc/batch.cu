@@ -34,10 +34,9 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct BatchProblem {
-    const float4* nodes;
+    const float4* nodes;  // 8-wide nodes
     const float4* tv;
     DataDev data;
-    int root;
     int iter_limit;
     int phi;
     int M;
@@ -79,7 +78,7 @@ __global__ void __launch_bounds__(128, 8)
         if (t >= (unsigned long long)n_tiles) break;
         const Tile tile = tiles[t];
         const BatchProblem& P = probs[tile.problem];
-        const DLGeom G{P.nodes, P.tv, P.root, P.iter_limit, P.edge_thr_L, P.tauL, P.graze};
+        const DLGeom G{P.nodes, P.tv, P.iter_limit, P.edge_thr_L, P.tauL, P.graze};
         const StreamKey key{(uint32_t)seed ^ P.problem, (uint32_t)(seed >> 32)};
 #pragma unroll 1
         for (int r = 0; r < ROUNDS; ++r) {
@@ -387,7 +386,6 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
         bp.nodes = wp.nodes;
         bp.tv = wp.tv;
         bp.data = wp.data;
-        bp.root = wp.root;
         bp.iter_limit = wp.iter_limit;
         bp.phi = wp.phi;
         bp.M = max_len[p];

@@ -311,11 +311,185 @@ int dev_alloc(T** p, int64_t count, cudaStream_t s)
     return WOB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// 8-wide BVH, collapsed top-down from the binary tree: a wide node starts
+// from a binary interior node's two children and repeatedly replaces the
+// interior child of largest surface area by its two children, up to 8.
+// Layout (6 float4 = 96 bytes):
+//   f[0] = (origin x, y, z, bits: ex | ey << 8 | ez << 16 | nint << 24 | nchild << 28)
+//   f[1..3] = per axis: 8 quantised lows (bytes, slots 0..7) then 8 highs
+//   f[4..5] = refs[0..7]: refs[0] = first internal child (when nint > 0);
+//             leaf slots s >= nint hold binary leaf refs ~(first << 3 | count - 1)
+// Slots 0 .. nint-1 are interior children stored at first_child + slot;
+// child box = origin + q * 2^(e - 127) per axis, rounded outward.
+// ---------------------------------------------------------------------------
+struct WEntry {
+    int ref;
+    float lo[3], hi[3];
+};
+
+__device__ __forceinline__ float box_area(const WEntry& e)
+{
+    const float dx = e.hi[0] - e.lo[0], dy = e.hi[1] - e.lo[1], dz = e.hi[2] - e.lo[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// children of binary interior node i as two entries
+__device__ __forceinline__ void binary_children(const float4* __restrict__ nodes, int i, WEntry& a,
+                                                WEntry& b)
+{
+    const float4 n0 = nodes[4 * i + 0], n1 = nodes[4 * i + 1], n2 = nodes[4 * i + 2];
+    const int4 n3 = reinterpret_cast<const int4*>(nodes)[4 * i + 3];
+    a.ref = n3.x;
+    a.lo[0] = n0.x; a.hi[0] = n0.y; a.lo[1] = n0.z; a.hi[1] = n0.w; a.lo[2] = n2.x; a.hi[2] = n2.y;
+    b.ref = n3.y;
+    b.lo[0] = n1.x; b.hi[0] = n1.y; b.lo[1] = n1.z; b.hi[1] = n1.w; b.lo[2] = n2.z; b.hi[2] = n2.w;
+}
+
+__global__ void k_wide_collapse(const float4* __restrict__ nodes, int root_ref, float3 root_lo,
+                                float3 root_hi, int64_t w_begin, int64_t w_end,
+                                int32_t* __restrict__ src, float4* __restrict__ wn,
+                                int* __restrict__ counter)
+{
+    for (int64_t w = w_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < w_end;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        WEntry e[8];
+        int n;
+        const int s0 = w == 0 ? root_ref : src[w];
+        if (s0 >= 0) {
+            binary_children(nodes, s0, e[0], e[1]);
+            n = 2;
+        } else {  // the whole mesh is one leaf
+            e[0].ref = s0;
+            e[0].lo[0] = root_lo.x; e[0].lo[1] = root_lo.y; e[0].lo[2] = root_lo.z;
+            e[0].hi[0] = root_hi.x; e[0].hi[1] = root_hi.y; e[0].hi[2] = root_hi.z;
+            n = 1;
+        }
+        while (n < 8) {
+            int best = -1;
+            float ba = -1.f;
+            for (int j = 0; j < n; ++j)
+                if (e[j].ref >= 0 && box_area(e[j]) > ba) {
+                    ba = box_area(e[j]);
+                    best = j;
+                }
+            if (best < 0) break;
+            WEntry a, b;
+            binary_children(nodes, e[best].ref, a, b);
+            e[best] = a;
+            e[n++] = b;
+        }
+        // interior children first
+        WEntry o[8];
+        int nint = 0;
+        for (int j = 0; j < n; ++j)
+            if (e[j].ref >= 0) o[nint++] = e[j];
+        int k = nint;
+        for (int j = 0; j < n; ++j)
+            if (e[j].ref < 0) o[k++] = e[j];
+        const int first_child = nint > 0 ? atomicAdd(counter, nint) : 0;
+        for (int j = 0; j < nint; ++j) src[first_child + j] = o[j].ref;
+        // node box and quantisation (FP64, outward)
+        double lo[3], hi[3];
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = o[0].lo[c];
+            hi[c] = o[0].hi[c];
+            for (int j = 1; j < n; ++j) {
+                lo[c] = fmin(lo[c], (double)o[j].lo[c]);
+                hi[c] = fmax(hi[c], (double)o[j].hi[c]);
+            }
+        }
+        // origin rounded down; the scale covers [origin, hi] in 255 steps
+        float org[3];
+        for (int c = 0; c < 3; ++c) org[c] = __double2float_rd(lo[c]);
+        uint32_t ebits[3];
+        double scale[3];
+        for (int c = 0; c < 3; ++c) {
+            const double ext = hi[c] - (double)org[c];
+            int ex = -126;
+            if (ext > 0.0) {
+                int e2;
+                frexp(ext / 255.0, &e2);  // ext / 255 < 2^e2
+                ex = e2 < -126 ? -126 : e2;
+            }
+            ebits[c] = (uint32_t)(ex + 127);
+            scale[c] = ldexp(1.0, ex);
+        }
+        uint32_t q[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // [axis][lo0-3, lo4-7, hi0-3, hi4-7]
+        for (int j = 0; j < n; ++j)
+            for (int c = 0; c < 3; ++c) {
+                const double ql = floor(((double)o[j].lo[c] - org[c]) / scale[c]);
+                const double qh = ceil(((double)o[j].hi[c] - org[c]) / scale[c]);
+                const uint32_t bl = (uint32_t)fmin(fmax(ql, 0.0), 255.0);
+                const uint32_t bh = (uint32_t)fmin(fmax(qh, 0.0), 255.0);
+                q[c][j >> 2] |= bl << (8 * (j & 3));
+                q[c][2 + (j >> 2)] |= bh << (8 * (j & 3));
+            }
+        int refs[8];
+        for (int j = 0; j < 8; ++j) refs[j] = (j < n && j >= nint) ? o[j].ref : 0;
+        if (nint > 0) refs[0] = first_child;
+        float4* d = wn + 6 * w;
+        const uint32_t hdr = ebits[0] | (ebits[1] << 8) | (ebits[2] << 16) | ((uint32_t)nint << 24) |
+                             ((uint32_t)n << 28);
+        d[0] = make_float4(org[0], org[1], org[2], __uint_as_float(hdr));
+        for (int c = 0; c < 3; ++c)
+            d[1 + c] = make_float4(__uint_as_float(q[c][0]), __uint_as_float(q[c][1]),
+                                   __uint_as_float(q[c][2]), __uint_as_float(q[c][3]));
+        d[4] = make_float4(__int_as_float(refs[0]), __int_as_float(refs[1]),
+                           __int_as_float(refs[2]), __int_as_float(refs[3]));
+        d[5] = make_float4(__int_as_float(refs[4]), __int_as_float(refs[5]),
+                           __int_as_float(refs[6]), __int_as_float(refs[7]));
+    }
+}
+
 }  // namespace
+
+// Collapse the binary tree into 8-wide nodes (level by level from the root).
+int build_wide(BvhDev& b, const MeshDev& m, cudaStream_t s)
+{
+    const int64_t cap = b.n_nodes_alloc > 0 ? b.n_nodes_alloc : 1;
+    WOB_CUDA_TRY(cudaMalloc((void**)&b.wnodes, 6 * cap * sizeof(float4)));
+    int32_t* src = nullptr;
+    int* counter = nullptr;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&src, cap * sizeof(int32_t), s));
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&counter, sizeof(int), s));
+    const int one = 1;
+    WOB_CUDA_TRY(cudaMemcpyAsync(counter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    const float pad = (float)(4e-6 * m.L);
+    const float3 rlo = make_float3((float)m.lo[0] - pad, (float)m.lo[1] - pad, (float)m.lo[2] - pad);
+    const float3 rhi = make_float3((float)m.hi[0] + pad, (float)m.hi[1] + pad, (float)m.hi[2] + pad);
+    int64_t w_begin = 0, w_end = 1;
+    int levels = 0, rc = WOB_OK;
+    while (w_begin < w_end && levels < 1024) {
+        const int grid = grid_for((const void*)k_wide_collapse, 128, 0, w_end - w_begin);
+        k_wide_collapse<<<grid, 128, 0, s>>>(b.nodes, b.root, rlo, rhi, w_begin, w_end, src,
+                                             b.wnodes, counter);
+        int c = 0;
+        if (cudaMemcpyAsync(&c, counter, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = WOB_ERR_CUDA;
+            break;
+        }
+        w_begin = w_end;
+        w_end = c;
+        ++levels;
+    }
+    cudaFreeAsync(src, s);
+    cudaFreeAsync(counter, s);
+    if (rc != WOB_OK) {
+        set_error("wide BVH collapse failed");
+        return rc;
+    }
+    b.n_wide = w_end;
+    b.wide_levels = levels;
+    return WOB_OK;
+}
 
 void free_bvh(BvhDev& b)
 {
     cudaFree(b.nodes);
+    cudaFree(b.wnodes);
+    b.wnodes = nullptr;
     cudaFree(b.tv);
     cudaFree(b.order);
     cudaFree(b.inv_order);
@@ -437,6 +611,19 @@ int build_bvh_impl(MeshDev& m, int leaf_size, cudaStream_t s, BvhDev& b)
         free_bvh(b);
         return WOB_ERR_UNSUPPORTED;
     }
+    if (b.n_nodes_alloc >= (1 << 24)) {
+        set_error("BVH: %lld interior nodes exceed the wide traversal's 2^24", (long long)b.n_nodes_alloc);
+        free_bvh(b);
+        return WOB_ERR_UNSUPPORTED;
+    }
+    const int wrc = build_wide(b, m, s);
+    if (wrc != WOB_OK) {
+        free_bvh(b);
+        return wrc;
+    }
+    // the binary nodes were only the input of the collapse
+    cudaFree(b.nodes);
+    b.nodes = nullptr;
     return WOB_OK;
 }
 

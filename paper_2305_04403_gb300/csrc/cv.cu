@@ -361,7 +361,7 @@ __global__ void k_cvw_init(WalkParams p, CvWalk st)
 
 // Line of step k from the current vertex: traversal, pick, FP64 refine and
 // the weight (first step (m/2)s, later -phi m s).
-__global__ void __launch_bounds__(128, 8) k_cvw_trace(WalkParams p, CvWalk st, int k)
+__global__ void __launch_bounds__(128, 4) k_cvw_trace(WalkParams p, CvWalk st, int k)
 {
     const StreamKey key{p.key0, p.key1};
     int stack[kStackSize];
@@ -380,14 +380,11 @@ __global__ void __launch_bounds__(128, 8) k_cvw_trace(WalkParams p, CvWalk st, i
                                    make_float3((float)d.x, (float)d.y, (float)d.z));
         const float Tthr = p.edge_thr_L * fabsf(L.Sz);
         Trav t;
-        trav_init(t, p.root);
+        trav_init(t);
         uint32_t nn = 0, nt = 0;
-        while (t.ref != kNoRef) {
-            descend<false>(p.nodes, L, t, stack, nn, err, p.iter_limit);
-            if (t.ref == kNoRef) break;
-            test_leaf<false, false>(p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL, p.graze,
-                                    self, t, hits, stack, key, q, w, (uint32_t)k, nt);
-        }
+        trace_wide<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+                                 p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn, nt,
+                                 err, p.iter_limit);
         if (t.m == 0) {
             st.alive[i] = 0;
             st.own[i] = st.T;

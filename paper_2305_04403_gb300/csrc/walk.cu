@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
 {
     const StreamKey key{p.key0, p.key1};
     const int64_t total = p.Q * (int64_t)p.N;
-    const DLGeom G{p.nodes, p.tv, p.root, p.iter_limit, p.edge_thr_L, p.tauL, p.graze};
+    const DLGeom G{p.nodes, p.tv, p.iter_limit, p.edge_thr_L, p.tauL, p.graze};
     __shared__ double slots[8 * 128];
     const WalkSlot ws{slots + threadIdx.x, 128};
     int err = 0;
@@ -226,7 +226,7 @@ __global__ void k_reduce_accum(const double* __restrict__ per_walk, int64_t Q, i
 }
 
 __global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __restrict__ tv,
-                              const int32_t* __restrict__ inv_order, int root, int64_t n_tris,
+                              const int32_t* __restrict__ inv_order, int64_t n_tris,
                               int iter_limit, const double* __restrict__ o,
                               const double* __restrict__ d, const int32_t* __restrict__ exclude,
                               const uint32_t* __restrict__ keys, int64_t n, uint32_t key0,
@@ -244,7 +244,7 @@ __global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __
         const int self = (ex >= 0 && ex < n_tris) ? inv_order[ex] : -1;
         Trav t;
         const int pos = trace_line<true>(
-            nodes, tv, root, make_float3((float)x.x, (float)x.y, (float)x.z),
+            nodes, tv, make_float3((float)x.x, (float)x.y, (float)x.z),
             make_float3((float)dd.x, (float)dd.y, (float)dd.z), self, key, keys[3 * i],
             keys[3 * i + 1], keys[3 * i + 2], edge_thr_L, tauL, kGraze, t, err, iter_limit);
         m[i] = t.m;
@@ -357,7 +357,7 @@ int launch_trace_lines(const BvhDev& b, const double* o, const double* d, const 
 {
     const int threads = 128;
     k_trace_lines<<<grid_for((const void*)k_trace_lines, threads, 0, n), threads, 0, s>>>(
-        b.nodes, b.tv, b.inv_order, b.root, b.mesh->T, (int)(4 * b.n_nodes_alloc + 64), o, d,
+        b.wnodes, b.tv, b.inv_order, b.mesh->T, (int)(4 * b.n_wide + 64), o, d,
         exclude, keys, n, key0, key1, tauL,
         edge_thr_L, m, sum_s, prim, s_out, t, y, flag, error_word);
     WOB_CUDA_TRY(cudaGetLastError());

@@ -94,15 +94,15 @@ __device__ __forceinline__ double3 line_axis(StreamKey key, uint32_t q, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// BVH layout.  A node holds the boxes of both children (so one 64-byte fetch
-// decides which children the line meets) and two child references:
-//   ref >= 0 : interior node index
-//   ref <  0 : leaf, ~ref = first << 3 | (count - 1), triangles
-//              tv[3 * first .. 3 * (first + count) - 1] in leaf order.
-//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   n3 = (ref0, ref1, -, -) as int bits
+// BVH layout (built in bvh.cu): a binary LBVH collapsed into 8-wide nodes
+// of 6 float4 (96 bytes), root = node 0:
+//   f[0] = (origin x, y, z, bits: ex | ey << 8 | ez << 16 | nint << 24 | nchild << 28)
+//   f[1..3] = per axis: quantised child lows (8 bytes) then highs (8 bytes);
+//             child box = origin + q * 2^(e - 127), rounded outward
+//   f[4..5] = refs[0..7]: refs[0] = first interior child when nint > 0
+//             (interior children are slots 0 .. nint-1, stored at
+//             refs[0] + slot); leaf slots hold ~(first << 3 | (count - 1)),
+//             triangles tv[3 * first .. 3 * (first + count) - 1].
 // Triangle in leaf order: tv[3p] = (v0, original id bits), tv[3p+1] =
 // (v1, |(v1-v0) x (v2-v0)|), tv[3p+2] = (v2, 0).
 // ---------------------------------------------------------------------------
@@ -158,34 +158,25 @@ __device__ __forceinline__ bool line_box(const LinePre& L, float lox, float hix,
 }
 
 // ---------------------------------------------------------------------------
-// All-hits traversal of one line, in resumable pieces so that a persistent
-// kernel can interleave lines: descend() walks interior nodes until it holds
-// a leaf (or the line is done), test_leaf() tests that leaf's triangles and
-// pops the next reference.  Hits are recorded by leaf position; the
+// All-hits traversal of one line.  Hits are recorded by leaf position; the
 // selection keys are computed after the traversal (select_hit), and only when
 // there is more than one hit.
 // ---------------------------------------------------------------------------
 constexpr int kMaxHits = 8;
 
 struct Trav {
-    int ref;        // node (>= 0) or leaf (< 0) to visit next; kNoRef when done
-    int sp;         // stack depth
     int m;          // hits so far
     int flag;       // near-degenerate line
     int sum_s;      // sum of sign(omega . n) over hits (debug only)
-    int iters;      // interior nodes visited (bounded)
     uint64_t best;  // smallest key among hits, once m > kMaxHits
     int bpos;       // its leaf position
 };
 
-__device__ __forceinline__ void trav_init(Trav& t, int root)
+__device__ __forceinline__ void trav_init(Trav& t)
 {
-    t.ref = root;
-    t.sp = 0;
     t.m = 0;
     t.flag = 0;
     t.sum_s = 0;
-    t.iters = 0;
     t.best = ~0ull;
     t.bpos = -1;
 }
@@ -213,108 +204,163 @@ __device__ __forceinline__ void keep_min(uint64_t k, uint32_t prim, int pos, uin
     }
 }
 
-// Descend interior nodes until t.ref is a leaf or the traversal is finished.
-template <bool COUNT>
-__device__ __forceinline__ void descend(const float4* __restrict__ nodes, const LinePre& L,
-                                        Trav& t, int* stack, uint32_t& n_nodes, int& err,
-                                        int iter_limit)
+// Line-triangle test of leaf triangle p (Woop, Benthin, Wald, "Watertight
+// ray/triangle intersection", JCGT 2013, applied to a line: no parameter
+// range): record a hit, flag near-degenerate configurations.
+template <bool SUM_S>
+__device__ __forceinline__ void test_tri(const float4* __restrict__ tv, const LinePre& L, float3 d,
+                                         float Tthr, float tauL, float graze, int p, Trav& t,
+                                         int* hits, StreamKey key, uint32_t q, uint32_t walk,
+                                         uint32_t step)
 {
-    while (t.ref >= 0) {
-        if (++t.iters > iter_limit) {  // a tree visits each node at most once
-            err |= 2;
-            t.ref = kNoRef;
-            t.sp = 0;
-            return;
-        }
-        const float4 n0 = __ldg(nodes + 4 * t.ref + 0);
-        const float4 n1 = __ldg(nodes + 4 * t.ref + 1);
-        const float4 n2 = __ldg(nodes + 4 * t.ref + 2);
-        const int4 n3 = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * t.ref + 3);
-        if (COUNT) n_nodes++;
-        const bool h0 = line_box(L, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
-        const bool h1 = line_box(L, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
-        if (h0 && h1) {
-            if (t.sp < kStackSize) {
-                stack[t.sp++] = n3.y;
-            } else {
-                err |= 1;
-            }
-            t.ref = n3.x;
-        } else if (h0) {
-            t.ref = n3.x;
-        } else if (h1) {
-            t.ref = n3.y;
-        } else {
-            t.ref = t.sp > 0 ? stack[--t.sp] : kNoRef;
-        }
+    const float4 a4 = __ldg(tv + 3 * p + 0);
+    const float4 b4 = __ldg(tv + 3 * p + 1);
+    const float4 c4 = __ldg(tv + 3 * p + 2);
+    const float3 A = make_float3(a4.x - L.ox, a4.y - L.oy, a4.z - L.oz);
+    const float3 B = make_float3(b4.x - L.ox, b4.y - L.oy, b4.z - L.oz);
+    const float3 C = make_float3(c4.x - L.ox, c4.y - L.oy, c4.z - L.oz);
+    const float Akz = comp(A, L.kz), Bkz = comp(B, L.kz), Ckz = comp(C, L.kz);
+    const float Ax = fmaf(-L.Sx, Akz, comp(A, L.kx));
+    const float Ay = fmaf(-L.Sy, Akz, comp(A, L.ky));
+    const float Bx = fmaf(-L.Sx, Bkz, comp(B, L.kx));
+    const float By = fmaf(-L.Sy, Bkz, comp(B, L.ky));
+    const float Cx = fmaf(-L.Sx, Ckz, comp(C, L.kx));
+    const float Cy = fmaf(-L.Sy, Ckz, comp(C, L.ky));
+    const float U = Cx * By - Cy * Bx;
+    const float V = Ax * Cy - Ay * Cx;
+    const float W = Bx * Ay - By * Ax;
+    const bool pos_side = (U > -Tthr) && (V > -Tthr) && (W > -Tthr);
+    const bool neg_side = (U < Tthr) && (V < Tthr) && (W < Tthr);
+    if (!(pos_side || neg_side)) return;
+    const float det = U + V + W;
+    const float mn = fminf(fminf(fabsf(U), fabsf(V)), fabsf(W));
+    if (mn < Tthr || fabsf(det) < graze * b4.w * fabsf(L.Sz)) t.flag = 1;
+    const bool hit = (U > 0.f && V > 0.f && W > 0.f) || (U < 0.f && V < 0.f && W < 0.f);
+    if (!hit) return;
+    const float T = fmaf(U, L.Sz * Akz, fmaf(V, L.Sz * Bkz, W * (L.Sz * Ckz)));
+    const float tl = T / det;
+    if (fabsf(tl) < tauL) t.flag = 1;
+    if (t.m < kMaxHits) {
+        hits[t.m] = p;
+    } else {
+        // more hits than recorded: from here on keep a running minimum
+        uint32_t bprim = t.bpos >= 0 ? prim_of(tv, t.bpos) : 0xFFFFFFFFu;
+        if (t.m == kMaxHits)
+            for (int i = 0; i < kMaxHits; ++i)
+                keep_min(hit_key(key, q, walk, step, prim_of(tv, hits[i])), prim_of(tv, hits[i]),
+                         hits[i], t.best, bprim, t.bpos);
+        keep_min(hit_key(key, q, walk, step, __float_as_uint(a4.w)), __float_as_uint(a4.w), p,
+                 t.best, bprim, t.bpos);
+    }
+    t.m++;
+    if (SUM_S) {
+        const float e1x = b4.x - a4.x, e1y = b4.y - a4.y, e1z = b4.z - a4.z;
+        const float e2x = c4.x - a4.x, e2y = c4.y - a4.y, e2z = c4.z - a4.z;
+        const float nx = e1y * e2z - e1z * e2y;
+        const float ny = e1z * e2x - e1x * e2z;
+        const float nz = e1x * e2y - e1y * e2x;
+        const float dn = d.x * nx + d.y * ny + d.z * nz;
+        t.sum_s += ((tl > 0.f) == (dn > 0.f)) ? 1 : -1;
     }
 }
 
-// Test the triangles of leaf t.ref (Woop, Benthin, Wald, "Watertight
-// ray/triangle intersection", JCGT 2013, applied to a line: no parameter
-// range), record hits, flag near-degenerate configurations, then pop.
-template <bool COUNT, bool SUM_S>
-__device__ __forceinline__ void test_leaf(const float4* __restrict__ tv, const LinePre& L,
-                                          float3 d, float Tthr, float tauL, float graze,
-                                          int exclude_pos, Trav& t, int* hits, int* stack,
-                                          StreamKey key, uint32_t q, uint32_t walk,
-                                          uint32_t step, uint32_t& n_tris)
+// ---------------------------------------------------------------------------
+// 8-wide traversal (nodes collapsed from the binary tree; layout in bvh.cu).
+// All hits are wanted, so the order of the children does not matter: a stack
+// entry is a group (first interior child, mask of children still to visit),
+// at most one per level.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pick4(int4 v, int j)
 {
-    const int first = leaf_first(t.ref), count = leaf_count(t.ref);
-    for (int p = first; p < first + count; ++p) {
-        if (p == exclude_pos) continue;
-        if (COUNT) n_tris++;
-        const float4 a4 = __ldg(tv + 3 * p + 0);
-        const float4 b4 = __ldg(tv + 3 * p + 1);
-        const float4 c4 = __ldg(tv + 3 * p + 2);
-        const float3 A = make_float3(a4.x - L.ox, a4.y - L.oy, a4.z - L.oz);
-        const float3 B = make_float3(b4.x - L.ox, b4.y - L.oy, b4.z - L.oz);
-        const float3 C = make_float3(c4.x - L.ox, c4.y - L.oy, c4.z - L.oz);
-        const float Akz = comp(A, L.kz), Bkz = comp(B, L.kz), Ckz = comp(C, L.kz);
-        const float Ax = fmaf(-L.Sx, Akz, comp(A, L.kx));
-        const float Ay = fmaf(-L.Sy, Akz, comp(A, L.ky));
-        const float Bx = fmaf(-L.Sx, Bkz, comp(B, L.kx));
-        const float By = fmaf(-L.Sy, Bkz, comp(B, L.ky));
-        const float Cx = fmaf(-L.Sx, Ckz, comp(C, L.kx));
-        const float Cy = fmaf(-L.Sy, Ckz, comp(C, L.ky));
-        const float U = Cx * By - Cy * Bx;
-        const float V = Ax * Cy - Ay * Cx;
-        const float W = Bx * Ay - By * Ax;
-        const bool pos_side = (U > -Tthr) && (V > -Tthr) && (W > -Tthr);
-        const bool neg_side = (U < Tthr) && (V < Tthr) && (W < Tthr);
-        if (!(pos_side || neg_side)) continue;
-        const float det = U + V + W;
-        const float mn = fminf(fminf(fabsf(U), fabsf(V)), fabsf(W));
-        if (mn < Tthr || fabsf(det) < graze * b4.w * fabsf(L.Sz)) t.flag = 1;
-        const bool hit = (U > 0.f && V > 0.f && W > 0.f) || (U < 0.f && V < 0.f && W < 0.f);
-        if (!hit) continue;
-        const float T = fmaf(U, L.Sz * Akz, fmaf(V, L.Sz * Bkz, W * (L.Sz * Ckz)));
-        const float tl = T / det;
-        if (fabsf(tl) < tauL) t.flag = 1;
-        if (t.m < kMaxHits) {
-            hits[t.m] = p;
-        } else {
-            // more hits than recorded: from here on keep a running minimum
-            uint32_t bprim = t.bpos >= 0 ? prim_of(tv, t.bpos) : 0xFFFFFFFFu;
-            if (t.m == kMaxHits)
-                for (int i = 0; i < kMaxHits; ++i)
-                    keep_min(hit_key(key, q, walk, step, prim_of(tv, hits[i])),
-                             prim_of(tv, hits[i]), hits[i], t.best, bprim, t.bpos);
-            keep_min(hit_key(key, q, walk, step, __float_as_uint(a4.w)), __float_as_uint(a4.w), p,
-                     t.best, bprim, t.bpos);
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+template <bool COUNT, bool SUM_S>
+__device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
+                                           const float4* __restrict__ tv, const LinePre& L,
+                                           float3 d, float Tthr, float tauL, float graze,
+                                           int exclude_pos, Trav& t, int* hits, int* stack,
+                                           StreamKey key, uint32_t q, uint32_t walk,
+                                           uint32_t step, uint32_t& n_nodes, uint32_t& n_tris,
+                                           int& err, int iter_limit)
+{
+    int node = 0, sp = 0, iters = 0;
+    while (true) {
+        if (node >= 0) {
+            if (++iters > iter_limit) {  // each node is visited at most once per line
+                err |= 2;
+                break;
+            }
+            if (COUNT) n_nodes++;
+            const float4* nd = wn + 6 * node;
+            const float4 h = __ldg(nd);
+            const uint32_t hdr = __float_as_uint(h.w);
+            const int nint = (hdr >> 24) & 15, nch = hdr >> 28;
+            // slab parameter of a quantised plane: (origin + q s - o) / d = q a + b
+            const float ax = __uint_as_float((hdr & 255u) << 23) * L.ix;
+            const float ay = __uint_as_float(((hdr >> 8) & 255u) << 23) * L.iy;
+            const float az = __uint_as_float(((hdr >> 16) & 255u) << 23) * L.iz;
+            const float bx = fmaf(h.x, L.ix, -L.oix), by = fmaf(h.y, L.iy, -L.oiy),
+                        bz = fmaf(h.z, L.iz, -L.oiz);
+            const uint4 qx = __ldg(reinterpret_cast<const uint4*>(nd + 1));
+            const uint4 qy = __ldg(reinterpret_cast<const uint4*>(nd + 2));
+            const uint4 qz = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+            uint32_t hit = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int sh = 8 * (j & 3);
+                const uint32_t lxw = j < 4 ? qx.x : qx.y, hxw = j < 4 ? qx.z : qx.w;
+                const uint32_t lyw = j < 4 ? qy.x : qy.y, hyw = j < 4 ? qy.z : qy.w;
+                const uint32_t lzw = j < 4 ? qz.x : qz.y, hzw = j < 4 ? qz.z : qz.w;
+                const float t0x = fmaf((float)((lxw >> sh) & 255u), ax, bx);
+                const float t1x = fmaf((float)((hxw >> sh) & 255u), ax, bx);
+                const float t0y = fmaf((float)((lyw >> sh) & 255u), ay, by);
+                const float t1y = fmaf((float)((hyw >> sh) & 255u), ay, by);
+                const float t0z = fmaf((float)((lzw >> sh) & 255u), az, bz);
+                const float t1z = fmaf((float)((hzw >> sh) & 255u), az, bz);
+                const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
+                const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+                if (j < nch && tn <= tf) hit |= 1u << j;
+            }
+            const int4 r0 = __ldg(reinterpret_cast<const int4*>(nd + 4));
+            uint32_t lm = hit >> nint;  // leaf children
+            if (lm) {
+                const int4 r1 = __ldg(reinterpret_cast<const int4*>(nd + 5));
+                while (lm) {
+                    const int j = nint + __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    const int ref = j < 4 ? pick4(r0, j) : pick4(r1, j - 4);
+                    const int first = leaf_first(ref), count = leaf_count(ref);
+                    for (int p = first; p < first + count; ++p) {
+                        if (p == exclude_pos) continue;
+                        if (COUNT) n_tris++;
+                        test_tri<SUM_S>(tv, L, d, Tthr, tauL, graze, p, t, hits, key, q, walk,
+                                        step);
+                    }
+                }
+            }
+            uint32_t im = hit & ((1u << nint) - 1u);  // interior children
+            if (im) {
+                const int c = __ffs(im) - 1;
+                im &= im - 1;
+                if (im) {
+                    if (sp < kStackSize) stack[sp++] = r0.x | (int)(im << 24);
+                    else err |= 1;
+                }
+                node = r0.x + c;
+                continue;
+            }
+            node = -1;
         }
-        t.m++;
-        if (SUM_S) {
-            const float e1x = b4.x - a4.x, e1y = b4.y - a4.y, e1z = b4.z - a4.z;
-            const float e2x = c4.x - a4.x, e2y = c4.y - a4.y, e2z = c4.z - a4.z;
-            const float nx = e1y * e2z - e1z * e2y;
-            const float ny = e1z * e2x - e1x * e2z;
-            const float nz = e1x * e2y - e1y * e2x;
-            const float dn = d.x * nx + d.y * ny + d.z * nz;
-            t.sum_s += ((tl > 0.f) == (dn > 0.f)) ? 1 : -1;
-        }
+        if (sp == 0) break;
+        const uint32_t e = (uint32_t)stack[--sp];
+        const int base = (int)(e & 0xFFFFFFu);
+        uint32_t m = e >> 24;
+        const int c = __ffs(m) - 1;
+        m &= m - 1;
+        if (m) stack[sp++] = base | (int)(m << 24);
+        node = base + c;
     }
-    t.ref = t.sp > 0 ? stack[--t.sp] : kNoRef;
 }
 
 // The picked hit (leaf position) after the traversal; -1 if m == 0.
@@ -338,7 +384,7 @@ __device__ __forceinline__ int select_hit(const float4* __restrict__ tv, const T
 // Whole traversal of one line (debug entry point).
 template <bool SUM_S>
 __device__ __forceinline__ int trace_line(const float4* __restrict__ nodes,
-                                          const float4* __restrict__ tv, int root, float3 o,
+                                          const float4* __restrict__ tv, float3 o,
                                           float3 d, int exclude_pos, StreamKey key, uint32_t q,
                                           uint32_t walk, uint32_t step, float edge_thr_L,
                                           float tauL, float graze, Trav& t, int& err,
@@ -349,13 +395,9 @@ __device__ __forceinline__ int trace_line(const float4* __restrict__ nodes,
     int stack[kStackSize];
     int hits[kMaxHits];
     uint32_t nn = 0, nt = 0;
-    trav_init(t, root);
-    while (t.ref != kNoRef) {
-        descend<false>(nodes, L, t, stack, nn, err, iter_limit);
-        if (t.ref == kNoRef) break;
-        test_leaf<false, SUM_S>(tv, L, d, Tthr, tauL, graze, exclude_pos, t, hits, stack, key, q,
-                                walk, step, nt);
-    }
+    trav_init(t);
+    trace_wide<false, SUM_S>(nodes, tv, L, d, Tthr, tauL, graze, exclude_pos, t, hits, stack, key,
+                             q, walk, step, nn, nt, err, iter_limit);
     return select_hit(tv, t, hits, key, q, walk, step);
 }
 
@@ -439,9 +481,8 @@ __device__ __forceinline__ void dl_accumulate(const float4* __restrict__ tv, con
 
 // Geometry a double-layer walk needs.
 struct DLGeom {
-    const float4* nodes;
+    const float4* nodes;  // 8-wide nodes, root = node 0
     const float4* tv;
-    int root;
     int iter_limit;
     float edge_thr_L;
     float tauL;
@@ -505,14 +546,11 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         }
         const float Tthr = G.edge_thr_L * fabsf(L.Sz);
         Trav t;
-        trav_init(t, G.root);
+        trav_init(t);
         uint32_t nn = 0, nt = 0;
-        while (t.ref != kNoRef) {
-            descend<COUNT>(G.nodes, L, t, stack, nn, err, G.iter_limit);
-            if (t.ref == kNoRef) break;
-            test_leaf<COUNT, false>(G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, G.tauL, G.graze,
-                                    self, t, hits, stack, key, q, w, (uint32_t)k, nt);
-        }
+        trace_wide<COUNT, false>(G.nodes, G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, G.tauL,
+                                 G.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn, nt,
+                                 err, G.iter_limit);
         if (COUNT) {
             c.lines++;
             c.nodes += nn;

@@ -38,6 +38,9 @@ struct MeshDev {
 
 struct BvhDev {
     float4* nodes = nullptr;  // 4 float4 per interior node
+    float4* wnodes = nullptr; // 8-wide nodes, 6 float4 each (collapsed from `nodes`)
+    int64_t n_wide = 0;
+    int wide_levels = 0;
     float4* tv = nullptr;     // 3 float4 per triangle, leaf order
     int32_t* order = nullptr; // leaf order -> original triangle id
     int32_t* inv_order = nullptr; // original triangle id -> leaf order
@@ -61,11 +64,10 @@ struct DataDev {
 
 struct WalkParams {
     // geometry
-    const float4* nodes;
+    const float4* nodes;  // 8-wide BVH nodes (root = node 0)
     const float4* tv;
     const int32_t* inv_order;
-    int root;
-    int iter_limit;  // traversal loop bound (4 x nodes + 64)
+    int iter_limit;  // traversal loop bound (4 x wide nodes + 64)
     const float* verts;
     const int32_t* tris;
     const NormalArea* tri_n;
