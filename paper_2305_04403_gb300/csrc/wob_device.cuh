@@ -270,6 +270,13 @@ __device__ __forceinline__ void test_tri(const float4* __restrict__ tv, const Li
 // entry is a group (first interior child, mask of children still to visit),
 // at most one per level.
 // ---------------------------------------------------------------------------
+// Byte b of w as an exact float: the byte is placed in the low mantissa of
+// 2^23 (one byte permute), then 2^23 is subtracted.
+__device__ __forceinline__ float dequant(uint32_t w, int b)
+{
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u | (uint32_t)b)) - 8388608.0f;
+}
+
 __device__ __forceinline__ int pick4(int4 v, int j)
 {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
@@ -305,21 +312,27 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
             const uint4 qx = __ldg(reinterpret_cast<const uint4*>(nd + 1));
             const uint4 qy = __ldg(reinterpret_cast<const uint4*>(nd + 2));
             const uint4 qz = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+            // per axis the near plane is the low one when the axis component
+            // is positive (t = q a + b is monotone in q): pick near / far
+            // byte words once, so a slab test is max of 3 nears <= min of 3 fars
+            const bool px_ = L.ix >= 0.f, py_ = L.iy >= 0.f, pz_ = L.iz >= 0.f;
+            const uint32_t nx0 = px_ ? qx.x : qx.z, nx1 = px_ ? qx.y : qx.w;
+            const uint32_t fx0 = px_ ? qx.z : qx.x, fx1 = px_ ? qx.w : qx.y;
+            const uint32_t ny0 = py_ ? qy.x : qy.z, ny1 = py_ ? qy.y : qy.w;
+            const uint32_t fy0 = py_ ? qy.z : qy.x, fy1 = py_ ? qy.w : qy.y;
+            const uint32_t nz0 = pz_ ? qz.x : qz.z, nz1 = pz_ ? qz.y : qz.w;
+            const uint32_t fz0 = pz_ ? qz.z : qz.x, fz1 = pz_ ? qz.w : qz.y;
             uint32_t hit = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int sh = 8 * (j & 3);
-                const uint32_t lxw = j < 4 ? qx.x : qx.y, hxw = j < 4 ? qx.z : qx.w;
-                const uint32_t lyw = j < 4 ? qy.x : qy.y, hyw = j < 4 ? qy.z : qy.w;
-                const uint32_t lzw = j < 4 ? qz.x : qz.y, hzw = j < 4 ? qz.z : qz.w;
-                const float t0x = fmaf((float)((lxw >> sh) & 255u), ax, bx);
-                const float t1x = fmaf((float)((hxw >> sh) & 255u), ax, bx);
-                const float t0y = fmaf((float)((lyw >> sh) & 255u), ay, by);
-                const float t1y = fmaf((float)((hyw >> sh) & 255u), ay, by);
-                const float t0z = fmaf((float)((lzw >> sh) & 255u), az, bz);
-                const float t1z = fmaf((float)((hzw >> sh) & 255u), az, bz);
-                const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
-                const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+                const float tnx = fmaf(dequant(j < 4 ? nx0 : nx1, j & 3), ax, bx);
+                const float tfx = fmaf(dequant(j < 4 ? fx0 : fx1, j & 3), ax, bx);
+                const float tny = fmaf(dequant(j < 4 ? ny0 : ny1, j & 3), ay, by);
+                const float tfy = fmaf(dequant(j < 4 ? fy0 : fy1, j & 3), ay, by);
+                const float tnz = fmaf(dequant(j < 4 ? nz0 : nz1, j & 3), az, bz);
+                const float tfz = fmaf(dequant(j < 4 ? fz0 : fz1, j & 3), az, bz);
+                const float tn = fmaxf(fmaxf(tnx, tny), tnz);
+                const float tf = fminf(fminf(tfx, tfy), tfz);
                 if (j < nch && tn <= tf) hit |= 1u << j;
             }
             const int4 r0 = __ldg(reinterpret_cast<const int4*>(nd + 4));
