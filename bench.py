@@ -311,6 +311,77 @@ def run_batched(args):
     }
 
 
+def run_sl(args):
+    """Third configuration: single-layer walks with area sampling (Sec. 4.3,
+    Table 1) on a seeded displaced torus (R = 1, tube 0.35, 500 x 200 quads =
+    200,000 triangles): an interior Neumann problem with data dh/dn of
+    h = 1/|x - (0, 0, 5)| and an exterior Robin problem (alpha = 2) with
+    h = 1/|x - (1, 0, 0.05)| (x0 inside the solid torus, so h is harmonic
+    outside it); 131,072 queries each, half on the boundary (area-uniform,
+    with their triangles) and half off it (inside resp. outside the torus),
+    512 walks, M = 24.  A step is both solves; a path vertex is one area
+    sample (Q x N x M per solve: a walk stops early only on an exact
+    coincidence of two points)."""
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    from paper_2305_04403_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    v, f, shape = I.displaced_torus()
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    Q, N, M = args.sl_queries, 512, 24
+    half = Q // 2
+    probs, qs, prs = [], [], []
+    for k, (kind, side, alpha, x0, inside) in enumerate(
+            [(wob.NEUMANN_SL, 1, 0.0, (0.0, 0.0, 5.0), True),
+             (wob.ROBIN_SL, -1, 2.0, (1.0, 0.0, 0.05), False)]):
+        pb, prim = I.boundary_points(v, f, half, seed=10 + k)
+        off = I.torus_queries(shape, Q - half, inside, seed=20 + k)
+        q = np.concatenate([pb, off]).astype(np.float32)
+        pr = np.concatenate([prim, np.full(Q - half, -1, np.int32)])
+        probs.append(wob.Problem(bvh, kind=kind, side=side, alpha=alpha,
+                                 data_mode=wob.DATA_POINT, x0=x0, problem=k))
+        qs.append(torch.from_numpy(q).cuda())
+        prs.append(torch.from_numpy(pr).cuda())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        for prob, q, pr in zip(probs, qs, prs):
+            wob.solve(prob, q, N, M, seed=SEED, query_prim=pr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    verts = 2 * Q * N * M
+    return {
+        "metric": METRIC, "value": verts * args.steps / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 geometry / f64 walk arithmetic",
+        "data": "synthetic (seeded displaced torus, seeded queries)",
+        "config": {"workload": f"displaced torus ({len(f)} tris), single layer, area sampling: "
+                               f"interior Neumann + exterior Robin (alpha 2), {Q} queries each "
+                               f"(half on the boundary), {N} walks, M = {M}",
+                   "path_vertices_per_step": verts,
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "clocks": clk.summary(), "gpu_launches": 4 * args.steps,
+    }
+
+
 def run_cv(args):
     """Learned control variate vs plain WoB: time to RMSE 1e-3 against the
     exact solution on the icosphere-L3 mesh (1,280 triangles) with
@@ -542,7 +613,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
-    ap.add_argument("--workload", default="star", choices=["star", "batched", "cv"])
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "cv", "sl"])
+    ap.add_argument("--sl-queries", type=int, default=131072)
     ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
     ap.add_argument("--cv-queries", type=int, default=65536,
                     help="queries of the cv workload (the metric is defined at 65,536)")
@@ -560,6 +632,8 @@ def main():
         line = run_batched(args)
     elif args.workload == "cv":
         line = run_cv(args)
+    elif args.workload == "sl":
+        line = run_sl(args)
     else:
         line = run_ours(args)
     if line is not None:

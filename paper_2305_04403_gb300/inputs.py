@@ -239,6 +239,26 @@ def star_slice_queries(shape: StarShape, n_side: int = 256, extent: float = 1.3,
     return p[keep].astype(np.float32)
 
 
+def torus_queries(shape: TorusShape, n: int, inside: bool, seed: int = 1,
+                  margin: float = 1e-2) -> np.ndarray:
+    """n points uniform inside the displaced torus (inside=True) or in the
+    box [-2, 2]^2 x [-1, 1] outside it, at least ``margin`` from its tube."""
+    rng = np.random.default_rng(seed)
+    ext = shape.R + 1.5 * shape.r if inside else 2.0
+    zext = 1.5 * shape.r if inside else 1.0
+    out = []
+    got = 0
+    while got < n:
+        p = rng.uniform(-1.0, 1.0, (4 * n, 3)) * np.array([ext, ext, zext])
+        if inside:
+            keep = torus_inside(shape, p, margin)
+        else:
+            keep = ~torus_inside(shape, p, -margin)
+        out.append(p[keep])
+        got += int(keep.sum())
+    return np.concatenate(out)[:n].astype(np.float32)
+
+
 def boundary_points(verts: np.ndarray, tris: np.ndarray, n: int, seed: int = 1):
     """Area-uniform points on the mesh and the triangle each lies on."""
     rng = np.random.default_rng(seed)
