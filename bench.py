@@ -45,9 +45,8 @@ OPS_NODE, OPS_TRI, OPS_HIT, OPS_LINE = 320, 41, 100, 235
 BYTES_NODE, BYTES_TRI = 96, 48
 # DRAM bytes (read + write) of one full-size k_dl_walks launch of this
 # workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
-# dram__bytes_write.sum (profiles/k_dl_walks_star6_full_traffic.md); None
-# until taken for the current kernel.
-TRAFFIC_FULL = None
+# dram__bytes_write.sum (profiles/k_dl_walks_star6_wide.md).
+TRAFFIC_FULL = (29497, 1, 40.09e6 + 224.95e6)
 
 
 def _peaks():
