@@ -381,6 +381,63 @@ def run_sl(args):
     }
 
 
+def run_nd(args):
+    """Neumann problem through the paper's direct boundary integral equation
+    (Sec. 4.2) on the third configuration's torus: interior, data dh/dn of
+    h = 1/|x - (0, 0, 5)|, 131,072 queries (half on the boundary, half
+    inside), 512 walks, M = 24.  Every vertex takes one line query (all
+    hits, 8-wide BVH) and one area sample for the G q source; from inside a
+    closed surface every line hits, so a walk has exactly M line queries.
+    A step is one solve; a path vertex is one line query."""
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    from paper_2305_04403_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    v, f, shape = I.displaced_torus()
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    Q, N, M = args.sl_queries, 512, 24
+    half = Q // 2
+    pb, prim = I.boundary_points(v, f, half, seed=10)
+    off = I.torus_queries(shape, Q - half, True, seed=20)
+    q = torch.from_numpy(np.concatenate([pb, off]).astype(np.float32)).cuda()
+    pr = torch.from_numpy(np.concatenate([prim, np.full(Q - half, -1, np.int32)])).cuda()
+    prob = wob.Problem(bvh, kind=wob.NEUMANN_DIRECT, side=1, data_mode=wob.DATA_POINT,
+                       x0=(0.0, 0.0, 5.0))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        wob.solve(prob, q, N, M, seed=SEED, query_prim=pr)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            wob.solve(prob, q, N, M, seed=SEED, query_prim=pr)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    lines = (Q - half) * N * M + half * N * (M - 1)
+    return {
+        "metric": METRIC, "value": lines * args.steps / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 geometry / f64 walk arithmetic",
+        "data": "synthetic (seeded displaced torus, seeded queries)",
+        "config": {"workload": f"displaced torus ({len(f)} tris), interior Neumann through the "
+                               f"direct boundary integral equation, {Q} queries (half on the "
+                               f"boundary), {N} walks, M = {M}",
+                   "line_queries_per_step": lines, "area_samples_per_step": Q * N * M + (Q - half) * N,
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
+    }
+
+
 def run_cv(args):
     """Learned control variate vs plain WoB: time to RMSE 1e-3 against the
     exact solution on the icosphere-L3 mesh (1,280 triangles) with
@@ -612,7 +669,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
-    ap.add_argument("--workload", default="star", choices=["star", "batched", "cv", "sl"])
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "cv", "sl", "nd"])
     ap.add_argument("--sl-queries", type=int, default=131072)
     ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
     ap.add_argument("--cv-queries", type=int, default=65536,
@@ -633,6 +690,8 @@ def main():
         line = run_cv(args)
     elif args.workload == "sl":
         line = run_sl(args)
+    elif args.workload == "nd":
+        line = run_nd(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -50,9 +50,12 @@ extern "C" {
 
 /* Boundary-integral formulation (Table 1 of the paper). */
 typedef enum {
-    WOB_DIRICHLET_DL = 0, /* Dirichlet data, double-layer potential (Sec. 4.1) */
-    WOB_NEUMANN_SL = 1,   /* Neumann data, single-layer potential (Sec. 4.3) */
-    WOB_ROBIN_SL = 2      /* Robin data, single-layer potential (Sec. 4.3) */
+    WOB_DIRICHLET_DL = 0,   /* Dirichlet data, double-layer potential (Sec. 4.1) */
+    WOB_NEUMANN_SL = 1,     /* Neumann data, single-layer potential (Sec. 4.3) */
+    WOB_ROBIN_SL = 2,       /* Robin data, single-layer potential (Sec. 4.3) */
+    WOB_NEUMANN_DIRECT = 3  /* Neumann data, direct boundary integral equation
+                               (Sec. 4.2): lines for the dG/dn_y term, one
+                               area-uniform point per vertex for the G q term */
 } wob_kind;
 
 /* How the boundary data is given. */
@@ -171,8 +174,16 @@ void wob_destroy_bvh(wob_bvh b);
  *   est[q] = mean of the walk values, var[q] = their unbiased sample variance
  *   (the standard error is sqrt(var / walks)).
  * queries: device, Q x 3 float.  query_prim: device, Q int32 (the triangle a
- * query lies on, -1 off the boundary) or NULL; used only by the single-layer
- * kinds, where it marks points on Gamma; must be NULL for WOB_DIRICHLET_DL.
+ * query lies on, -1 off the boundary) or NULL: for the single-layer kinds it
+ * marks points on Gamma; for WOB_NEUMANN_DIRECT a query on triangle
+ * query_prim[q] is the walk's first boundary vertex (weight 1) and the walk
+ * estimates u there; for WOB_DIRICHLET_DL use wob_solve_density.
+ * WOB_NEUMANN_DIRECT (Sec. 4.2): from a point off the boundary the first
+ * line has weight phi (m/2) s and the source phi |Gamma| G(x0, x') q(x') at
+ * an area-uniform x'; each boundary vertex has line weight phi m s and
+ * source 2 phi |Gamma| G q, halved at the last vertex (Sec. 4.1.2); q is
+ * dh/dn of the field (POLY, POINT) or the P1 vertex data.  Interior Neumann
+ * solutions are defined up to a constant: the walks do not fix it.
  * est, var: device, Q doubles.  walks >= 2, 1 <= max_len <= 4096.
  * Allocates scratch of Q * walks doubles on `stream` (stream-ordered).
  */

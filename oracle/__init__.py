@@ -87,6 +87,8 @@ def _load():
                                             I64, I64, I32, I32, U64, U32, D, D, P, P, P, P,
                                             ctypes.c_int]
             lib.oracle_dl_walks.restype = ctypes.c_int
+            lib.oracle_nd_walks.argtypes = lib.oracle_dl_walks.argtypes
+            lib.oracle_nd_walks.restype = ctypes.c_int
             lib.oracle_sl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, D, I32,
                                             P, I64, I64, I64, I32, I32, U64, U32, P, P,
                                             ctypes.c_int]
@@ -242,6 +244,38 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     del keep
     if rc != 0:
         raise RuntimeError("oracle_dl_walks failed")
+    out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
+    if want_lines:
+        out["line_m"] = line_m
+    return out
+
+
+def nd_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, problem: int = 0,
+             phi: int = 1, mode: int = DATA_POLY, vertex_data=None, poly=None, x0=None,
+             scale: float = 1.0, q_offset: int = 0, walk_begin: int = 0, tau: float = TAU,
+             graze: float = GRAZE, want_lines: bool = False, nthreads: int = 0,
+             query_prim=None) -> dict:
+    """Neumann walks through the direct boundary integral equation (Sec. 4.2):
+    lines for the dG/dn_y term, one area sample per vertex for the G q term,
+    q = dh/dn of the field (or the P1 vertex data); with query_prim the walks
+    start on the boundary.  Returns per_walk, flag, abs_terms (and line_m)."""
+    v = _c(verts, np.float32)
+    t = _c(tris, np.int32)
+    q = _c(queries, np.float32).reshape(-1, 3)
+    Q = q.shape[0]
+    data, keep = _data(mode, vertex_data, poly, x0, scale)
+    per_walk = np.empty((Q, walks), np.float64)
+    flag = np.empty((Q, walks), np.uint8)
+    line_m = np.empty((Q, walks, max_len), np.int32) if want_lines else None
+    abs_terms = np.empty((Q, walks), np.float64)
+    qp = None if query_prim is None else _c(query_prim, np.int32)
+    rc = _load().oracle_nd_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
+                                 _p(q), _p(qp), Q, q_offset, walk_begin, walks, max_len, seed,
+                                 problem, tau, graze, _p(per_walk), _p(flag), _p(line_m),
+                                 _p(abs_terms), nthreads)
+    del keep
+    if rc != 0:
+        raise RuntimeError("oracle_nd_walks failed")
     out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
     if want_lines:
         out["line_m"] = line_m

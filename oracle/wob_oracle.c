@@ -513,6 +513,70 @@ static double sl_walk(const mesh_t *M, const oracle_data *D, int kind, double al
     return W0 * S;
 }
 
+/* Neumann problem through the direct boundary integral equation (Sec. 4.2):
+ * on the boundary u = -2 phi int dG/dn_y u dA + 2 phi int G q dA, at a point
+ * off it u = -phi int dG/dn_y u dA + phi int G q dA (the Green representation
+ * with the normal pointing out of Omega; phi = +1 interior, -1 exterior).
+ * The dG/dn_y term is sampled with lines as in the double-layer walks: weight
+ * -phi dG/dn_y / p = phi (m/2) s from the query, -2 phi dG/dn_y / p = phi m s
+ * from a boundary vertex.  The G q term takes one area-uniform point x' per
+ * vertex: phi |Gamma| G(x, x') q(x') at the query, twice that on the
+ * boundary, and half of it at the last vertex x_M (the truncation rule of
+ * Sec. 4.1.2).  q = dh/dn (or the P1 vertex data).  start_prim >= 0: the
+ * query lies on that triangle and is boundary vertex 1 (weight 1). */
+static double nd_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const double x0[3],
+                      int64_t start_prim, uint32_t q, uint32_t walk, int32_t Mlen,
+                      uint64_t seed, uint32_t problem, double tauL, double graze,
+                      uint8_t *flag, int32_t *line_m, double *abs_terms)
+{
+    double x[3] = { x0[0], x0[1], x0[2] };
+    int64_t exclude = -1;
+    double S = 0.0, P = 1.0, A = 0.0;
+    const double four_pi = 4.0 * ORACLE_PI;
+    int32_t k0 = 0;
+    *flag = 0;
+    if (start_prim >= 0) {
+        exclude = start_prim;
+        k0 = 1;
+        if (line_m) line_m[0] = -1;
+    }
+    for (int32_t k = k0; k <= Mlen; ++k) {
+        /* source at vertex k */
+        int64_t j;
+        double y[3], b[3], r[3];
+        area_sample(M, seed, problem, q, walk, (uint32_t)k, &j, y, b);
+        sub3(y, x, r);
+        double rl = norm3(r);
+        if (rl >= 1e-12 * M->L) {
+            double N[3], n[3];
+            tri_normal(M, j, N);
+            double nl = norm3(N);
+            n[0] = N[0] / nl; n[1] = N[1] / nl; n[2] = N[2] / nl;
+            double f = boundary_data(D, M, j, y, b, n, KIND_NEUMANN_SL, 0.0);
+            double c = (k == 0) ? (double)phi : 2.0 * (double)phi;
+            if (k == Mlen) c *= 0.5;
+            double term = P * c * M->area * f / (four_pi * rl);
+            S += term;
+            A += fabs(term);
+        }
+        if (k == Mlen) break;
+        /* line from vertex k to vertex k + 1 */
+        double d[3];
+        line_axis(seed, problem, q, walk, (uint32_t)k, d);
+        line_result lr;
+        trace_line(M, x, d, exclude, seed, problem, q, walk, (uint32_t)k, tauL, graze, &lr);
+        if (line_m) line_m[k] = lr.m;
+        if (lr.flag) *flag = 1;
+        if (lr.m == 0) break;
+        const double ms = (double)lr.m * (double)lr.s;
+        P *= (k == 0) ? 0.5 * (double)phi * ms : (double)phi * ms;
+        x[0] = lr.y[0]; x[1] = lr.y[1]; x[2] = lr.y[2];
+        exclude = lr.prim;
+    }
+    *abs_terms = A;
+    return S;
+}
+
 /* ======================================================================== */
 /* Exported entry points (called from Python through ctypes).               */
 /* ======================================================================== */
@@ -675,6 +739,41 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
 /* Single-layer Neumann (kind 1) or Robin (kind 2) walks; query_prim is
  * accepted for symmetry with the library but the first step does not
  * depend on it (area sampling, u = int G mu dA holds on Gamma too). */
+/* Direct-BIE Neumann walks (nd_walk), laid out as oracle_dl_walks. */
+int oracle_nd_walks(const float *verts, int64_t V, const int32_t *tris, int64_t T,
+                    const oracle_data *D, int32_t phi, const float *queries,
+                    const int32_t *query_prim, int64_t Q,
+                    int64_t q_offset, int64_t walk_begin, int32_t N, int32_t Mlen,
+                    uint64_t seed, uint32_t problem, double tau, double graze,
+                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, double *abs_terms,
+                    int nthreads)
+{
+    mesh_t M;
+    if (mesh_init(&M, verts, V, tris, T, 1)) return -1;
+    double tauL = tau * M.L;
+    int nt = set_threads(nthreads);
+    int64_t total = Q * (int64_t)N;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+    for (int64_t i = 0; i < total; ++i) {
+        int64_t qi = i / N, w = i % N;
+        double x0[3] = { queries[3 * qi], queries[3 * qi + 1], queries[3 * qi + 2] };
+        int32_t *lm = NULL;
+        if (line_m) {
+            lm = line_m + i * Mlen;
+            for (int32_t k = 0; k < Mlen; ++k) lm[k] = -1;
+        }
+        uint8_t f;
+        double at;
+        per_walk[i] = nd_walk(&M, D, phi, x0, query_prim ? query_prim[qi] : -1,
+                              (uint32_t)(q_offset + qi), (uint32_t)(walk_begin + w), Mlen, seed,
+                              problem, tauL, graze, &f, lm, &at);
+        if (walk_flag) walk_flag[i] = f;
+        if (abs_terms) abs_terms[i] = at;
+    }
+    mesh_free(&M);
+    return 0;
+}
+
 int oracle_sl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t T,
                     const oracle_data *D, int32_t kind, double alpha, int32_t phi,
                     const float *queries, int64_t Q, int64_t q_offset, int64_t walk_begin,

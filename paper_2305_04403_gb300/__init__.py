@@ -19,14 +19,14 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
+    "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "NEUMANN_DIRECT", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
     "WobError", "Mesh", "BVH", "Problem", "Batch", "build_mesh", "build_bvh", "solve", "solve_range",
     "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "solve_density",
     "mlp_num_params", "mlp_forward", "mlp_train_step", "ControlVariate", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
 
-DIRICHLET_DL, NEUMANN_SL, ROBIN_SL = 0, 1, 2
+DIRICHLET_DL, NEUMANN_SL, ROBIN_SL, NEUMANN_DIRECT = 0, 1, 2, 3
 DATA_VERTEX_P1, DATA_POLY, DATA_POINT = 0, 1, 2
 
 _ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "DEGENERATE_MESH",

@@ -49,7 +49,7 @@ int check_problem(const wob_problem* prob)
         set_error("problem or problem->bvh is NULL");
         return WOB_ERR_INVALID_ARG;
     }
-    if (prob->kind < WOB_DIRICHLET_DL || prob->kind > WOB_ROBIN_SL) {
+    if (prob->kind < WOB_DIRICHLET_DL || prob->kind > WOB_NEUMANN_DIRECT) {
         set_error("unknown kind %d", prob->kind);
         return WOB_ERR_INVALID_ARG;
     }
@@ -144,6 +144,7 @@ int run_walks(WalkParams& p, const wob_debug_out* dbg, bool counted, cudaStream_
         p.line_m = dbg->line_m;
     }
     if (p.kind == WOB_DIRICHLET_DL) return launch_dl_walks(p, counted, dbg != nullptr, s);
+    if (p.kind == WOB_NEUMANN_DIRECT) return launch_nd_walks(p, dbg != nullptr, s);
     return launch_sl_walks(p, dbg != nullptr, s);
 }
 

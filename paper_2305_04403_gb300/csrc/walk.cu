@@ -111,7 +111,45 @@ __device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double
         gz = f * rz;
     }
     const double dhdn = n.x * gx + n.y * gy + n.z * gz;
-    return p.kind == WOB_NEUMANN_SL ? dhdn : dhdn + (double)p.alpha * h;
+    return p.kind == WOB_ROBIN_SL ? dhdn + (double)p.alpha * h : dhdn;
+}
+
+// Area-uniform boundary point of stream (q, w, step): triangle j (original
+// order) by inverse CDF of the areas (53-bit uniform), then a uniform point
+// on it (square-root warp), barycentrics b0..b2; n = the triangle's unit normal.
+struct AreaPoint {
+    int64_t j;
+    double3 y, n;
+    double b0, b1, b2;
+};
+
+__device__ __forceinline__ AreaPoint area_point(const WalkParams& p, StreamKey key, uint32_t q,
+                                                uint32_t w, uint32_t step)
+{
+    AreaPoint a;
+    const u32x4 u = stream_block(key, q, w, step, kPurposeArea, 0u, 0u);
+    const double target = u53(u.x, u.y) * p.area;
+    int64_t lo = 0, hi = p.T - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(p.cdf + mid) > target) hi = mid; else lo = mid + 1;
+    }
+    const double su = sqrt(u24(u.z)), u2 = u24(u.w);
+    a.b0 = 1.0 - su;
+    a.b1 = su * (1.0 - u2);
+    a.b2 = su * u2;
+    const int32_t* t = p.tris + 3 * lo;
+    const float* v0 = p.verts + 3 * (int64_t)__ldg(t);
+    const float* v1 = p.verts + 3 * (int64_t)__ldg(t + 1);
+    const float* v2 = p.verts + 3 * (int64_t)__ldg(t + 2);
+    a.y = make_double3(a.b0 * __ldg(v0) + a.b1 * __ldg(v1) + a.b2 * __ldg(v2),
+                       a.b0 * __ldg(v0 + 1) + a.b1 * __ldg(v1 + 1) + a.b2 * __ldg(v2 + 1),
+                       a.b0 * __ldg(v0 + 2) + a.b1 * __ldg(v1 + 2) + a.b2 * __ldg(v2 + 2));
+    const double2 nxy = __ldg(reinterpret_cast<const double2*>(p.tri_n + lo));
+    const double nz = __ldg(reinterpret_cast<const double*>(p.tri_n + lo) + 2);
+    a.n = make_double3(nxy.x, nxy.y, nz);
+    a.j = lo;
+    return a;
 }
 
 template <bool DEBUG>
@@ -132,25 +170,8 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
         double3 nx = make_double3(0.0, 0.0, 0.0);
         double S = 0.0, P = 1.0, W0 = 0.0;
         for (int k = 0; k < p.M; ++k) {
-            // area-uniform point: triangle by inverse CDF of the areas, then
-            // a uniform point on it (square-root warp)
-            const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeArea, 0u, 0u);
-            const double target = u53(u.x, u.y) * area;
-            int64_t lo = 0, hi = p.T - 1;
-            while (lo < hi) {
-                const int64_t mid = lo + ((hi - lo) >> 1);
-                if (__ldg(p.cdf + mid) > target) hi = mid; else lo = mid + 1;
-            }
-            const double su = sqrt(u24(u.z)), u2 = u24(u.w);
-            const double b0 = 1.0 - su, b1 = su * (1.0 - u2), b2 = su * u2;
-            const int32_t* t = p.tris + 3 * lo;
-            const float* v0 = p.verts + 3 * (int64_t)__ldg(t);
-            const float* v1 = p.verts + 3 * (int64_t)__ldg(t + 1);
-            const float* v2 = p.verts + 3 * (int64_t)__ldg(t + 2);
-            const double3 y = make_double3(
-                b0 * __ldg(v0) + b1 * __ldg(v1) + b2 * __ldg(v2),
-                b0 * __ldg(v0 + 1) + b1 * __ldg(v1 + 1) + b2 * __ldg(v2 + 1),
-                b0 * __ldg(v0 + 2) + b1 * __ldg(v1 + 2) + b2 * __ldg(v2 + 2));
+            const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
+            const double3 y = a.y;
             const double rx = y.x - x.x, ry = y.y - x.y, rz = y.z - x.z;
             const double rl = sqrt(rx * rx + ry * ry + rz * rz);
             if (rl < rmin) break;
@@ -161,10 +182,8 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
                 if (p.kind == WOB_ROBIN_SL) wk += (double)p.alpha / (kFourPi * rl);
                 P *= -2.0 * phi * area * wk;
             }
-            const double2 nxy = __ldg(reinterpret_cast<const double2*>(p.tri_n + lo));
-            const double nz = __ldg(reinterpret_cast<const double*>(p.tri_n + lo) + 2);
-            const double3 n = make_double3(nxy.x, nxy.y, nz);
-            const double f = sl_data(p, lo, y, b0, b1, b2, n);
+            const double3 n = a.n;
+            const double f = sl_data(p, a.j, y, a.b0, a.b1, a.b2, n);
             const double c = (k == p.M - 1) ? phi : 2.0 * phi;
             S = fma(P * c, f, S);
             x = y;
@@ -173,6 +192,81 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
         p.per_walk[idx] = W0 * S;
         if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
     }
+}
+
+// Neumann walks through the direct boundary integral equation (Sec. 4.2):
+// at a point x off the boundary u = phi (S q - int dG/dn_y u), on it
+// u = 2 phi (S q - int dG/dn_y u).  Each vertex takes one area-uniform
+// point x' for the source (|Gamma| G(x, x') q(x'), times c = phi off the
+// boundary, 2 phi on it, halved at the last vertex x_M -- Sec. 4.1.2) and
+// one line for the dG/dn_y term (weight phi (m/2) s from x0, phi m s from a
+// boundary vertex, as the double-layer walks).  A query on triangle
+// query_prim is boundary vertex 1 with weight 1.  One thread per walk.
+template <bool DEBUG>
+__global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams p)
+{
+    const StreamKey key{p.key0, p.key1};
+    const int64_t total = p.Q * (int64_t)p.N;
+    const double phi = (double)p.phi;
+    const double rmin = 1e-12 * p.L;
+    int err = 0;
+    int stack[kStackSize];
+    int hits[kMaxHits];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = idx / p.N;
+        const uint32_t q = p.q_base + (uint32_t)qi;
+        const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
+        double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+        int32_t* lm = DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr;
+        if (DEBUG && lm)
+            for (int k = 0; k < p.M; ++k) lm[k] = -1;
+        int self = -1, k0 = 0, wflag = 0;
+        if (p.query_prim) {
+            const int32_t prim = p.query_prim[qi];
+            if (prim >= 0 && prim < p.T) {
+                self = p.inv_order[prim];
+                k0 = 1;
+            }
+        }
+        double S = 0.0, P = 1.0;
+        for (int k = k0; k <= p.M; ++k) {
+            // source at vertex k
+            const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
+            const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
+            const double rl = sqrt(rx * rx + ry * ry + rz * rz);
+            if (rl >= rmin) {
+                const double f = sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n);
+                double c = (k == 0) ? phi : 2.0 * phi;
+                if (k == p.M) c *= 0.5;
+                S = fma(P * c * p.area / (kFourPi * rl), f, S);
+            }
+            if (k == p.M) break;
+            // line from vertex k to vertex k + 1
+            const double3 d = line_axis(key, q, w, (uint32_t)k);
+            const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
+                                       make_float3((float)d.x, (float)d.y, (float)d.z));
+            const float Tthr = p.edge_thr_L * fabsf(L.Sz);
+            Trav t;
+            trav_init(t);
+            uint32_t nn = 0, nt = 0;
+            trace_wide<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+                                     p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn,
+                                     nt, err, p.iter_limit);
+            wflag |= t.flag;
+            if (DEBUG && lm) lm[k] = t.m;
+            if (t.m == 0) break;
+            const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
+            const Refined r = refine_hit(p.tv, pos, x, d);
+            const double ms = (double)t.m * (double)r.s;
+            P *= (k == 0) ? 0.5 * phi * ms : phi * ms;
+            x = r.y;
+            self = pos;
+        }
+        p.per_walk[idx] = S;
+        if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
+    }
+    if (err) atomicOr(p.error_word, err);
 }
 
 // One warp per query: mean and unbiased variance in a fixed order.
@@ -326,6 +420,18 @@ int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s)
         k_sl_walks<true><<<grid_for((const void*)k_sl_walks<true>, threads, 0, work), threads, 0, s>>>(p);
     else
         k_sl_walks<false><<<grid_for((const void*)k_sl_walks<false>, threads, 0, work), threads, 0, s>>>(p);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_nd_walks(const WalkParams& p, bool debug, cudaStream_t s)
+{
+    const int threads = 128;
+    const int64_t work = p.Q * (int64_t)p.N;
+    if (debug)
+        k_nd_walks<true><<<grid_for((const void*)k_nd_walks<true>, threads, 0, work), threads, 0, s>>>(p);
+    else
+        k_nd_walks<false><<<grid_for((const void*)k_nd_walks<false>, threads, 0, work), threads, 0, s>>>(p);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }

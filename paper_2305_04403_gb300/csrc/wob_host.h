@@ -53,6 +53,7 @@ void free_bvh(BvhDev& b);
 // walk.cu
 int launch_dl_walks(const WalkParams& p, bool counted, bool debug, cudaStream_t s);
 int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s);
+int launch_nd_walks(const WalkParams& p, bool debug, cudaStream_t s);
 int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
                   cudaStream_t s);
 int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum,
