@@ -43,17 +43,22 @@ GRAZE = 1e-4
 
 
 def build(force: bool = False) -> str:
-    """Compile ``wob_oracle.c`` into ``oracle/_build/liboracle.so``."""
-    os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    """Compile ``wob_oracle.c`` into ``oracle/_build/liboracle.so``.  With
+    the environment variable ORACLE_PLANT=k (tests of the pins only) a
+    variant with planted mistake k is built into ``oracle/_build/plant_k``."""
+    plant = int(os.environ.get("ORACLE_PLANT", "0"))
+    out_dir = _OUT_DIR if plant == 0 else os.path.join(_OUT_DIR, f"plant_{plant}")
+    lib_path = os.path.join(out_dir, "liboracle.so")
+    os.makedirs(out_dir, exist_ok=True)
+    if (not force and os.path.exists(lib_path)
+            and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)):
+        return lib_path
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           f"-DORACLE_PLANT={plant}", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 class _Data(ctypes.Structure):

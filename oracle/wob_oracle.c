@@ -47,6 +47,17 @@
 
 #define ORACLE_PI 3.14159265358979323846
 
+/* Test infrastructure: a nonzero ORACLE_PLANT compiles one known mistake
+ * into the oracle so that a test can show its pins catch it (1: no half on
+ * the last double-layer term; 2: first double-layer weight negated; 3:
+ * double-layer recursion sign flipped; 4: hit sign s negated; 5: Robin term
+ * of the single layer with the wrong sign; 6: direct-Neumann first line
+ * without the 1/2; 7: direct-Neumann last source not halved).  0 (the
+ * default) is the oracle. */
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+
 enum { PURPOSE_DIR = 0, PURPOSE_HIT = 1, PURPOSE_AREA = 2 };
 enum { KIND_DIRICHLET_DL = 0, KIND_NEUMANN_SL = 1, KIND_ROBIN_SL = 2 };
 enum { DATA_VERTEX_P1 = 0, DATA_POLY = 1, DATA_POINT = 2 };
@@ -365,6 +376,9 @@ static void trace_line(const mesh_t *M, const double o[3], const double d[3], in
         double t = dot3(N, A) / dn;
         if (fabs(t) < tauL) r->flag = 1;
         int s = ((t > 0.0) == (dn > 0.0)) ? 1 : -1;
+#if ORACLE_PLANT == 4
+        s = -s;
+#endif
         r->m += 1;
         r->sum_s += s;
         uint32_t x[4];
@@ -431,10 +445,18 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
             W0 = 0.5 * (double)r.m * (double)r.s;
         else
             P *= -(double)phi * (double)r.m * (double)r.s;
+#if ORACLE_PLANT == 2
+        if (k == 0) W0 = -W0;
+#elif ORACLE_PLANT == 3
+        if (k > 0) P = -P;
+#endif
         /* line k reaches vertex k + 1 of the walk (density walks: vertex 1 is x0) */
         double n[3] = { 0.0, 0.0, 0.0 };
         double g = boundary_data(D, M, r.prim, r.y, r.b, n, KIND_DIRICHLET_DL, 0.0);
         double c = (k == Mlen - 1) ? (double)phi : 2.0 * (double)phi;
+#if ORACLE_PLANT == 1
+        c = 2.0 * (double)phi;
+#endif
         S += P * c * g;
         A += fabs(P * c * g);
         x[0] = r.y[0]; x[1] = r.y[1]; x[2] = r.y[2];
@@ -496,6 +518,9 @@ static double sl_walk(const mesh_t *M, const oracle_data *D, int kind, double al
         } else {
             double w = dot3(r, nx) / (four_pi * rl * rl * rl);
             if (kind == KIND_ROBIN_SL) w += alpha / (four_pi * rl);
+#if ORACLE_PLANT == 5
+            if (kind == KIND_ROBIN_SL) w -= 2.0 * alpha / (four_pi * rl);
+#endif
             P *= -2.0 * (double)phi * M->area * w;
         }
         double N[3], n[3];
@@ -554,7 +579,9 @@ static double nd_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
             n[0] = N[0] / nl; n[1] = N[1] / nl; n[2] = N[2] / nl;
             double f = boundary_data(D, M, j, y, b, n, KIND_NEUMANN_SL, 0.0);
             double c = (k == 0) ? (double)phi : 2.0 * (double)phi;
+#if ORACLE_PLANT != 7
             if (k == Mlen) c *= 0.5;
+#endif
             double term = P * c * M->area * f / (four_pi * rl);
             S += term;
             A += fabs(term);
@@ -569,7 +596,11 @@ static double nd_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
         if (lr.flag) *flag = 1;
         if (lr.m == 0) break;
         const double ms = (double)lr.m * (double)lr.s;
+#if ORACLE_PLANT == 6
+        P *= (double)phi * ms;
+#else
         P *= (k == 0) ? 0.5 * (double)phi * ms : (double)phi * ms;
+#endif
         x[0] = lr.y[0]; x[1] = lr.y[1]; x[2] = lr.y[2];
         exclude = lr.prim;
     }
