@@ -438,6 +438,51 @@ def run_nd(args):
     }
 
 
+def run_grad(args):
+    """The default workload (star L6 slice, 1,024 walks, M = 16) through
+    wob_solve_grad: value and gradient from the same walks (Sec. 4.1.3).  A
+    step is one solve; a path vertex is one line query (the same count as
+    the default workload, from the counting walks)."""
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    torch.cuda.set_device(0)
+    v, f, q = _workload()
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    prob = wob.Problem(bvh, kind=wob.DIRICHLET_DL, side=1, data_mode=wob.DATA_POINT, x0=X0)
+    qd = torch.from_numpy(q).cuda()
+    _, _, st = wob.solve_counted(prob, qd, WALKS, MAX_LEN, seed=SEED)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        wob.solve_grad(prob, qd, WALKS, MAX_LEN, seed=SEED)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            wob.solve_grad(prob, qd, WALKS, MAX_LEN, seed=SEED)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    return {
+        "metric": METRIC, "value": st["lines"] * args.steps / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 geometry / f64 accumulation",
+        "data": "synthetic (seeded star mesh, slice queries)",
+        "config": {"workload": f"star-shaped icosphere L6, z=0 slice Q={len(q)}, {WALKS} walks, "
+                               f"M={MAX_LEN}: value + gradient from the same walks",
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "clocks": clk.summary(), "gpu_launches": 5 * args.steps,
+    }
+
+
 def run_cv(args):
     """Learned control variate vs plain WoB: time to RMSE 1e-3 against the
     exact solution on the icosphere-L3 mesh (1,280 triangles) with
@@ -669,7 +714,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
-    ap.add_argument("--workload", default="star", choices=["star", "batched", "cv", "sl", "nd"])
+    ap.add_argument("--workload", default="star",
+                    choices=["star", "batched", "cv", "sl", "nd", "grad"])
     ap.add_argument("--sl-queries", type=int, default=131072)
     ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
     ap.add_argument("--cv-queries", type=int, default=65536,
@@ -692,6 +738,8 @@ def main():
         line = run_sl(args)
     elif args.workload == "nd":
         line = run_nd(args)
+    elif args.workload == "grad":
+        line = run_grad(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -220,6 +220,23 @@ int wob_solve_debug(const wob_problem *prob, const float *queries, const int32_t
                     int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
                     double *var, const wob_debug_out *dbg, void *stream);
 
+/*
+ * Value and gradient of u at Q points off the boundary from the same walks
+ * (Sec. 4.1.3, path reuse): only the first step's weight changes, from
+ * -dG/dn_y / p = (m/2) s to -grad_x dG/dn_y / p = (m/2) s times
+ * -(n - 3 (w . n) w) / (r (w . n)), with w = (x1 - x0) / r and n the normal
+ * at the first hit (App. A).  The gradient weight grows as 1 / (w . n) at
+ * grazing hits (a heavy-tailed estimator, as the paper observes near the
+ * boundary).  WOB_DIRICHLET_DL only.  est, var: device, Q doubles;
+ * grad_est, grad_var: device, 3 x Q doubles, component-major (component c of
+ * query q at [c * Q + q]); per_walk_grad: optional device 3 x Q x walks
+ * (component-major) per-walk gradients.  Allocates Q * walks * 4 doubles of
+ * scratch on `stream`.
+ */
+int wob_solve_grad(const wob_problem *prob, const float *queries, int64_t Q, int32_t walks,
+                   int32_t max_len, uint64_t seed, double *est, double *var, double *grad_est,
+                   double *grad_var, double *per_walk_grad, void *stream);
+
 /* As wob_solve, counting traversal work into *stats (synchronises). */
 int wob_solve_counted(const wob_problem *prob, const float *queries, const int32_t *query_prim,
                       int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,

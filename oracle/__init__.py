@@ -89,10 +89,10 @@ def _load():
                                                P, P, P, P, P, P, P, ctypes.c_int]
             lib.oracle_trace_lines.restype = ctypes.c_int
             lib.oracle_dl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, P, P, I64,
-                                            I64, I64, I32, I32, U64, U32, D, D, P, P, P, P,
+                                            I64, I64, I32, I32, U64, U32, D, D, P, P, P, P, P,
                                             ctypes.c_int]
             lib.oracle_dl_walks.restype = ctypes.c_int
-            lib.oracle_nd_walks.argtypes = lib.oracle_dl_walks.argtypes
+            lib.oracle_nd_walks.argtypes = lib.oracle_dl_walks.argtypes[:-2] + [ctypes.c_int]
             lib.oracle_nd_walks.restype = ctypes.c_int
             lib.oracle_sl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, D, I32,
                                             P, I64, I64, I64, I32, I32, U64, U32, P, P,
@@ -225,12 +225,13 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
              phi: int = 1, mode: int = DATA_POLY, vertex_data=None, poly=None, x0=None,
              scale: float = 1.0, q_offset: int = 0, walk_begin: int = 0, tau: float = TAU,
              graze: float = GRAZE, want_lines: bool = False, nthreads: int = 0,
-             query_prim=None) -> dict:
+             query_prim=None, want_grad: bool = False) -> dict:
     """Double-layer Dirichlet walks; with query_prim (the triangle each query
     lies on) the walks start on the boundary and estimate the density nu
     there.  Returns per_walk (Q,N), flag (Q,N),
     abs_terms (Q,N: sum over the walk's terms of |term|, the scale of its
-    rounding error) and, with want_lines, line_m (Q,N,M)."""
+    rounding error), with want_lines line_m (Q,N,M) and with want_grad the
+    per-walk gradient estimates grad (3,Q,N) of the same walks."""
     v = _c(verts, np.float32)
     t = _c(tris, np.int32)
     q = _c(queries, np.float32).reshape(-1, 3)
@@ -241,17 +242,20 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     line_m = np.empty((Q, walks, max_len), np.int32) if want_lines else None
     abs_terms = np.empty((Q, walks), np.float64)
     qp = None if query_prim is None else _c(query_prim, np.int32)
+    grad = np.empty((3, Q, walks), np.float64) if want_grad else None
     rc = _load().oracle_dl_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
                                  _p(q), _p(qp), Q, q_offset, walk_begin, walks, max_len, seed,
                                  problem,
                                  tau, graze, _p(per_walk), _p(flag), _p(line_m), _p(abs_terms),
-                                 nthreads)
+                                 _p(grad), nthreads)
     del keep
     if rc != 0:
         raise RuntimeError("oracle_dl_walks failed")
     out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
     if want_lines:
         out["line_m"] = line_m
+    if want_grad:
+        out["grad"] = grad
     return out
 
 

@@ -411,11 +411,31 @@ static void trace_line(const mesh_t *M, const double o[3], const double d[3], in
 /* start_prim >= 0: the walk starts ON the boundary, at x0 on that triangle,
  * and estimates the density nu(x0) (Eq. indirect_double_boundary_reordered2):
  * x0 is vertex 1 (first weight 1), and M - 1 lines follow. */
+/* Gradient weight of the first step (Sec. 4.1.3): the first line's weight
+ * -dG/dn_y / p = (m/2) s becomes -grad_x dG/dn_y / p, with
+ * grad_x dG/dn_y(x, y) = (n - 3 (w . n) w) / (4 pi r^3), w = (y - x) / r
+ * (App. A), i.e. (m/2) s times -(n - 3 (w . n) w) / (r (w . n)).  Returns
+ * that last factor. */
+static void grad_factor(const mesh_t *M, int64_t prim, const double x[3], const double y[3],
+                        double out[3])
+{
+    double N[3], n[3], w[3];
+    tri_normal(M, prim, N);
+    double nl = norm3(N);
+    n[0] = N[0] / nl; n[1] = N[1] / nl; n[2] = N[2] / nl;
+    sub3(y, x, w);
+    double r = norm3(w);
+    w[0] /= r; w[1] /= r; w[2] /= r;
+    double wn = dot3(w, n);
+    for (int c = 0; c < 3; ++c) out[c] = -(n[c] - 3.0 * wn * w[c]) / (r * wn);
+}
+
 static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const double x0[3],
                       int64_t start_prim, uint32_t q, uint32_t walk, int32_t Mlen,
                       uint64_t seed, uint32_t problem, double tauL, double graze,
-                      uint8_t *flag, int32_t *line_m, double *abs_terms)
+                      uint8_t *flag, int32_t *line_m, double *abs_terms, double grad[3])
 {
+    double gf[3] = { 0.0, 0.0, 0.0 };
     double x[3] = { x0[0], x0[1], x0[2] };
     int64_t exclude = -1;
     double S = 0.0, P = 1.0, W0 = 0.0, A = 0.0;
@@ -441,10 +461,12 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
         if (line_m) line_m[k] = r.m;
         if (r.flag) *flag = 1;
         if (r.m == 0) break;
-        if (k == 0)
+        if (k == 0) {
             W0 = 0.5 * (double)r.m * (double)r.s;
-        else
+            if (grad) grad_factor(M, r.prim, x, r.y, gf);
+        } else {
             P *= -(double)phi * (double)r.m * (double)r.s;
+        }
 #if ORACLE_PLANT == 2
         if (k == 0) W0 = -W0;
 #elif ORACLE_PLANT == 3
@@ -463,6 +485,8 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
         exclude = r.prim;
     }
     *abs_terms = fabs(W0) * A;
+    if (grad)
+        for (int c = 0; c < 3; ++c) grad[c] = gf[c] * W0 * S;
     return W0 * S;
 }
 
@@ -738,7 +762,7 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
                     int64_t q_offset, int64_t walk_begin, int32_t N, int32_t Mlen,
                     uint64_t seed, uint32_t problem, double tau, double graze,
                     double *per_walk, uint8_t *walk_flag, int32_t *line_m, double *abs_terms,
-                    int nthreads)
+                    double *per_walk_grad, int nthreads)
 {
     mesh_t M;
     if (mesh_init(&M, verts, V, tris, T, 0)) return -1;
@@ -756,10 +780,13 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
         }
         uint8_t f;
         double at;
+        double g3[3];
         per_walk[i] = dl_walk(&M, D, phi, x0, query_prim ? query_prim[qi] : -1,
                               (uint32_t)(q_offset + qi),
                               (uint32_t)(walk_begin + w), Mlen, seed, problem, tauL, graze, &f, lm,
-                              &at);
+                              &at, per_walk_grad ? g3 : NULL);
+        if (per_walk_grad)
+            for (int c = 0; c < 3; ++c) per_walk_grad[c * total + i] = g3[c];
         if (walk_flag) walk_flag[i] = f;
         if (abs_terms) abs_terms[i] = at;
     }

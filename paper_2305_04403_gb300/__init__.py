@@ -139,6 +139,8 @@ def load_library() -> ctypes.CDLL:
                                 ctypes.c_int),
             "wob_solve_density": ([ctypes.POINTER(_Problem), P, P, I64, I32, I32, U64, P, P, P],
                                   ctypes.c_int),
+            "wob_solve_grad": ([ctypes.POINTER(_Problem), P, I64, I32, I32, U64, P, P, P, P, P, P],
+                               ctypes.c_int),
             "wob_mlp_num_params": ([], ctypes.c_int),
             "wob_mlp_init": ([P, U64, P], ctypes.c_int),
             "wob_mlp_forward": ([P, P, I64, P, P], ctypes.c_int),
@@ -390,6 +392,27 @@ def solve_noalloc(problem: Problem, queries, walks: int, max_len: int, seed: int
                                             max_len, seed, _ptr(est), _ptr(var),
                                             _stream(stream)))
     return est, var
+
+
+def solve_grad(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
+               per_walk: bool = False, stream=None) -> dict:
+    """wob_solve_grad: est, var (Q,), grad_est, grad_var (3, Q) and, with
+    per_walk, the per-walk gradients (3, Q, walks) of the same walks."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    Q = q.shape[0]
+    out = dict(est=torch.empty(Q, dtype=torch.float64, device="cuda"),
+               var=torch.empty(Q, dtype=torch.float64, device="cuda"),
+               grad_est=torch.empty((3, Q), dtype=torch.float64, device="cuda"),
+               grad_var=torch.empty((3, Q), dtype=torch.float64, device="cuda"))
+    if per_walk:
+        out["grad"] = torch.empty((3, Q, walks), dtype=torch.float64, device="cuda")
+    pc = problem._c()
+    _check(load_library().wob_solve_grad(ctypes.byref(pc), _ptr(q), Q, walks, max_len, seed,
+                                         _ptr(out["est"]), _ptr(out["var"]), _ptr(out["grad_est"]),
+                                         _ptr(out["grad_var"]), _ptr(out.get("grad")),
+                                         _stream(stream)))
+    return out
 
 
 def solve_density(problem: Problem, points, prims, walks: int, max_len: int, seed: int = 0,

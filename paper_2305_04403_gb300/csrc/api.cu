@@ -407,6 +407,48 @@ int wob_solve_debug(const wob_problem* prob, const float* queries, const int32_t
                         nullptr, nullptr, dbg, nullptr, (cudaStream_t)stream, density);
 }
 
+int wob_solve_grad(const wob_problem* prob, const float* queries, int64_t Q, int32_t walks,
+                   int32_t max_len, uint64_t seed, double* est, double* var, double* grad_est,
+                   double* grad_var, double* per_walk_grad, void* stream)
+{
+    clear_error();
+    WOB_TRY(check_problem(prob));
+    WOB_TRY(check_sizes(Q, 0, walks, max_len));
+    if (prob->kind != WOB_DIRICHLET_DL) {
+        set_error("wob_solve_grad: gradients are implemented for WOB_DIRICHLET_DL");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    if (walks < 2 || (Q > 0 && (!queries || !est || !var || !grad_est || !grad_var))) {
+        set_error("wob_solve_grad: walks < 2 or a NULL output");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (Q == 0) return WOB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    WalkParams p;
+    fill_params(p, prob, queries, nullptr, Q, 0, walks, max_len, seed);
+    Scratch sc;
+    sc.s = s;
+    const int64_t W = Q * (int64_t)walks;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.per_walk, W * sizeof(double), s));
+    double* g = per_walk_grad;
+    double* g_owned = nullptr;
+    if (!g) {
+        WOB_CUDA_TRY(cudaMallocAsync((void**)&g_owned, 3 * W * sizeof(double), s));
+        g = g_owned;
+    }
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(Control), s));
+    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(Control), s));
+    p.tile_counter = &sc.err->next_tile;
+    p.per_walk = sc.per_walk;
+    p.per_walk_grad = g;
+    int rc = run_walks(p, nullptr, false, s, &sc.err->err);
+    if (rc == WOB_OK) rc = launch_reduce(sc.per_walk, Q, walks, est, var, s);
+    for (int c = 0; c < 3 && rc == WOB_OK; ++c)
+        rc = launch_reduce(g + c * W, Q, walks, grad_est + c * Q, grad_var + c * Q, s);
+    if (g_owned) cudaFreeAsync(g_owned, s);
+    return rc;
+}
+
 int wob_solve_counted(const wob_problem* prob, const float* queries, const int32_t* query_prim,
                       int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double* est,
                       double* var, wob_stats* stats, void* stream)

@@ -37,13 +37,13 @@ constexpr double kFourPi = 12.566370614359172953850573533118;
 // together share the fetches of the upper tree levels; variants that broke
 // this (persistent lanes refilled from a global counter, or a wavefront of
 // separate traversal and FP64-update kernels) measured 8-18% slower.
-template <bool COUNT, bool DEBUG>
+template <bool COUNT, bool DEBUG, bool GRAD = false>
 __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams p)
 {
     const StreamKey key{p.key0, p.key1};
     const int64_t total = p.Q * (int64_t)p.N;
     const DLGeom G{p.nodes, p.tv, p.iter_limit, p.edge_thr_L, p.tauL, p.graze};
-    __shared__ double slots[8 * 128];
+    __shared__ double slots[(GRAD ? 11 : 8) * 128];
     const WalkSlot ws{slots + threadIdx.x, 128};
     int err = 0;
     int stack[kStackSize];
@@ -68,9 +68,15 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
             const int32_t prim = p.query_prim[qi];
             start = (prim >= 0 && prim < p.T) ? p.inv_order[prim] : -1;
         }
-        p.per_walk[idx] = dl_walk<COUNT, DEBUG>(G, p.data, (double)p.phi, p.M, key, q, w, x, start,
-                                                ws, stack, hits, err, wflag,
-                                                DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c);
+        const double v = dl_walk<COUNT, DEBUG, GRAD>(
+            G, p.data, (double)p.phi, p.M, key, q, w, x, start, ws, stack, hits, err, wflag,
+            DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c);
+        p.per_walk[idx] = v;
+        if (GRAD) {  // gradient of the same walk: first-step factor x walk value
+            p.per_walk_grad[idx] = ws.get(8) * v;
+            p.per_walk_grad[total + idx] = ws.get(9) * v;
+            p.per_walk_grad[2 * total + idx] = ws.get(10) * v;
+        }
         if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
     }
     if (err) atomicOr(p.error_word, err);
@@ -398,7 +404,10 @@ int launch_dl_walks(const WalkParams& p, bool counted, bool debug, cudaStream_t 
 {
     const int threads = 128;
     const int64_t work = p.Q * (int64_t)p.N;
-    if (counted) {
+    if (p.per_walk_grad) {
+        k_dl_walks<false, false, true><<<grid_for((const void*)k_dl_walks<false, false, true>,
+                                                  threads, 0, work), threads, 0, s>>>(p);
+    } else if (counted) {
         k_dl_walks<true, true><<<grid_for((const void*)k_dl_walks<true, true>, threads, 0, work),
                                  threads, 0, s>>>(p);
     } else if (debug) {

@@ -518,6 +518,35 @@ struct WalkSlot {
     __device__ __forceinline__ void set(int j, double v) const { base[j * stride] = v; }
 };
 
+// Gradient weight of the first step (Sec. 4.1.3): the first line's weight
+// -dG/dn_y / p = (m/2) s becomes -grad_x dG/dn_y / p, with
+// grad_x dG/dn_y(x, y) = (n - 3 (w . n) w) / (4 pi r^3), w = (y - x) / r
+// (App. A): (m/2) s times -(n - 3 (w . n) w) / (r (w . n)), the factor
+// returned here (FP64, normal from the leaf triangle's vertices).
+__device__ __forceinline__ double3 grad_factor(const float4* __restrict__ tv, int pos, double3 x,
+                                               double3 y)
+{
+    const float4 a4 = __ldg(tv + 3 * pos + 0);
+    const float4 b4 = __ldg(tv + 3 * pos + 1);
+    const float4 c4 = __ldg(tv + 3 * pos + 2);
+    const double e1x = (double)b4.x - a4.x, e1y = (double)b4.y - a4.y, e1z = (double)b4.z - a4.z;
+    const double e2x = (double)c4.x - a4.x, e2y = (double)c4.y - a4.y, e2z = (double)c4.z - a4.z;
+    double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const double nl = sqrt(nx * nx + ny * ny + nz * nz);
+    nx /= nl;
+    ny /= nl;
+    nz /= nl;
+    double wx = y.x - x.x, wy = y.y - x.y, wz = y.z - x.z;
+    const double r = sqrt(wx * wx + wy * wy + wz * wz);
+    wx /= r;
+    wy /= r;
+    wz /= r;
+    const double wn = wx * nx + wy * ny + wz * nz;
+    const double k = -1.0 / (r * wn);
+    return make_double3(k * (nx - 3.0 * wn * wx), k * (ny - 3.0 * wn * wy),
+                        k * (nz - 3.0 * wn * wz));
+}
+
 // One double-layer walk from x (Sec. 4.1.1-4.1.2, ray sampling of Sec.
 // 4.4.1): per line, draw the axis, traverse (descend to a leaf, test it,
 // repeat), pick the hit (keys only when m > 1), refine it in FP64 and
@@ -526,14 +555,19 @@ struct WalkSlot {
 // that triangle (leaf position) and the walk estimates the density nu(x0)
 // (Eq. indirect_double_boundary_reordered2): x0 is vertex 1 with weight 1
 // and lines 1 .. M-1 follow.
-template <bool COUNT, bool DEBUG>
+template <bool COUNT, bool DEBUG, bool GRAD = false>
 __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, double phi, int M,
                                           StreamKey key, uint32_t q, uint32_t w, double3 x0,
                                           int start_pos, const WalkSlot& ws, int* stack,
                                           int* hits, int& err, int& wflag, int32_t* line_m,
                                           WalkCount& c)
 {
-    enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP };
+    enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP, GX, GY, GZ };  // GX..GZ: GRAD only
+    if (GRAD) {
+        ws.set(GX, 0.0);
+        ws.set(GY, 0.0);
+        ws.set(GZ, 0.0);
+    }
     ws.set(X0, x0.x);
     ws.set(X1, x0.y);
     ws.set(X2, x0.z);
@@ -581,7 +615,14 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
         const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
         double S = ws.get(SS), P = ws.get(PP);
+        const double3 xk = x;
         dl_accumulate(G.tv, D, pos, t.m, k, M, phi, x, d, S, P);
+        if (GRAD && k == 0 && start_pos < 0) {
+            const double3 gf = grad_factor(G.tv, pos, xk, x);
+            ws.set(GX, gf.x);
+            ws.set(GY, gf.y);
+            ws.set(GZ, gf.z);
+        }
         ws.set(X0, x.x);
         ws.set(X1, x.y);
         ws.set(X2, x.z);

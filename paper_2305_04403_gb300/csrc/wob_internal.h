@@ -95,6 +95,7 @@ struct WalkParams {
     float graze;
     // outputs
     double* per_walk;    // Q x N
+    double* per_walk_grad;  // 3 x Q x N gradient estimates (gradient kernels only)
     uint8_t* walk_flag;  // Q x N (optional)
     int32_t* line_m;     // Q x N x M (optional)
     unsigned long long* counters;  // [lines, nodes, tris, hits, flagged] (optional)

@@ -215,3 +215,26 @@ def test_sl_exterior_neumann_and_robin_closed_form(sphere3, M):
                     mode=O.DATA_POINT, x0=x0)
     est, var = O.reduce(pw)
     _check(est, var, n, multipole(x0, QOUT, lambda l: (2 * alpha - 1) / (2 * l + 1), M, False))
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+@pytest.mark.parametrize("poly,l", [(Z, 1), (X2Y2, 2)])
+def test_dl_gradient_closed_form(sphere3, M, poly, l):
+    """Gradient from the same walks (Sec. 4.1.3): only the first weight
+    changes, to -grad_x dG/dn_y / p, so the estimate's expectation is the
+    gradient of the truncated solution, ratio_M(b_l) grad h_l, mode by mode."""
+    v, f = sphere3
+    n = 40000
+    r = O.dl_walks(v, f, QIN, n, M, mode=O.DATA_POLY, poly=poly, tau=TAU, want_grad=True)
+    q = QIN.astype(float)
+    if l == 1:
+        gh = np.tile([0.0, 0.0, 1.0], (len(q), 1))
+    else:
+        gh = np.stack([2 * q[:, 0], -2 * q[:, 1], np.zeros(len(q))], 1)
+    pred = ratio(-1.0 / (2 * l + 1), M) * gh
+    for c in range(3):
+        est, var = O.reduce(r["grad"][c])
+        _check(est, var, n, pred[:, c])
+    # the value is unchanged by asking for the gradient
+    r0 = O.dl_walks(v, f, QIN, 64, M, mode=O.DATA_POLY, poly=poly, tau=TAU)
+    assert np.array_equal(r0["per_walk"], r["per_walk"][:, :64])
