@@ -108,6 +108,8 @@ extern "C" int wob_solve_noalloc(const wob_problem* prob, const float* queries,
     WOB_CUDA_TRY(cudaMemsetAsync(check, 0, 4 * sizeof(int), s));  // both must start at zero
     if (p.kind == WOB_DIRICHLET_DL)
         WOB_TRY(launch_dl_walks(p, false, false, s));
+    else if (p.kind == WOB_NEUMANN_DIRECT)
+        WOB_TRY(launch_nd_walks(p, false, s));
     else
         WOB_TRY(launch_sl_walks(p, false, s));
     return launch_reduce(values, Q, walks, est, var, s);

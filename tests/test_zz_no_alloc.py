@@ -65,6 +65,23 @@ def test_noalloc_matches_wob_solve_twice(wob):
         assert torch.allclose(var, var_ref, rtol=1e-12, atol=tol)
 
 
+def test_noalloc_direct_neumann_matches(wob):
+    """Every kind takes its own walk kernel here too (the direct-BIE Neumann
+    walks, not the single-layer ones)."""
+    v, f = I.icosphere(2)
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh)
+    prob = wob.Problem(bvh, kind=wob.NEUMANN_DIRECT, side=1, data_mode=wob.DATA_POLY,
+                       poly=(0, 0, 0, 1, 0, 0, 0, 0, 0, 0))
+    q = torch.from_numpy(I.ball_queries(96, 0.8, 6)).cuda()
+    for seed in (2, 3):
+        est_ref, var_ref = wob.solve(prob, q, 64, 3, seed=seed)
+        rc, est, var = _noalloc(wob, prob, q, 64, 3, seed)
+        torch.cuda.synchronize()
+        assert rc == 0
+        assert torch.allclose(est, est_ref, rtol=0, atol=1e-12 * est_ref.abs().max().item())
+
+
 def test_noalloc_single_layer_matches(wob):
     v, f = I.icosphere(2)
     mesh = wob.build_mesh(v, f)
