@@ -53,10 +53,17 @@ typedef enum {
     WOB_DIRICHLET_DL = 0,   /* Dirichlet data, double-layer potential (Sec. 4.1) */
     WOB_NEUMANN_SL = 1,     /* Neumann data, single-layer potential (Sec. 4.3) */
     WOB_ROBIN_SL = 2,       /* Robin data, single-layer potential (Sec. 4.3) */
-    WOB_NEUMANN_DIRECT = 3  /* Neumann data, direct boundary integral equation
+    WOB_NEUMANN_DIRECT = 3, /* Neumann data, direct boundary integral equation
                                (Sec. 4.2): lines for the dG/dn_y term, one
                                area-uniform point per vertex for the G q term */
+    WOB_MIXED_SL = 4        /* a Dirichlet, Neumann or Robin condition per
+                               triangle (bc_type), single-layer potential;
+                               Dirichlet parts through mu = mu - k S mu + k u_D
+                               sampled with the branch probability p_k (Sec. 4.3) */
 } wob_kind;
+
+/* Boundary condition of a triangle in WOB_MIXED_SL problems. */
+typedef enum { WOB_BC_DIRICHLET = 0, WOB_BC_NEUMANN = 1, WOB_BC_ROBIN = 2 } wob_bc;
 
 /* How the boundary data is given. */
 typedef enum {
@@ -103,6 +110,15 @@ typedef struct {
  *   tau:       near-degenerate line threshold relative to the mesh diagonal
  *              (0 = default 2e-6); lines passing closer than tau*L to a
  *              triangle edge are flagged in the debug outputs.
+ *   bc_type:   WOB_MIXED_SL only: device, T bytes (wob_bc, original triangle
+ *              order); data from the field h: u_D = h, q = dh/dn, Robin
+ *              dh/dn + alpha h (POLY or POINT mode).
+ *   k_mix, p_k: WOB_MIXED_SL only: the constant k > 0 of the Dirichlet parts
+ *              and the probability 0 < p_k < 1 of moving (the paper uses 4
+ *              and 2/3; on the unit sphere the series converges for k < 2).
+ *   ris:       single-layer kinds: 0 or 1 = area-uniform next points; 2..64 =
+ *              resampled importance sampling from `ris` uniform candidates
+ *              with target |kernel| (the paper uses 16).
  */
 typedef struct {
     wob_bvh bvh;
@@ -116,6 +132,10 @@ typedef struct {
     float scale;
     uint32_t problem;
     float tau;
+    const uint8_t *bc_type;
+    float k_mix;
+    float p_k;
+    int32_t ris;
 } wob_problem;
 
 /* Per-walk outputs for parity checks (each pointer device, may be NULL). */

@@ -33,6 +33,8 @@ _lib = None
 KIND_DIRICHLET_DL = 0
 KIND_NEUMANN_SL = 1
 KIND_ROBIN_SL = 2
+KIND_MIXED_SL = 4
+BC_DIRICHLET, BC_NEUMANN, BC_ROBIN = 0, 1, 2
 DATA_VERTEX_P1 = 0
 DATA_POLY = 1
 DATA_POINT = 2
@@ -96,7 +98,7 @@ def _load():
             lib.oracle_nd_walks.restype = ctypes.c_int
             lib.oracle_sl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, D, I32,
                                             P, I64, I64, I64, I32, I32, U64, U32, P, P,
-                                            ctypes.c_int]
+                                            P, D, D, I32, ctypes.c_int]
             lib.oracle_sl_walks.restype = ctypes.c_int
             lib.oracle_reduce.argtypes = [P, I64, I32, P, P]
             _lib = lib
@@ -295,9 +297,13 @@ def sl_walks(verts, tris, queries, walks: int, max_len: int, kind: int = KIND_NE
              alpha: float = 0.0, seed: int = 0, problem: int = 0, phi: int = 1,
              mode: int = DATA_POINT, vertex_data=None, poly=None, x0=None, scale: float = 1.0,
              q_offset: int = 0, walk_begin: int = 0, nthreads: int = 0,
-             want_abs: bool = False):
-    """Single-layer Neumann / Robin walks with area sampling; per_walk (Q,N)
-    (and, with want_abs, the per-walk sum of |term|)."""
+             want_abs: bool = False, bc_type=None, kmix: float = 0.0, pk: float = 0.0,
+             ris: int = 0):
+    """Single-layer Neumann / Robin / mixed walks; per_walk (Q,N) (and, with
+    want_abs, the per-walk sum of |term|).  Mixed (kind KIND_MIXED_SL):
+    bc_type (T,) uint8 condition per triangle, constant kmix and branch
+    probability pk of the Dirichlet parts.  ris > 1: resampled importance
+    sampling of the next point from ris uniform candidates."""
     v = _c(verts, np.float32)
     t = _c(tris, np.int32)
     q = _c(queries, np.float32).reshape(-1, 3)
@@ -305,9 +311,11 @@ def sl_walks(verts, tris, queries, walks: int, max_len: int, kind: int = KIND_NE
     data, keep = _data(mode, vertex_data, poly, x0, scale)
     per_walk = np.empty((Q, walks), np.float64)
     abs_terms = np.empty((Q, walks), np.float64)
+    bc = None if bc_type is None else _c(bc_type, np.uint8)
     rc = _load().oracle_sl_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), kind,
                                  alpha, phi, _p(q), Q, q_offset, walk_begin, walks, max_len,
-                                 seed, problem, _p(per_walk), _p(abs_terms), nthreads)
+                                 seed, problem, _p(per_walk), _p(abs_terms), _p(bc), kmix, pk,
+                                 ris, nthreads)
     del keep
     if rc != 0:
         raise RuntimeError("oracle_sl_walks failed")

@@ -58,8 +58,9 @@
 #define ORACLE_PLANT 0
 #endif
 
-enum { PURPOSE_DIR = 0, PURPOSE_HIT = 1, PURPOSE_AREA = 2 };
-enum { KIND_DIRICHLET_DL = 0, KIND_NEUMANN_SL = 1, KIND_ROBIN_SL = 2 };
+enum { PURPOSE_DIR = 0, PURPOSE_HIT = 1, PURPOSE_AREA = 2, PURPOSE_BRANCH = 4, PURPOSE_RIS = 5 };
+enum { KIND_DIRICHLET_DL = 0, KIND_NEUMANN_SL = 1, KIND_ROBIN_SL = 2, KIND_MIXED_SL = 4 };
+enum { BC_DIRICHLET = 0, BC_NEUMANN = 1, BC_ROBIN = 2 };
 enum { DATA_VERTEX_P1 = 0, DATA_POLY = 1, DATA_POINT = 2 };
 
 /* ------------------------------------------------------------------------ */
@@ -499,11 +500,12 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
 /* next point drawn uniformly by area (p = 1/|Gamma|), and the last vertex  */
 /* weighted phi f instead of 2 phi f (Sec. 4.1.2).                          */
 /* ------------------------------------------------------------------------ */
-static void area_sample(const mesh_t *M, uint64_t seed, uint32_t problem, uint32_t q,
-                        uint32_t walk, uint32_t step, int64_t *tri, double y[3], double b[3])
+static void area_sample_at(const mesh_t *M, uint64_t seed, uint32_t problem, uint32_t q,
+                           uint32_t walk, uint32_t step, uint32_t attempt, int64_t *tri,
+                           double y[3], double b[3])
 {
     uint32_t x[4];
-    stream_block(seed, problem, q, walk, step, PURPOSE_AREA, 0, 0, x);
+    stream_block(seed, problem, q, walk, step, PURPOSE_AREA, attempt, 0, x);
     double target = u53(x[0], x[1]) * M->area;
     /* first triangle whose inclusive prefix area exceeds the target */
     int64_t lo = 0, hi = M->T - 1;
@@ -522,41 +524,134 @@ static void area_sample(const mesh_t *M, uint64_t seed, uint32_t problem, uint32
     for (int c = 0; c < 3; ++c) y[c] = b[0] * v0[c] + b[1] * v1[c] + b[2] * v2[c];
 }
 
+static void area_sample(const mesh_t *M, uint64_t seed, uint32_t problem, uint32_t q,
+                        uint32_t walk, uint32_t step, int64_t *tri, double y[3], double b[3])
+{
+    area_sample_at(M, seed, problem, q, walk, step, 0, tri, y, b);
+}
+
+/* Unit normal of triangle j. */
+static void unit_normal(const mesh_t *M, int64_t j, double n[3])
+{
+    double N[3];
+    tri_normal(M, j, N);
+    double nl = norm3(N);
+    n[0] = N[0] / nl; n[1] = N[1] / nl; n[2] = N[2] / nl;
+}
+
+/* Transition kernel of the single-layer recursion from x (boundary
+ * condition bx, normal nx; bx < 0: the query, off the boundary) to y,
+ * without the 1/p of the sampling (Table 1; Sec. 4.3 for Dirichlet parts):
+ *   query:    G(x, y)                      (u = int G mu)
+ *   Neumann:  -2 phi dG/dn_x(x, y)
+ *   Robin:    -2 phi (dG/dn_x(x, y) + alpha G(x, y))
+ *   Dirichlet (moving branch): -(k / p_k) G(x, y)
+ * dG/dn_x(x, y) = (y - x) . n_x / (4 pi r^3).  Returns 0 for r < rmin. */
+static double sl_kernel(int bx, const double x[3], const double nx[3], const double y[3],
+                        int32_t phi, double alpha, double kmix, double pk, double rmin)
+{
+    double r[3];
+    sub3(y, x, r);
+    double rl = norm3(r);
+    if (rl < rmin) return 0.0;
+    const double four_pi = 4.0 * ORACLE_PI;
+    double G = 1.0 / (four_pi * rl);
+    if (bx < 0) return G;
+    if (bx == BC_DIRICHLET) return -(kmix / pk) * G;
+    double dgdn = dot3(r, nx) / (four_pi * rl * rl * rl);
+    if (bx == BC_NEUMANN) return -2.0 * (double)phi * dgdn;
+    double w = dgdn + alpha * G;
+#if ORACLE_PLANT == 5
+    w -= 2.0 * alpha * G;
+#endif
+    return -2.0 * (double)phi * w;
+}
+
+/* Single-layer walks (Table 1, Sec. 4.3): u(x0) = int G mu dA and, at a
+ * boundary point x with condition bx, mu(x) = int K(x, y) mu(y) dA + src(x):
+ *   Neumann   src = 2 phi q,            Robin src = 2 phi (q + alpha h),
+ *   Dirichlet src = k u_D, and mu(x) = mu(x) - k int G mu + k u_D sampled by
+ *   a branch: with probability p_k move (kernel -(k/p_k) G), otherwise stay
+ *   at x with weight 1 / (1 - p_k) (mixed problems, Sec. 4.3).
+ * The source of the last vertex is halved (Sec. 4.1.2).  bc (mixed problems
+ * only, else NULL) gives each triangle's condition; kind NEUMANN_SL /
+ * ROBIN_SL use that condition everywhere.  Next points: area-uniform
+ * (ris <= 1) or resampled importance sampling (Talbot et al. 2005): ris
+ * uniform candidates, one picked with probability proportional to |K|, the
+ * weight sign(K) (sum of |Gamma| |K| over the candidates) / ris. */
 static double sl_walk(const mesh_t *M, const oracle_data *D, int kind, double alpha, int32_t phi,
                       const double x0[3], uint32_t q, uint32_t walk, int32_t Mlen,
-                      uint64_t seed, uint32_t problem, double *abs_terms)
+                      uint64_t seed, uint32_t problem, double *abs_terms, const uint8_t *bc,
+                      double kmix, double pk, int32_t ris)
 {
     double x[3] = { x0[0], x0[1], x0[2] };
     double nx[3] = { 0.0, 0.0, 0.0 };
+    int bx = -1;
+    int64_t jx = -1;
     double S = 0.0, P = 1.0, W0 = 0.0, Aabs = 0.0;
-    const double four_pi = 4.0 * ORACLE_PI;
+    const double rmin = 1e-12 * M->L;
+    const int uniform_bc = kind == KIND_ROBIN_SL ? BC_ROBIN : BC_NEUMANN;
     for (int32_t k = 0; k < Mlen; ++k) {
         int64_t j;
-        double y[3], b[3], r[3];
-        area_sample(M, seed, problem, q, walk, (uint32_t)k, &j, y, b);
-        sub3(y, x, r);
-        double rl = norm3(r);
-        if (rl < 1e-12 * M->L) break; /* a zero-measure coincidence: empty sample */
-        if (k == 0) {
-            W0 = M->area / (four_pi * rl);
-        } else {
-            double w = dot3(r, nx) / (four_pi * rl * rl * rl);
-            if (kind == KIND_ROBIN_SL) w += alpha / (four_pi * rl);
-#if ORACLE_PLANT == 5
-            if (kind == KIND_ROBIN_SL) w -= 2.0 * alpha / (four_pi * rl);
-#endif
-            P *= -2.0 * (double)phi * M->area * w;
+        double y[3], b[3], ny[3];
+        double wfac;
+        int stay = 0;
+        if (bx == BC_DIRICHLET) {
+            uint32_t u[4];
+            stream_block(seed, problem, q, walk, (uint32_t)k, PURPOSE_BRANCH, 0, 0, u);
+            stay = u24(u[0]) >= pk;
         }
-        double N[3], n[3];
-        tri_normal(M, j, N);
-        double nl = norm3(N);
-        n[0] = N[0] / nl; n[1] = N[1] / nl; n[2] = N[2] / nl;
-        double f = boundary_data(D, M, j, y, b, n, kind, alpha);
-        double c = (k == Mlen - 1) ? (double)phi : 2.0 * (double)phi;
-        S += P * c * f;
-        Aabs += fabs(P * c * f);
+        if (stay) {
+            j = jx;
+            y[0] = x[0]; y[1] = x[1]; y[2] = x[2];
+            barycentric(M, j, y, b);
+            wfac = 1.0 / (1.0 - pk);
+        } else if (ris <= 1) {
+            area_sample(M, seed, problem, q, walk, (uint32_t)k, &j, y, b);
+            double r[3];
+            sub3(y, x, r);
+            if (norm3(r) < rmin) break; /* a zero-measure coincidence: empty sample */
+            wfac = M->area * sl_kernel(bx, x, nx, y, phi, alpha, kmix, pk, rmin);
+        } else {
+            double sumw = 0.0, wc[64];
+            for (int32_t c = 0; c < ris; ++c) {
+                int64_t jc;
+                double yc[3], bc3[3];
+                area_sample_at(M, seed, problem, q, walk, (uint32_t)k, (uint32_t)c, &jc, yc, bc3);
+                wc[c] = fabs(sl_kernel(bx, x, nx, yc, phi, alpha, kmix, pk, rmin));
+                sumw += wc[c];
+            }
+            if (!(sumw > 0.0)) break; /* every candidate has a zero kernel */
+            uint32_t u[4];
+            stream_block(seed, problem, q, walk, (uint32_t)k, PURPOSE_RIS, 0, 0, u);
+            double target = u53(u[0], u[1]) * sumw, acc = 0.0;
+            int32_t pick = ris - 1;
+            for (int32_t c = 0; c < ris; ++c) {
+                acc += wc[c];
+                if (acc > target) { pick = c; break; }
+            }
+            area_sample_at(M, seed, problem, q, walk, (uint32_t)k, (uint32_t)pick, &j, y, b);
+            double K = sl_kernel(bx, x, nx, y, phi, alpha, kmix, pk, rmin);
+            wfac = (K > 0.0 ? 1.0 : -1.0) * M->area * sumw / (double)ris;
+        }
+        if (k == 0) W0 = wfac; else P *= wfac;
+        unit_normal(M, j, ny);
+        int by = bc ? (int)bc[j] : uniform_bc;
+        double src;
+        if (by == BC_DIRICHLET) {
+            src = kmix * boundary_data(D, M, j, y, b, ny, KIND_DIRICHLET_DL, 0.0);
+        } else {
+            double f = boundary_data(D, M, j, y, b, ny,
+                                     by == BC_ROBIN ? KIND_ROBIN_SL : KIND_NEUMANN_SL, alpha);
+            src = 2.0 * (double)phi * f;
+        }
+        if (k == Mlen - 1) src *= 0.5;
+        S += P * src;
+        Aabs += fabs(P * src);
         x[0] = y[0]; x[1] = y[1]; x[2] = y[2];
-        nx[0] = n[0]; nx[1] = n[1]; nx[2] = n[2];
+        nx[0] = ny[0]; nx[1] = ny[1]; nx[2] = ny[2];
+        bx = by;
+        jx = j;
     }
     *abs_terms = fabs(W0) * Aabs;
     return W0 * S;
@@ -836,8 +931,11 @@ int oracle_sl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
                     const oracle_data *D, int32_t kind, double alpha, int32_t phi,
                     const float *queries, int64_t Q, int64_t q_offset, int64_t walk_begin,
                     int32_t N, int32_t Mlen, uint64_t seed, uint32_t problem,
-                    double *per_walk, double *abs_terms, int nthreads)
+                    double *per_walk, double *abs_terms, const uint8_t *bc, double kmix,
+                    double pk, int32_t ris, int nthreads)
 {
+    if (ris > 64 || (kind == KIND_MIXED_SL && (!bc || !(kmix > 0.0) || !(pk > 0.0 && pk < 1.0))))
+        return -1;
     mesh_t M;
     if (mesh_init(&M, verts, V, tris, T, 1)) return -1;
     int nt = set_threads(nthreads);
@@ -848,7 +946,8 @@ int oracle_sl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
         double x0[3] = { queries[3 * qi], queries[3 * qi + 1], queries[3 * qi + 2] };
         double at;
         per_walk[i] = sl_walk(&M, D, kind, alpha, phi, x0, (uint32_t)(q_offset + qi),
-                              (uint32_t)(walk_begin + w), Mlen, seed, problem, &at);
+                              (uint32_t)(walk_begin + w), Mlen, seed, problem, &at,
+                              kind == KIND_MIXED_SL ? bc : NULL, kmix, pk, ris);
         if (abs_terms) abs_terms[i] = at;
     }
     mesh_free(&M);

@@ -19,14 +19,16 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "NEUMANN_DIRECT", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
+    "DIRICHLET_DL", "NEUMANN_SL", "ROBIN_SL", "NEUMANN_DIRECT", "MIXED_SL", "BC_DIRICHLET",
+    "BC_NEUMANN", "BC_ROBIN", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
     "WobError", "Mesh", "BVH", "Problem", "Batch", "build_mesh", "build_bvh", "solve", "solve_range",
     "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "solve_density",
     "mlp_num_params", "mlp_forward", "mlp_train_step", "ControlVariate", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
 
-DIRICHLET_DL, NEUMANN_SL, ROBIN_SL, NEUMANN_DIRECT = 0, 1, 2, 3
+DIRICHLET_DL, NEUMANN_SL, ROBIN_SL, NEUMANN_DIRECT, MIXED_SL = 0, 1, 2, 3, 4
+BC_DIRICHLET, BC_NEUMANN, BC_ROBIN = 0, 1, 2
 DATA_VERTEX_P1, DATA_POLY, DATA_POINT = 0, 1, 2
 
 _ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "DEGENERATE_MESH",
@@ -60,7 +62,9 @@ class _Problem(ctypes.Structure):
                 ("alpha", ctypes.c_float), ("data_mode", ctypes.c_int32),
                 ("vertex_data", ctypes.c_void_p), ("poly", ctypes.c_float * 10),
                 ("x0", ctypes.c_float * 3), ("scale", ctypes.c_float),
-                ("problem", ctypes.c_uint32), ("tau", ctypes.c_float)]
+                ("problem", ctypes.c_uint32), ("tau", ctypes.c_float),
+                ("bc_type", ctypes.c_void_p), ("k_mix", ctypes.c_float), ("p_k", ctypes.c_float),
+                ("ris", ctypes.c_int32)]
 
 
 class _BatchParams(ctypes.Structure):
@@ -283,22 +287,32 @@ class Problem:
     scale: float = 1.0
     problem: int = 0
     tau: float = 0.0
+    bc_type: object = None              # device uint8 tensor (T,) for MIXED_SL
+    k_mix: float = 0.0
+    p_k: float = 0.0
+    ris: int = 0
     _keep: list = field(default_factory=list, repr=False)
 
     def _c(self) -> _Problem:
         import torch
         p = _Problem()
+        self._keep = []
         p.bvh = self.bvh.handle
         p.kind, p.side, p.alpha, p.data_mode = self.kind, self.side, self.alpha, self.data_mode
         if self.vertex_data is not None:
             vd = _dev(self.vertex_data, torch.float32)
-            self._keep = [vd]
+            self._keep.append(vd)
             p.vertex_data = vd.data_ptr()
         for i, c in enumerate(self.poly):
             p.poly[i] = float(c)
         for i, c in enumerate(self.x0):
             p.x0[i] = float(c)
         p.scale, p.problem, p.tau = self.scale, self.problem, self.tau
+        if self.bc_type is not None:
+            bc = _dev(self.bc_type, torch.uint8)
+            self._keep.append(bc)
+            p.bc_type = bc.data_ptr()
+        p.k_mix, p.p_k, p.ris = self.k_mix, self.p_k, self.ris
         return p
 
 

@@ -49,8 +49,18 @@ int check_problem(const wob_problem* prob)
         set_error("problem or problem->bvh is NULL");
         return WOB_ERR_INVALID_ARG;
     }
-    if (prob->kind < WOB_DIRICHLET_DL || prob->kind > WOB_NEUMANN_DIRECT) {
+    if (prob->kind < WOB_DIRICHLET_DL || prob->kind > WOB_MIXED_SL) {
         set_error("unknown kind %d", prob->kind);
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->kind == WOB_MIXED_SL &&
+        (!prob->bc_type || !(prob->k_mix > 0.0f) || !(prob->p_k > 0.0f && prob->p_k < 1.0f) ||
+         prob->data_mode == WOB_DATA_VERTEX_P1)) {
+        set_error("WOB_MIXED_SL needs bc_type, k_mix > 0, 0 < p_k < 1 and POLY or POINT data");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (prob->ris < 0 || prob->ris > kMaxRis) {
+        set_error("ris must be in [0, %d]", kMaxRis);
         return WOB_ERR_INVALID_ARG;
     }
     if (prob->side != 1 && prob->side != -1) {
@@ -109,6 +119,10 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     p.area = m.area;
     p.L = m.L;
     p.kind = prob->kind;
+    p.bc_type = prob->kind == WOB_MIXED_SL ? prob->bc_type : nullptr;
+    p.kmix = prob->k_mix;
+    p.pk = prob->p_k;
+    p.ris = prob->ris;
     p.phi = prob->side;
     p.alpha = prob->alpha;
     p.data.mode = prob->data_mode;

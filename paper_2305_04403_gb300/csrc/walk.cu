@@ -90,9 +90,10 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
 }
 
 // Data of the single-layer problems at y on triangle j (original order):
-// Neumann flux dh/dn or Robin data dh/dn + alpha h (P1: the vertex values).
+// with condition bc (wob_bc) the field h (Dirichlet), its normal derivative
+// dh/dn (Neumann) or dh/dn + alpha h (Robin); P1 mode: the vertex values.
 __device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double3 y, double b0,
-                                          double b1, double b2, double3 n)
+                                          double b1, double b2, double3 n, int bc)
 {
     const DataDev& D = p.data;
     if (D.mode == WOB_DATA_VERTEX_P1) {
@@ -116,11 +117,12 @@ __device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double
         gy = f * ry;
         gz = f * rz;
     }
+    if (bc == WOB_BC_DIRICHLET) return h;
     const double dhdn = n.x * gx + n.y * gy + n.z * gz;
-    return p.kind == WOB_ROBIN_SL ? dhdn + (double)p.alpha * h : dhdn;
+    return bc == WOB_BC_ROBIN ? dhdn + (double)p.alpha * h : dhdn;
 }
 
-// Area-uniform boundary point of stream (q, w, step): triangle j (original
+// Area-uniform boundary point of stream (q, w, step, attempt): triangle j (original
 // order) by inverse CDF of the areas (53-bit uniform), then a uniform point
 // on it (square-root warp), barycentrics b0..b2; n = the triangle's unit normal.
 struct AreaPoint {
@@ -130,10 +132,10 @@ struct AreaPoint {
 };
 
 __device__ __forceinline__ AreaPoint area_point(const WalkParams& p, StreamKey key, uint32_t q,
-                                                uint32_t w, uint32_t step)
+                                                uint32_t w, uint32_t step, uint32_t attempt = 0u)
 {
     AreaPoint a;
-    const u32x4 u = stream_block(key, q, w, step, kPurposeArea, 0u, 0u);
+    const u32x4 u = stream_block(key, q, w, step, kPurposeArea, attempt, 0u);
     const double target = u53(u.x, u.y) * p.area;
     int64_t lo = 0, hi = p.T - 1;
     while (lo < hi) {
@@ -158,6 +160,35 @@ __device__ __forceinline__ AreaPoint area_point(const WalkParams& p, StreamKey k
     return a;
 }
 
+// Transition kernel of the single-layer recursion from x (condition bx,
+// normal nx; bx < 0: the query) to y, without the 1/p of the sampling
+// (Table 1; Sec. 4.3 for the Dirichlet parts of mixed problems): G (query),
+// -2 phi dG/dn_x (Neumann), -2 phi (dG/dn_x + alpha G) (Robin), -(k/p_k) G
+// (Dirichlet, moving branch); dG/dn_x = (y - x) . n_x / (4 pi r^3).  0 for
+// r < rmin.
+__device__ __forceinline__ double sl_kernel(const WalkParams& p, int bx, double3 x, double3 nx,
+                                            double3 y, double rmin)
+{
+    const double rx = y.x - x.x, ry = y.y - x.y, rz = y.z - x.z;
+    const double rl = sqrt(rx * rx + ry * ry + rz * rz);
+    if (rl < rmin) return 0.0;
+    const double G = 1.0 / (kFourPi * rl);
+    if (bx < 0) return G;
+    if (bx == WOB_BC_DIRICHLET) return -((double)p.kmix / (double)p.pk) * G;
+    const double dgdn = (rx * nx.x + ry * nx.y + rz * nx.z) / (kFourPi * rl * rl * rl);
+    const double phi = (double)p.phi;
+    if (bx == WOB_BC_NEUMANN) return -2.0 * phi * dgdn;
+    return -2.0 * phi * (dgdn + (double)p.alpha * G);
+}
+
+// Single-layer walks (Table 1, Sec. 4.3), one thread per walk:
+// u(x0) = int G mu and mu(x) = int K(x, y) mu(y) + src(x), src = 2 phi q
+// (Neumann), 2 phi (q + alpha h) (Robin), k u_D (Dirichlet parts of mixed
+// problems, whose mu(x) = mu(x) - k S mu + k u_D is sampled by moving with
+// probability p_k or staying at x with weight 1 / (1 - p_k)).  The last
+// source is halved (Sec. 4.1.2).  Next points: area-uniform, or resampled
+// importance sampling (Talbot et al. 2005) from p.ris uniform candidates
+// with target |K|: weight sign(K) |Gamma| (sum of |K| over the candidates) / ris.
 template <bool DEBUG>
 __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
 {
@@ -166,6 +197,8 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
     const double phi = (double)p.phi;
     const double area = p.area;
     const double rmin = 1e-12 * p.L;
+    const int uniform_bc = p.kind == WOB_ROBIN_SL ? WOB_BC_ROBIN : WOB_BC_NEUMANN;
+    double wc[kMaxRis];
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t qi = idx / p.N;
@@ -174,26 +207,62 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
         const uint32_t w = (uint32_t)(p.walk_begin + wi);
         double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
         double3 nx = make_double3(0.0, 0.0, 0.0);
+        int bx = -1;
+        int64_t jx = -1;
         double S = 0.0, P = 1.0, W0 = 0.0;
         for (int k = 0; k < p.M; ++k) {
-            const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
-            const double3 y = a.y;
-            const double rx = y.x - x.x, ry = y.y - x.y, rz = y.z - x.z;
-            const double rl = sqrt(rx * rx + ry * ry + rz * rz);
-            if (rl < rmin) break;
-            if (k == 0) {
-                W0 = area / (kFourPi * rl);  // |Gamma| G
-            } else {
-                double wk = (rx * nx.x + ry * nx.y + rz * nx.z) / (kFourPi * rl * rl * rl);
-                if (p.kind == WOB_ROBIN_SL) wk += (double)p.alpha / (kFourPi * rl);
-                P *= -2.0 * phi * area * wk;
+            bool stay = false;
+            if (bx == WOB_BC_DIRICHLET) {
+                const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeBranch, 0u, 0u);
+                stay = u24(u.x) >= (double)p.pk;
             }
-            const double3 n = a.n;
-            const double f = sl_data(p, a.j, y, a.b0, a.b1, a.b2, n);
-            const double c = (k == p.M - 1) ? phi : 2.0 * phi;
-            S = fma(P * c, f, S);
-            x = y;
-            nx = n;
+            AreaPoint a;
+            double wfac;
+            if (stay) {
+                a.j = jx;
+                a.y = x;
+                a.n = nx;
+                a.b0 = a.b1 = a.b2 = 0.0;  // mixed problems take analytic data
+                wfac = 1.0 / (1.0 - (double)p.pk);
+            } else if (p.ris <= 1) {
+                a = area_point(p, key, q, w, (uint32_t)k);
+                const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
+                if (sqrt(rx * rx + ry * ry + rz * rz) < rmin) break;  // empty sample
+                wfac = area * sl_kernel(p, bx, x, nx, a.y, rmin);
+            } else {
+                double sumw = 0.0;
+                for (int c = 0; c < p.ris; ++c) {
+                    const AreaPoint ac = area_point(p, key, q, w, (uint32_t)k, (uint32_t)c);
+                    wc[c] = fabs(sl_kernel(p, bx, x, nx, ac.y, rmin));
+                    sumw += wc[c];
+                }
+                if (!(sumw > 0.0)) break;  // every candidate has a zero kernel
+                const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeRis, 0u, 0u);
+                const double target = u53(u.x, u.y) * sumw;
+                double acc = 0.0;
+                int pick = p.ris - 1;
+                for (int c = 0; c < p.ris; ++c) {
+                    acc += wc[c];
+                    if (acc > target) {
+                        pick = c;
+                        break;
+                    }
+                }
+                a = area_point(p, key, q, w, (uint32_t)k, (uint32_t)pick);
+                const double K = sl_kernel(p, bx, x, nx, a.y, rmin);
+                wfac = (K > 0.0 ? 1.0 : -1.0) * area * sumw / (double)p.ris;
+            }
+            if (k == 0) W0 = wfac; else P *= wfac;
+            const int by = p.bc_type ? (int)__ldg(p.bc_type + a.j) : uniform_bc;
+            double src = by == WOB_BC_DIRICHLET
+                             ? (double)p.kmix * sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by)
+                             : 2.0 * phi * sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by);
+            if (k == p.M - 1) src *= 0.5;
+            S = fma(P, src, S);
+            x = a.y;
+            nx = a.n;
+            bx = by;
+            jx = a.j;
         }
         p.per_walk[idx] = W0 * S;
         if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
@@ -242,7 +311,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
             const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
             const double rl = sqrt(rx * rx + ry * ry + rz * rz);
             if (rl >= rmin) {
-                const double f = sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n);
+                const double f = sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
                 double c = (k == 0) ? phi : 2.0 * phi;
                 if (k == p.M) c *= 0.5;
                 S = fma(P * c * p.area / (kFourPi * rl), f, S);

@@ -13,6 +13,9 @@ constexpr uint32_t kPurposeDir = 0;   // line axis draws
 constexpr uint32_t kPurposeHit = 1;   // hit-selection keys
 constexpr uint32_t kPurposeArea = 2;  // area-sampled boundary points
 constexpr uint32_t kPurposeInit = 3;  // initial network weights
+constexpr uint32_t kPurposeBranch = 4;  // move / stay on Dirichlet parts of mixed problems
+constexpr uint32_t kPurposeRis = 5;     // resampled importance sampling pick
+constexpr int kMaxRis = 64;             // candidates of one resampling
 constexpr int kStackSize = 64;        // traversal stack entries per line
 constexpr int kNoRef = INT32_MIN;     // empty traversal stack marker
 constexpr int64_t kMaxTriangles = (int64_t(1) << 28) - 2;
@@ -77,6 +80,9 @@ struct WalkParams {
     double L;
     // problem
     int kind;
+    const uint8_t* bc_type;  // mixed problems: condition per triangle (original order)
+    float kmix, pk;          // mixed problems: Dirichlet-part constant, move probability
+    int ris;                 // > 1: resampled importance sampling candidates
     int phi;
     float alpha;
     DataDev data;

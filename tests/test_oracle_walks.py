@@ -238,3 +238,51 @@ def test_dl_gradient_closed_form(sphere3, M, poly, l):
     # the value is unchanged by asking for the gradient
     r0 = O.dl_walks(v, f, QIN, 64, M, mode=O.DATA_POLY, poly=poly, tau=TAU)
     assert np.array_equal(r0["per_walk"], r["per_walk"][:, :64])
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_sl_mixed_all_dirichlet_closed_form(sphere3, M):
+    """Dirichlet parts of a mixed problem (Sec. 4.3): mu = mu - k S mu + k u_D,
+    sampled by a move (probability p_k, kernel -(k/p_k) G) or a stay (weight
+    1/(1 - p_k)).  In expectation the operator is I - k S, eigenvalue
+    b_l = 1 - k/(2l+1) on the sphere; the final step u = S mu divides by
+    k/(2l+1), so mode l of the estimate is ratio_M(b_l) h_l."""
+    v, f = sphere3
+    n = 100000
+    bc = np.full(len(f), O.BC_DIRICHLET, np.uint8)
+    pw = O.sl_walks(v, f, QIN, n, M, kind=O.KIND_MIXED_SL, phi=1, mode=O.DATA_POLY, poly=Z,
+                    bc_type=bc, kmix=1.5, pk=0.75)
+    est, var = O.reduce(pw)
+    _check(est, var, n, ratio(1.0 - 1.5 / 3.0, M) * QIN[:, 2].astype(float))
+
+
+def test_sl_mixed_with_one_condition_is_that_problem(sphere3):
+    """A mixed problem whose triangles all carry the Neumann (or Robin)
+    condition is walk for walk the Neumann (Robin) problem."""
+    v, f = sphere3
+    for cond, kind, alpha in ((O.BC_NEUMANN, O.KIND_NEUMANN_SL, 0.0),
+                              (O.BC_ROBIN, O.KIND_ROBIN_SL, 0.25)):
+        bc = np.full(len(f), cond, np.uint8)
+        a = O.sl_walks(v, f, QOUT, 64, 4, kind=O.KIND_MIXED_SL, alpha=alpha, phi=-1,
+                       mode=O.DATA_POINT, x0=(0.1, 0.2, 0.3), bc_type=bc, kmix=1.0, pk=0.5)
+        b = O.sl_walks(v, f, QOUT, 64, 4, kind=kind, alpha=alpha, phi=-1, mode=O.DATA_POINT,
+                       x0=(0.1, 0.2, 0.3))
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_sl_ris_is_unbiased(sphere3, M):
+    """Resampled importance sampling of the next point (16 uniform
+    candidates, target |kernel|) keeps the expectation: the same sphere
+    closed forms as area sampling, for interior Neumann and exterior Robin."""
+    v, f = sphere3
+    n = 40000
+    pw = O.sl_walks(v, f, QIN, n, M, kind=O.KIND_NEUMANN_SL, phi=1, mode=O.DATA_POLY, poly=Z,
+                    ris=16)
+    est, var = O.reduce(pw)
+    _check(est, var, n, ratio(1 / 3, M) * QIN[:, 2].astype(float))
+    alpha, x0 = 0.25, (0.1, 0.2, 0.3)
+    pw = O.sl_walks(v, f, QOUT, n, M, kind=O.KIND_ROBIN_SL, alpha=alpha, phi=-1,
+                    mode=O.DATA_POINT, x0=x0, ris=16)
+    est, var = O.reduce(pw)
+    _check(est, var, n, multipole(x0, QOUT, lambda l: (2 * alpha - 1) / (2 * l + 1), M, False))
