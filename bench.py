@@ -341,7 +341,7 @@ def run_sl(args):
         q = np.concatenate([pb, off]).astype(np.float32)
         pr = np.concatenate([prim, np.full(Q - half, -1, np.int32)])
         probs.append(wob.Problem(bvh, kind=kind, side=side, alpha=alpha,
-                                 data_mode=wob.DATA_POINT, x0=x0, problem=k))
+                                 data_mode=wob.DATA_POINT, x0=x0, problem=k, ris=args.sl_ris))
         qs.append(torch.from_numpy(q).cuda())
         prs.append(torch.from_numpy(pr).cuda())
     stream = torch.cuda.current_stream()
@@ -372,7 +372,8 @@ def run_sl(args):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 geometry / f64 walk arithmetic",
         "data": "synthetic (seeded displaced torus, seeded queries)",
-        "config": {"workload": f"displaced torus ({len(f)} tris), single layer, area sampling: "
+        "config": {"workload": f"displaced torus ({len(f)} tris), single layer, "
+                               f"{'area sampling' if args.sl_ris <= 1 else f'RIS ({args.sl_ris} candidates)'}: "
                                f"interior Neumann + exterior Robin (alpha 2), {Q} queries each "
                                f"(half on the boundary), {N} walks, M = {M}",
                    "path_vertices_per_step": verts,
@@ -480,6 +481,60 @@ def run_grad(args):
                                f"M={MAX_LEN}: value + gradient from the same walks",
                    "l2": "flushed (512 MB write) between timed steps"},
         "clocks": clk.summary(), "gpu_launches": 5 * args.steps,
+    }
+
+
+def run_mixed(args):
+    """Mixed boundary conditions (Sec. 4.3) with the paper's settings: every
+    triangle of the 200,000-triangle displaced torus takes a Dirichlet,
+    Neumann or Robin (alpha = 1) condition at random (seed 0), k = 4,
+    p_k = 2/3, next points by resampled importance sampling from 16 uniform
+    candidates, M = 4; data from h = 1/|x - (0, 0, 5)|; 131,072 queries inside
+    the torus, 512 walks.  A path vertex is one vertex of a walk (a picked
+    point or a stay)."""
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    from paper_2305_04403_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    v, f, shape = I.displaced_torus()
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    Q, N, M = args.sl_queries, 512, 4
+    q = torch.from_numpy(I.torus_queries(shape, Q, True, seed=20)).cuda()
+    bc = torch.from_numpy(np.random.default_rng(0).integers(0, 3, len(f)).astype(np.uint8)).cuda()
+    prob = wob.Problem(bvh, kind=wob.MIXED_SL, side=1, alpha=1.0, data_mode=wob.DATA_POINT,
+                       x0=(0.0, 0.0, 5.0), bc_type=bc, k_mix=4.0, p_k=2.0 / 3.0, ris=16)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        wob.solve(prob, q, N, M, seed=SEED)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            wob.solve(prob, q, N, M, seed=SEED)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    verts = Q * N * M
+    return {
+        "metric": METRIC, "value": verts * args.steps / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 geometry / f64 walk arithmetic",
+        "data": "synthetic (seeded displaced torus, seeded conditions and queries)",
+        "config": {"workload": f"displaced torus ({len(f)} tris), mixed Dirichlet / Neumann / "
+                               f"Robin conditions at random, k = 4, p_k = 2/3, RIS with 16 "
+                               f"candidates, {Q} interior queries, {N} walks, M = {M}",
+                   "path_vertices_per_step": verts, "area_samples_per_step": 16 * verts,
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
     }
 
 
@@ -715,7 +770,9 @@ def main():
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
     ap.add_argument("--workload", default="star",
-                    choices=["star", "batched", "cv", "sl", "nd", "grad"])
+                    choices=["star", "batched", "cv", "sl", "nd", "grad", "mixed"])
+    ap.add_argument("--sl-ris", type=int, default=0,
+                    help="sl workload: resampling candidates (0 = area sampling)")
     ap.add_argument("--sl-queries", type=int, default=131072)
     ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
     ap.add_argument("--cv-queries", type=int, default=65536,
@@ -740,6 +797,8 @@ def main():
         line = run_nd(args)
     elif args.workload == "grad":
         line = run_grad(args)
+    elif args.workload == "mixed":
+        line = run_mixed(args)
     else:
         line = run_ours(args)
     if line is not None:
