@@ -96,6 +96,11 @@ def _load():
             lib.oracle_dl_walks.restype = ctypes.c_int
             lib.oracle_nd_walks.argtypes = lib.oracle_dl_walks.argtypes[:-2] + [ctypes.c_int]
             lib.oracle_nd_walks.restype = ctypes.c_int
+            lib.oracle_fwd_paths.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, I64, I32,
+                                             U64, U32, I32, D, D, D, P, P, P, ctypes.c_int]
+            lib.oracle_fwd_paths.restype = ctypes.c_int
+            lib.oracle_fwd_connect.argtypes = [P, I64, P, P, I64, I32, P, ctypes.c_int]
+            lib.oracle_fwd_connect.restype = None
             lib.oracle_sl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, D, I32,
                                             P, I64, I64, I64, I32, I32, U64, U32, P, P,
                                             P, D, D, I32, ctypes.c_int]
@@ -290,6 +295,41 @@ def nd_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
     if want_lines:
         out["line_m"] = line_m
+    return out
+
+
+def fwd_paths(verts, tris, paths: int, max_len: int, seed: int = 0, problem: int = 0,
+              phi: int = 1, mode: int = DATA_POINT, vertex_data=None, poly=None, x0=None,
+              scale: float = 1.0, start_mode: int = 0, beta: float = 0.1, tau: float = TAU,
+              graze: float = GRAZE, nthreads: int = 0) -> dict:
+    """Forward single-layer Neumann paths (Sec. 4.4.3): zpos (N, M, 3) vertex
+    positions, zw (N, M) vertex weights c_j a_j (0 after a miss), flag (N).
+    start_mode 0: area-uniform starts; 1: weighted by |q| per triangle
+    (+ beta times its mean, so that every triangle can start a path)."""
+    v = _c(verts, np.float32)
+    t = _c(tris, np.int32)
+    data, keep = _data(mode, vertex_data, poly, x0, scale)
+    zpos = np.empty((paths, max_len, 3), np.float64)
+    zw = np.empty((paths, max_len), np.float64)
+    flag = np.empty(paths, np.uint8)
+    rc = _load().oracle_fwd_paths(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
+                                  paths, max_len, seed, problem, start_mode, beta, tau, graze,
+                                  _p(zpos), _p(zw), _p(flag), nthreads)
+    del keep
+    if rc != 0:
+        raise RuntimeError("oracle_fwd_paths failed")
+    return dict(zpos=zpos, zw=zw, flag=flag)
+
+
+def fwd_connect(queries, zpos, zw, nthreads: int = 0) -> np.ndarray:
+    """Per-path values (Q, N) of forward paths at the query points:
+    sum_j zw[p, j] G(x_q, z_pj)."""
+    q = _c(queries, np.float32).reshape(-1, 3)
+    zp = _c(zpos, np.float64)
+    w = _c(zw, np.float64)
+    N, M = w.shape
+    out = np.empty((q.shape[0], N), np.float64)
+    _load().oracle_fwd_connect(_p(q), q.shape[0], _p(zp), _p(w), N, M, _p(out), nthreads)
     return out
 
 

@@ -59,6 +59,8 @@
 #endif
 
 enum { PURPOSE_DIR = 0, PURPOSE_HIT = 1, PURPOSE_AREA = 2, PURPOSE_BRANCH = 4, PURPOSE_RIS = 5 };
+/* walk index of the forward paths' streams (path p uses query index p) */
+#define FORWARD_WALK 0xFFFFFFFFu
 enum { KIND_DIRICHLET_DL = 0, KIND_NEUMANN_SL = 1, KIND_ROBIN_SL = 2, KIND_MIXED_SL = 4 };
 enum { BC_DIRICHLET = 0, BC_NEUMANN = 1, BC_ROBIN = 2 };
 enum { DATA_VERTEX_P1 = 0, DATA_POLY = 1, DATA_POINT = 2 };
@@ -925,6 +927,143 @@ int oracle_nd_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
     }
     mesh_free(&M);
     return 0;
+}
+
+/* Forward (adjoint) single-layer Neumann paths (Sec. 4.4.3; the estimator
+ * of Sabelfeld and Simonov that starts on the boundary).  With
+ * u(x) = int G(x, y) mu(y) dA and mu = T mu + f, T's kernel
+ * K(y, z) = -2 phi dG/dn_x(y, z) and f = 2 phi q, the truncated solution is
+ * sum_j c_j <G(x, .), T^j f> (c_j = 1, 1/2 for j = M - 1, Sec. 4.1.2).  A
+ * path reads that product from the source end: z_0 ~ p on the boundary,
+ * weight a_0 = f(z_0) / p(z_0); from z_j a line (as the double-layer walks)
+ * picks z_{j+1}, and K(z_{j+1}, z_j) / p = phi m s (s = sign(w . n at
+ * z_{j+1})), so a_{j+1} = a_j phi m s.  Vertex j contributes
+ * c_j a_j G(x, z_j) to every evaluation point x (the explicit connection).
+ * Start density p: start_mode 0 area-uniform, 1 proportional per triangle to
+ * area (|q(centroid)| + beta mean|q|) and uniform on the triangle (the
+ * boundary-value-weighted start; beta > 0 keeps it positive everywhere).
+ * Outputs per path: vertex positions zpos (M x 3) and weights zw (M, the
+ * c_j a_j; 0 after a miss), flag (near-degenerate line). */
+static void fwd_path(const mesh_t *M, const oracle_data *D, int32_t phi, const double *wcdf,
+                     double wtot, int32_t start_mode, double beta, double qbar, uint32_t path,
+                     int32_t Mlen, uint64_t seed, uint32_t problem, double tauL, double graze,
+                     double *zpos, double *zw, uint8_t *flag)
+{
+    for (int32_t j = 0; j < Mlen; ++j) {
+        zpos[3 * j] = zpos[3 * j + 1] = zpos[3 * j + 2] = 0.0;
+        zw[j] = 0.0;
+    }
+    *flag = 0;
+    /* start point */
+    uint32_t u[4];
+    stream_block(seed, problem, path, FORWARD_WALK, 0, PURPOSE_AREA, 0, 0, u);
+    const double *cdf = start_mode == 1 ? wcdf : M->cdf;
+    double tot = start_mode == 1 ? wtot : M->area;
+    double target = u53(u[0], u[1]) * tot;
+    int64_t lo = 0, hi = M->T - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    double su = sqrt(u24(u[2])), u2 = u24(u[3]);
+    double b[3] = { 1.0 - su, su * (1.0 - u2), su * u2 };
+    double v0[3], v1[3], v2[3], z[3], n[3];
+    vtx(M, lo, 0, v0); vtx(M, lo, 1, v1); vtx(M, lo, 2, v2);
+    for (int c = 0; c < 3; ++c) z[c] = b[0] * v0[c] + b[1] * v1[c] + b[2] * v2[c];
+    unit_normal(M, lo, n);
+    double pdf;
+    if (start_mode == 1) {
+        double N[3];
+        tri_normal(M, lo, N);
+        double A = 0.5 * norm3(N);
+        double w = cdf[lo] - (lo > 0 ? cdf[lo - 1] : 0.0);
+        pdf = (w / A) / tot;
+    } else {
+        pdf = 1.0 / M->area;
+    }
+    double a = 2.0 * (double)phi * boundary_data(D, M, lo, z, b, n, KIND_NEUMANN_SL, 0.0) / pdf;
+    int64_t prim = lo;
+    for (int32_t j = 0; j < Mlen; ++j) {
+        double c = (j == Mlen - 1) ? 0.5 : 1.0;
+        zpos[3 * j] = z[0]; zpos[3 * j + 1] = z[1]; zpos[3 * j + 2] = z[2];
+        zw[j] = c * a;
+        if (j == Mlen - 1) break;
+        double d[3];
+        line_axis(seed, problem, path, FORWARD_WALK, (uint32_t)j, d);
+        line_result r;
+        trace_line(M, z, d, prim, seed, problem, path, FORWARD_WALK, (uint32_t)j, tauL, graze, &r);
+        if (r.flag) *flag = 1;
+        if (r.m == 0) break;
+        a *= (double)phi * (double)r.m * (double)r.s;
+        z[0] = r.y[0]; z[1] = r.y[1]; z[2] = r.y[2];
+        prim = r.prim;
+    }
+}
+
+/* N forward paths (fwd_path); zpos: N x M x 3, zw: N x M, flag: N. */
+int oracle_fwd_paths(const float *verts, int64_t V, const int32_t *tris, int64_t T,
+                     const oracle_data *D, int32_t phi, int64_t N, int32_t Mlen, uint64_t seed,
+                     uint32_t problem, int32_t start_mode, double beta, double tau, double graze,
+                     double *zpos, double *zw, uint8_t *flag, int nthreads)
+{
+    mesh_t M;
+    if (mesh_init(&M, verts, V, tris, T, 1)) return -1;
+    double *wcdf = (double *)malloc((size_t)T * sizeof(double));
+    if (!wcdf) { mesh_free(&M); return -1; }
+    /* boundary-value-weighted start: per-triangle weight area (|q(c)| + beta qbar) */
+    double qsum = 0.0;
+    for (int64_t j = 0; j < T; ++j) {
+        double v0[3], v1[3], v2[3], c[3], n[3], N3[3];
+        double b[3] = { 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0 };
+        vtx(&M, j, 0, v0); vtx(&M, j, 1, v1); vtx(&M, j, 2, v2);
+        for (int k = 0; k < 3; ++k) c[k] = (v0[k] + v1[k] + v2[k]) / 3.0;
+        unit_normal(&M, j, n);
+        tri_normal(&M, j, N3);
+        double A = 0.5 * norm3(N3);
+        wcdf[j] = A * fabs(boundary_data(D, &M, j, c, b, n, KIND_NEUMANN_SL, 0.0));
+        qsum += wcdf[j];
+    }
+    double qbar = qsum / M.area, acc = 0.0;
+    for (int64_t j = 0; j < T; ++j) {
+        double N3[3];
+        tri_normal(&M, j, N3);
+        double A = 0.5 * norm3(N3);
+        acc += wcdf[j] + beta * qbar * A;
+        wcdf[j] = acc;
+    }
+    double tauL = tau * M.L;
+    int nt = set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+    for (int64_t p = 0; p < N; ++p)
+        fwd_path(&M, D, phi, wcdf, acc, start_mode, beta, qbar, (uint32_t)p, Mlen, seed, problem,
+                 tauL, graze, zpos + p * Mlen * 3, zw + p * Mlen, flag + p);
+    free(wcdf);
+    mesh_free(&M);
+    return 0;
+}
+
+/* Explicit connection of N forward paths to Q points: per_path[q][p] =
+ * sum_j zw[p][j] G(x_q, z_pj), G = 1 / (4 pi r); est = mean over paths. */
+void oracle_fwd_connect(const float *queries, int64_t Q, const double *zpos, const double *zw,
+                        int64_t N, int32_t Mlen, double *per_path, int nthreads)
+{
+    int nt = set_threads(nthreads);
+    const double four_pi = 4.0 * ORACLE_PI;
+#pragma omp parallel for schedule(static) num_threads(nt)
+    for (int64_t q = 0; q < Q; ++q) {
+        double x[3] = { queries[3 * q], queries[3 * q + 1], queries[3 * q + 2] };
+        for (int64_t p = 0; p < N; ++p) {
+            double v = 0.0;
+            for (int32_t j = 0; j < Mlen; ++j) {
+                double w = zw[p * Mlen + j];
+                if (w == 0.0) continue;
+                const double *z = zpos + (p * Mlen + j) * 3;
+                double r[3] = { z[0] - x[0], z[1] - x[1], z[2] - x[2] };
+                v += w / (four_pi * norm3(r));
+            }
+            per_path[q * N + p] = v;
+        }
+    }
 }
 
 int oracle_sl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t T,
