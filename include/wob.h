@@ -257,6 +257,33 @@ int wob_solve_grad(const wob_problem *prob, const float *queries, int64_t Q, int
                    int32_t max_len, uint64_t seed, double *est, double *var, double *grad_est,
                    double *grad_var, double *per_walk_grad, void *stream);
 
+/*
+ * Forward (adjoint) estimator of single-layer Neumann problems (Sec. 4.4.3;
+ * the boundary-sampling advantage of Sec. 5): `paths` paths start ON the
+ * boundary at z_0 with weight 2 phi q(z_0) / p(z_0), follow lines as the
+ * double-layer walks (all hits, one picked; weight phi m s per step) for
+ * max_len vertices (the last weighted 1/2, Sec. 4.1.2), and every vertex is
+ * connected to every query: u(x) = mean over paths of sum_j w_j G(x, z_j).
+ * One set of paths serves all Q queries (cost ~ paths x max_len x Q for the
+ * connections).  start_mode 0: z_0 area-uniform; 1: per triangle
+ * proportional to area (|q(centroid)| + beta mean |q|), uniform on it -- the
+ * boundary-value-weighted start for sparse data (beta > 0 keeps every
+ * triangle reachable, so the estimate stays unbiased).  Expectation: that of
+ * wob_solve for the same problem and max_len.  prob: WOB_NEUMANN_SL (phi
+ * from side; ris is not used).  queries: device Q x 3; est, var: device Q
+ * (var: unbiased variance of one path's contribution).  zpos (paths x
+ * max_len x 3) and zw (paths x max_len), device, optional: the path
+ * vertices and their weights (0 after a missed line); scratch for them is
+ * allocated on `stream` when NULL.  path_flag (device, paths bytes,
+ * optional): 1 if a line of the path was near-degenerate.  Paths draw from
+ * the streams of query index = path index, walk index 0xFFFFFFFF.
+ * 1 <= max_len <= 1024.
+ */
+int wob_solve_forward(const wob_problem *prob, const float *queries, int64_t Q, int32_t paths,
+                      int32_t max_len, uint64_t seed, int32_t start_mode, float beta,
+                      double *est, double *var, double *zpos, double *zw, uint8_t *path_flag,
+                      void *stream);
+
 /* As wob_solve, counting traversal work into *stats (synchronises). */
 int wob_solve_counted(const wob_problem *prob, const float *queries, const int32_t *query_prim,
                       int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,

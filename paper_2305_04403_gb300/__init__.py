@@ -145,6 +145,8 @@ def load_library() -> ctypes.CDLL:
                                   ctypes.c_int),
             "wob_solve_grad": ([ctypes.POINTER(_Problem), P, I64, I32, I32, U64, P, P, P, P, P, P],
                                ctypes.c_int),
+            "wob_solve_forward": ([ctypes.POINTER(_Problem), P, I64, I32, I32, U64, I32, F, P, P,
+                                   P, P, P, P], ctypes.c_int),
             "wob_mlp_num_params": ([], ctypes.c_int),
             "wob_mlp_init": ([P, U64, P], ctypes.c_int),
             "wob_mlp_forward": ([P, P, I64, P, P], ctypes.c_int),
@@ -426,6 +428,29 @@ def solve_grad(problem: Problem, queries, walks: int, max_len: int, seed: int = 
                                          _ptr(out["est"]), _ptr(out["var"]), _ptr(out["grad_est"]),
                                          _ptr(out["grad_var"]), _ptr(out.get("grad")),
                                          _stream(stream)))
+    return out
+
+
+def solve_forward(problem: Problem, queries, paths: int, max_len: int, seed: int = 0,
+                  start_mode: int = 1, beta: float = 0.1, want_paths: bool = False,
+                  stream=None) -> dict:
+    """wob_solve_forward: est, var (Q,) and, with want_paths, the path
+    vertices zpos (paths, max_len, 3), weights zw (paths, max_len) and
+    near-degenerate flags (paths,)."""
+    import torch
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    Q = q.shape[0]
+    out = dict(est=torch.empty(Q, dtype=torch.float64, device="cuda"),
+               var=torch.empty(Q, dtype=torch.float64, device="cuda"))
+    if want_paths:
+        out["zpos"] = torch.empty((paths, max_len, 3), dtype=torch.float64, device="cuda")
+        out["zw"] = torch.empty((paths, max_len), dtype=torch.float64, device="cuda")
+        out["flag"] = torch.empty(paths, dtype=torch.uint8, device="cuda")
+    pc = problem._c()
+    _check(load_library().wob_solve_forward(ctypes.byref(pc), _ptr(q), Q, paths, max_len, seed,
+                                            start_mode, beta, _ptr(out["est"]), _ptr(out["var"]),
+                                            _ptr(out.get("zpos")), _ptr(out.get("zw")),
+                                            _ptr(out.get("flag")), _stream(stream)))
     return out
 
 

@@ -8,6 +8,8 @@
 #include <new>
 #include <string>
 
+#include <climits>
+
 #include "wob_host.h"
 
 namespace wob {
@@ -460,6 +462,47 @@ int wob_solve_grad(const wob_problem* prob, const float* queries, int64_t Q, int
     for (int c = 0; c < 3 && rc == WOB_OK; ++c)
         rc = launch_reduce(g + c * W, Q, walks, grad_est + c * Q, grad_var + c * Q, s);
     if (g_owned) cudaFreeAsync(g_owned, s);
+    return rc;
+}
+
+int wob_solve_forward(const wob_problem* prob, const float* queries, int64_t Q, int32_t paths,
+                      int32_t max_len, uint64_t seed, int32_t start_mode, float beta,
+                      double* est, double* var, double* zpos, double* zw, uint8_t* path_flag,
+                      void* stream)
+{
+    clear_error();
+    WOB_TRY(check_problem(prob));
+    if (prob->kind != WOB_NEUMANN_SL) {
+        set_error("wob_solve_forward: forward paths are implemented for WOB_NEUMANN_SL");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    if (paths < 2 || max_len < 1 || max_len > 1024 || (start_mode != 0 && start_mode != 1) ||
+        !(beta > 0.0f) || Q < 0 || (Q > 0 && (!queries || !est || !var)) ||
+        (int64_t)paths * max_len > INT32_MAX) {
+        set_error("wob_solve_forward: invalid arguments (paths >= 2, 1 <= max_len <= 1024, "
+                  "start_mode 0 or 1, beta > 0)");
+        return WOB_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    WalkParams p;
+    fill_params(p, prob, queries, nullptr, Q, 0, paths, max_len, seed);
+    Scratch sc;
+    sc.s = s;
+    const int64_t R = (int64_t)paths * max_len;
+    double* zp = zpos;
+    double* w = zw;
+    double* own = nullptr;
+    if (!zp || !w) {
+        WOB_CUDA_TRY(cudaMallocAsync((void**)&own, 4 * R * sizeof(double), s));
+        if (!zp) zp = own;
+        if (!w) w = own + 3 * R;
+    }
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(Control), s));
+    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(Control), s));
+    p.error_word = &sc.err->err;
+    int rc = launch_forward(p, paths, start_mode, (double)beta, queries, Q, zp, w, path_flag, est,
+                            var, s);
+    if (own) cudaFreeAsync(own, s);
     return rc;
 }
 

@@ -344,6 +344,176 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
     if (err) atomicOr(p.error_word, err);
 }
 
+// ---------------------------------------------------------------------------
+// Forward (adjoint) single-layer Neumann paths (Sec. 4.4.3).  With
+// u(x) = int G(x, y) mu(y) dA, mu = T mu + f, T's kernel
+// K(y, z) = -2 phi dG/dn_x(y, z) and f = 2 phi q, a path reads the truncated
+// series sum_j c_j <G(x, .), T^j f> from its source end: z_0 ~ p on the
+// boundary, a_0 = f(z_0) / p(z_0); from z_j a line (all hits, one picked,
+// as the double-layer walks) gives z_{j+1} and K(z_{j+1}, z_j) / p = phi m s,
+// so a_{j+1} = a_j phi m s; vertex j then contributes c_j a_j G(x, z_j) to
+// every evaluation point x (c_j = 1, 1/2 for the last, Sec. 4.1.2).
+// Streams: path p draws as query p, walk kForwardWalk.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kForwardWalk = 0xFFFFFFFFu;
+
+// Start weight of triangle j for boundary-value-weighted paths, first part:
+// area x |q(centroid)|.
+__global__ void k_fwd_qc(WalkParams p, double* __restrict__ aq)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < p.T;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t* t = p.tris + 3 * j;
+        double c[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 3; ++k)
+            for (int d = 0; d < 3; ++d) c[d] += (double)__ldg(p.verts + 3 * (int64_t)__ldg(t + k) + d);
+        const double3 y = make_double3(c[0] / 3.0, c[1] / 3.0, c[2] / 3.0);
+        const NormalArea na = p.tri_n[j];
+        const double3 n = make_double3(na.nx, na.ny, na.nz);
+        const double q = sl_data(p, j, y, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, n, WOB_BC_NEUMANN);
+        aq[j] = na.area * fabs(q);
+    }
+}
+
+// ... second part: + beta mean|q| area (mean over the boundary, from the
+// inclusive sums of the first part); inclusive sums of the result are the CDF.
+__global__ void k_fwd_mix(WalkParams p, const double* __restrict__ aq_incl, double beta,
+                          double* __restrict__ w)
+{
+    const double qbar = aq_incl[p.T - 1] / p.area;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < p.T;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double aq = aq_incl[j] - (j > 0 ? aq_incl[j - 1] : 0.0);
+        w[j] = aq + beta * qbar * p.tri_n[j].area;
+    }
+}
+
+__global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS)
+    k_fwd_paths(WalkParams p, int64_t n_paths, int start_mode, const double* __restrict__ wcdf,
+                double* __restrict__ zpos, double* __restrict__ zw, uint8_t* __restrict__ flags)
+{
+    const StreamKey key{p.key0, p.key1};
+    const double phi = (double)p.phi;
+    const double* cdf = start_mode == 1 ? wcdf : p.cdf;
+    const double tot = start_mode == 1 ? wcdf[p.T - 1] : p.area;
+    int err = 0;
+    int stack[kStackSize];
+    int hits[kMaxHits];
+    for (int64_t path = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; path < n_paths;
+         path += (int64_t)gridDim.x * blockDim.x) {
+        double* zp = zpos + path * p.M * 3;
+        double* wp = zw + path * p.M;
+        for (int j = 0; j < p.M; ++j) {
+            zp[3 * j] = zp[3 * j + 1] = zp[3 * j + 2] = 0.0;
+            wp[j] = 0.0;
+        }
+        const uint32_t q = (uint32_t)path;
+        const u32x4 u = stream_block(key, q, kForwardWalk, 0u, kPurposeArea, 0u, 0u);
+        const double target = u53(u.x, u.y) * tot;
+        int64_t lo = 0, hi = p.T - 1;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (__ldg(cdf + mid) > target) hi = mid; else lo = mid + 1;
+        }
+        const double su = sqrt(u24(u.z)), u2 = u24(u.w);
+        const double b0 = 1.0 - su, b1 = su * (1.0 - u2), b2 = su * u2;
+        const int32_t* t = p.tris + 3 * lo;
+        const float* v0 = p.verts + 3 * (int64_t)__ldg(t);
+        const float* v1 = p.verts + 3 * (int64_t)__ldg(t + 1);
+        const float* v2 = p.verts + 3 * (int64_t)__ldg(t + 2);
+        double3 z = make_double3(b0 * __ldg(v0) + b1 * __ldg(v1) + b2 * __ldg(v2),
+                                 b0 * __ldg(v0 + 1) + b1 * __ldg(v1 + 1) + b2 * __ldg(v2 + 1),
+                                 b0 * __ldg(v0 + 2) + b1 * __ldg(v1 + 2) + b2 * __ldg(v2 + 2));
+        const NormalArea na = p.tri_n[lo];
+        const double pdf = start_mode == 1
+                               ? ((cdf[lo] - (lo > 0 ? cdf[lo - 1] : 0.0)) / na.area) / tot
+                               : 1.0 / p.area;
+        double a = 2.0 * phi *
+                   sl_data(p, lo, z, b0, b1, b2, make_double3(na.nx, na.ny, na.nz), WOB_BC_NEUMANN) /
+                   pdf;
+        int self = p.inv_order[lo], flag = 0;
+        for (int j = 0; j < p.M; ++j) {
+            zp[3 * j] = z.x;
+            zp[3 * j + 1] = z.y;
+            zp[3 * j + 2] = z.z;
+            wp[j] = (j == p.M - 1 ? 0.5 : 1.0) * a;
+            if (j == p.M - 1) break;
+            const double3 d = line_axis(key, q, kForwardWalk, (uint32_t)j);
+            const LinePre L = line_pre(make_float3((float)z.x, (float)z.y, (float)z.z),
+                                       make_float3((float)d.x, (float)d.y, (float)d.z));
+            const float Tthr = p.edge_thr_L * fabsf(L.Sz);
+            Trav tr;
+            trav_init(tr);
+            uint32_t nn = 0, nt = 0;
+            trace_wide<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+                                     p.graze, self, tr, hits, stack, key, q, kForwardWalk,
+                                     (uint32_t)j, nn, nt, err, p.iter_limit);
+            flag |= tr.flag;
+            if (tr.m == 0) break;
+            const int pos = select_hit(p.tv, tr, hits, key, q, kForwardWalk, (uint32_t)j);
+            const Refined r = refine_hit(p.tv, pos, z, d);
+            a *= phi * (double)tr.m * (double)r.s;
+            z = r.y;
+            self = pos;
+        }
+        if (flags) flags[path] = (uint8_t)flag;
+    }
+    if (err) atomicOr(p.error_word, err);
+}
+
+// Explicit connection of every path vertex to every query (an N-body sum):
+// per query, v_p = sum_j w_pj G(x, z_pj) for each path, est = mean of v_p,
+// var = their unbiased variance.  The block stages whole paths (position and
+// weight as float4) in shared memory; distances, G and v_p in FP32, the sums
+// over paths in FP64.
+constexpr int kFwdTile = 1024;  // vertex records per tile (max_len <= kFwdTile)
+
+__global__ void __launch_bounds__(128) k_fwd_connect(const float* __restrict__ queries, int64_t Q,
+                                                     const double* __restrict__ zpos,
+                                                     const double* __restrict__ zw,
+                                                     int64_t n_paths, int M,
+                                                     double* __restrict__ est,
+                                                     double* __restrict__ var)
+{
+    __shared__ float4 rec[kFwdTile];
+    const int ppt = kFwdTile / M;  // whole paths per tile
+    constexpr float kInv4Pi = 0.0795774715459476678f;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < Q;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = base + threadIdx.x;
+        const bool ok = qi < Q;
+        const float xx = ok ? queries[3 * qi] : 0.f, xy = ok ? queries[3 * qi + 1] : 0.f,
+                    xz = ok ? queries[3 * qi + 2] : 0.f;
+        double sum = 0.0, sumsq = 0.0;
+        for (int64_t p0 = 0; p0 < n_paths; p0 += ppt) {
+            const int np = (int)(n_paths - p0 < ppt ? n_paths - p0 : ppt);
+            __syncthreads();
+            for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
+                const int64_t r = p0 * M + i;
+                rec[i] = make_float4((float)zpos[3 * r], (float)zpos[3 * r + 1],
+                                     (float)zpos[3 * r + 2], (float)zw[r]);
+            }
+            __syncthreads();
+            for (int pp = 0; pp < np; ++pp) {
+                float v = 0.f;
+                for (int j = 0; j < M; ++j) {
+                    const float4 z = rec[pp * M + j];
+                    if (z.w == 0.f) continue;  // after a miss (uniform across the block)
+                    const float dx = z.x - xx, dy = z.y - xy, dz = z.z - xz;
+                    v = fmaf(z.w * kInv4Pi, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), v);
+                }
+                sum += (double)v;
+                sumsq = fma((double)v, (double)v, sumsq);
+            }
+        }
+        if (ok) {
+            const double mean = sum / (double)n_paths;
+            est[qi] = mean;
+            var[qi] = n_paths > 1 ? fmax(sumsq - sum * mean, 0.0) / (double)(n_paths - 1) : 0.0;
+        }
+    }
+}
+
 // One warp per query: mean and unbiased variance in a fixed order.
 __global__ void k_reduce(const double* __restrict__ per_walk, int64_t Q, int32_t N,
                          double* __restrict__ est, double* __restrict__ var)
@@ -512,6 +682,39 @@ int launch_nd_walks(const WalkParams& p, bool debug, cudaStream_t s)
         k_nd_walks<false><<<grid_for((const void*)k_nd_walks<false>, threads, 0, work), threads, 0, s>>>(p);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
+}
+
+int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double beta,
+                   const float* queries, int64_t Q, double* zpos, double* zw, uint8_t* flags,
+                   double* est, double* var, cudaStream_t s)
+{
+    double* buf = nullptr;  // aq, its sums, start weights, their sums: 4 x T doubles
+    if (start_mode == 1) {
+        WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, 4 * p.T * sizeof(double), s));
+        const int g = grid_for((const void*)k_fwd_qc, 256, 0, p.T);
+        k_fwd_qc<<<g, 256, 0, s>>>(p, buf);
+        int rc = inclusive_scan<double>(buf, buf + p.T, p.T, s);
+        if (rc == WOB_OK) {
+            k_fwd_mix<<<g, 256, 0, s>>>(p, buf + p.T, beta, buf + 2 * p.T);
+            rc = inclusive_scan<double>(buf + 2 * p.T, buf + 3 * p.T, p.T, s);
+        }
+        if (rc != WOB_OK) {
+            cudaFreeAsync(buf, s);
+            return rc;
+        }
+    }
+    const int threads = 128;
+    k_fwd_paths<<<grid_for((const void*)k_fwd_paths, threads, 0, n_paths), threads, 0, s>>>(
+        p, n_paths, start_mode, buf ? buf + 3 * p.T : nullptr, zpos, zw, flags);
+    int rc = cudaGetLastError() == cudaSuccess ? WOB_OK : WOB_ERR_CUDA;
+    if (rc == WOB_OK && Q > 0) {
+        k_fwd_connect<<<grid_for((const void*)k_fwd_connect, threads, 0, Q), threads, 0, s>>>(
+            queries, Q, zpos, zw, n_paths, p.M, est, var);
+        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+    }
+    if (buf) cudaFreeAsync(buf, s);
+    if (rc != WOB_OK) set_error("forward paths failed");
+    return rc;
 }
 
 int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,

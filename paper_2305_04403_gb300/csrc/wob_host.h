@@ -54,6 +54,10 @@ void free_bvh(BvhDev& b);
 int launch_dl_walks(const WalkParams& p, bool counted, bool debug, cudaStream_t s);
 int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s);
 int launch_nd_walks(const WalkParams& p, bool debug, cudaStream_t s);
+// forward single-layer Neumann paths and their connection to the queries
+int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double beta,
+                   const float* queries, int64_t Q, double* zpos, double* zw, uint8_t* flags,
+                   double* est, double* var, cudaStream_t s);
 int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
                   cudaStream_t s);
 int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum,
