@@ -538,6 +538,107 @@ def run_mixed(args):
     }
 
 
+def run_fwd(args):
+    """Forward (adjoint) single-layer estimator for an interior Neumann
+    problem with sparse data (Sec. 4.4.3 and the Neumann example of Sec. 5):
+    the 200,000-triangle displaced torus, P1 data zero except for six signed
+    Gaussian bumps (width 0.05, integrating to zero), 131,072 queries inside
+    the torus, 65,536 paths of M = 24 vertices that start where |q| is large
+    (boundary-value-weighted, beta = 0.1), every vertex connected to every
+    query.  A step is one wob_solve_forward call; the unit is one
+    (path vertex, query) connection.  Beside it, untimed: the same call with
+    area-uniform starts and the backward single-layer walks (512 per query),
+    compared by variance x time."""
+    import torch
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    from paper_2305_04403_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    v, f, shape = I.displaced_torus()
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh, leaf_size=args.leaf)
+    Q, P, M, N = args.sl_queries, args.fwd_paths, 24, 512
+    q = torch.from_numpy(I.torus_queries(shape, Q, True, seed=20)).cuda()
+    vd = torch.from_numpy(I.bump_data(v, f)).cuda()
+    prob = wob.Problem(bvh, kind=wob.NEUMANN_SL, side=1, data_mode=wob.DATA_VERTEX_P1,
+                       vertex_data=vd)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    no_q = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps):
+        out, ms = None, []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return out, float(np.median(ms))
+
+    fwd = lambda mode, qq=q: wob.solve_forward(prob, qq, P, M, seed=SEED, start_mode=mode, beta=0.1)
+    for _ in range(args.warmup):
+        fwd(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            out_w = fwd(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    t_w = total_ms / args.steps
+    _, t_paths = timed(lambda: fwd(1, no_q), 3)
+    out_u, t_u = timed(lambda: fwd(0), 2)
+    (est_b, var_b), t_b = timed(lambda: wob.solve(prob, q, N, M, seed=SEED), 2)
+    ew, vw = out_w["est"].cpu().numpy(), out_w["var"].cpu().numpy() / P
+    eu, vu = out_u["est"].cpu().numpy(), out_u["var"].cpu().numpy() / P
+    eb, vb = est_b.cpu().numpy(), var_b.cpu().numpy() / N
+    z = np.abs(ew - eb) / np.sqrt(vw + vb)
+    pairs = P * M * Q
+    t_conn = max(t_w - t_paths, 1e-6)
+    sm = clk.summary()
+    sm_max = sm.get("sm_max_mhz") or 2070.0
+    peak = 152 * 16 * sm_max * 1e6 / 1e9          # G pairs/s: one MUFU rsqrt per pair
+    achieved = pairs / (t_conn / 1e3) / 1e9
+    return {
+        "metric": METRIC + " (forward estimator: vertex-query connections)",
+        "value": pairs * args.steps / (total_ms / 1e3), "unit": "connections/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_w,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 geometry and connections / f64 path weights and sums",
+        "data": "synthetic (seeded displaced torus, six seeded bumps, seeded queries)",
+        "config": {"workload": f"displaced torus ({len(f)} tris), interior Neumann, sparse data "
+                               f"(6 bumps), forward single-layer paths with boundary-value-weighted "
+                               f"starts: {P} paths x M = {M} connected to {Q} interior queries",
+                   "path_vertices_per_step": P * M, "connections_per_step": pairs,
+                   "paths_only_ms": t_paths,
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "compare": {
+            "ms": {"forward_weighted": t_w, "forward_uniform": t_u, f"backward_{N}_walks": t_b},
+            "median_var_of_estimate": {"forward_weighted": float(np.median(vw)),
+                                       "forward_uniform": float(np.median(vu)),
+                                       f"backward_{N}_walks": float(np.median(vb))},
+            "median_var_x_time_gain_vs_backward": {
+                "forward_weighted": float(np.median(vb * t_b / (vw * t_w))),
+                "forward_uniform": float(np.median(vb * t_b / (vu * t_u)))},
+            "agreement_forward_vs_backward": {"frac_within_4_sigma": float((z <= 4).mean()),
+                                              "median_z": float(np.median(z))}},
+        "clocks": sm, "gpu_launches": (4 + 2) * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G pairs/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_fwd_connect",
+                     "peak_source": f"152 SMs x 16 MUFU rsqrt/clk x {sm_max:.0f} MHz; connection "
+                                    f"time = step - the same call with no queries"},
+    }
+
+
 def run_cv(args):
     """Learned control variate vs plain WoB: time to RMSE 1e-3 against the
     exact solution on the icosphere-L3 mesh (1,280 triangles) with
@@ -770,10 +871,11 @@ def main():
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
     ap.add_argument("--workload", default="star",
-                    choices=["star", "batched", "cv", "sl", "nd", "grad", "mixed"])
+                    choices=["star", "batched", "cv", "sl", "nd", "grad", "mixed", "fwd"])
     ap.add_argument("--sl-ris", type=int, default=0,
                     help="sl workload: resampling candidates (0 = area sampling)")
     ap.add_argument("--sl-queries", type=int, default=131072)
+    ap.add_argument("--fwd-paths", type=int, default=1 << 16, help="fwd workload: paths")
     ap.add_argument("--cv-len", type=int, default=2, help="residual walk length (cv workload)")
     ap.add_argument("--cv-queries", type=int, default=65536,
                     help="queries of the cv workload (the metric is defined at 65,536)")
@@ -799,6 +901,8 @@ def main():
         line = run_grad(args)
     elif args.workload == "mixed":
         line = run_mixed(args)
+    elif args.workload == "fwd":
+        line = run_fwd(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -463,55 +463,167 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS)
 
 // Explicit connection of every path vertex to every query (an N-body sum):
 // per query, v_p = sum_j w_pj G(x, z_pj) for each path, est = mean of v_p,
-// var = their unbiased variance.  The block stages whole paths (position and
-// weight as float4) in shared memory; distances, G and v_p in FP32, the sums
-// over paths in FP64.
-constexpr int kFwdTile = 1024;  // vertex records per tile (max_len <= kFwdTile)
+// var = their unbiased variance.
+//
+// k_fwd_pack turns each path into M float4 records (position, w / 4 pi; a
+// vertex of weight 0 -- after a missed line -- sits far away with weight 0,
+// so the inner loop needs no branch) and one live byte (0: every record of
+// the path is 0, the path adds nothing but still counts in the mean).
+// k_fwd_connect: work items are (block of kFwdThreads x kFwdQ queries, split
+// of the paths); a persistent grid takes them in turn.  Whole paths are
+// staged in shared memory; each thread keeps kFwdQ queries in registers, so
+// one broadcast shared load feeds kFwdQ pairs; distances, G and v_p in FP32.
+// The sums over paths run in FP32 for kFwdFold paths and are then folded into
+// FP64 sums kept in shared memory (FP64 issues at 1/64 of the FP32 rate on
+// this GPU: one FP64 add per path and query would cost as much as the
+// pairs).  k_fwd_finish adds the
+// splits' FP64 partial sums in a fixed order.
+constexpr int kFwdTile = 1024;     // vertex records per tile (max_len <= kFwdTile)
+constexpr int kFwdThreads = 128;
+constexpr int kFwdQ = 8;           // queries per thread
+constexpr int kFwdFold = 32;       // paths summed in FP32 before an FP64 fold
+constexpr float kFwdFar = 1e18f;   // |r|^2 ~ 3e36 stays finite in FP32
 
-__global__ void __launch_bounds__(128) k_fwd_connect(const float* __restrict__ queries, int64_t Q,
-                                                     const double* __restrict__ zpos,
-                                                     const double* __restrict__ zw,
-                                                     int64_t n_paths, int M,
-                                                     double* __restrict__ est,
-                                                     double* __restrict__ var)
+__global__ void k_fwd_pack(const double* __restrict__ zpos, const double* __restrict__ zw,
+                           int64_t n_paths, int M, float4* __restrict__ rec,
+                           uint8_t* __restrict__ live)
+{
+    constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;
+    for (int64_t path = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; path < n_paths;
+         path += (int64_t)gridDim.x * blockDim.x) {
+        int any = 0;
+        for (int j = 0; j < M; ++j) {
+            const int64_t r = path * M + j;
+            const float w = (float)(zw[r] * kInv4Pi);
+            rec[r] = w != 0.f ? make_float4((float)zpos[3 * r], (float)zpos[3 * r + 1],
+                                            (float)zpos[3 * r + 2], w)
+                              : make_float4(kFwdFar, kFwdFar, kFwdFar, 0.f);
+            any |= w != 0.f;
+        }
+        live[path] = (uint8_t)any;
+    }
+}
+
+// 1 / sqrt(x), the approximate MUFU form (relative error below 2^-22), with
+// subnormal inputs and results flushed to zero: a squared distance here is
+// either 0 (a query on a path vertex) or far above the subnormal range.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void __launch_bounds__(kFwdThreads)
+    k_fwd_connect(const float* __restrict__ queries, int64_t Q, const float4* __restrict__ rec_g,
+                  const uint8_t* __restrict__ live_g, int64_t n_paths, int M, int64_t q_blocks,
+                  int splits, int64_t per_split, double* __restrict__ part)
 {
     __shared__ float4 rec[kFwdTile];
+    __shared__ uint8_t live[kFwdTile];
+    __shared__ double fsum[kFwdQ][kFwdThreads], fsq[kFwdQ][kFwdThreads];  // FP64 folds
     const int ppt = kFwdTile / M;  // whole paths per tile
-    constexpr float kInv4Pi = 0.0795774715459476678f;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < Q;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = base + threadIdx.x;
-        const bool ok = qi < Q;
-        const float xx = ok ? queries[3 * qi] : 0.f, xy = ok ? queries[3 * qi + 1] : 0.f,
-                    xz = ok ? queries[3 * qi + 2] : 0.f;
-        double sum = 0.0, sumsq = 0.0;
-        for (int64_t p0 = 0; p0 < n_paths; p0 += ppt) {
-            const int np = (int)(n_paths - p0 < ppt ? n_paths - p0 : ppt);
+    const int64_t items = q_blocks * splits;
+    const int t = threadIdx.x;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t qb = item % q_blocks;
+        const int sp = (int)(item / q_blocks);
+        const int64_t pb = (int64_t)sp * per_split;
+        const int64_t pe = pb + per_split < n_paths ? pb + per_split : n_paths;
+        float x[kFwdQ], y[kFwdQ], z[kFwdQ], s32[kFwdQ], ss32[kFwdQ];
+#pragma unroll
+        for (int k = 0; k < kFwdQ; ++k) {
+            const int64_t qi = (qb * kFwdQ + k) * kFwdThreads + t;
+            const bool ok = qi < Q;
+            x[k] = ok ? queries[3 * qi] : 0.f;
+            y[k] = ok ? queries[3 * qi + 1] : 0.f;
+            z[k] = ok ? queries[3 * qi + 2] : 0.f;
+            s32[k] = ss32[k] = 0.f;
+            fsum[k][t] = fsq[k][t] = 0.0;
+        }
+        int cnt = 0;
+        for (int64_t p0 = pb; p0 < pe; p0 += ppt) {
+            const int np = (int)(pe - p0 < ppt ? pe - p0 : ppt);
             __syncthreads();
-            for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
-                const int64_t r = p0 * M + i;
-                rec[i] = make_float4((float)zpos[3 * r], (float)zpos[3 * r + 1],
-                                     (float)zpos[3 * r + 2], (float)zw[r]);
-            }
+            for (int i = t; i < np * M; i += kFwdThreads) rec[i] = rec_g[p0 * M + i];
+            for (int i = t; i < np; i += kFwdThreads) live[i] = live_g[p0 + i];
             __syncthreads();
             for (int pp = 0; pp < np; ++pp) {
-                float v = 0.f;
+                if (!live[pp]) continue;  // the same path for the whole block
+                float v[kFwdQ];
+#pragma unroll
+                for (int k = 0; k < kFwdQ; ++k) v[k] = 0.f;
+                const float4* rp = rec + pp * M;
+#pragma unroll 2
                 for (int j = 0; j < M; ++j) {
-                    const float4 z = rec[pp * M + j];
-                    if (z.w == 0.f) continue;  // after a miss (uniform across the block)
-                    const float dx = z.x - xx, dy = z.y - xy, dz = z.z - xz;
-                    v = fmaf(z.w * kInv4Pi, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), v);
+                    const float4 c = rp[j];
+#pragma unroll
+                    for (int k = 0; k < kFwdQ; ++k) {
+                        const float dx = c.x - x[k], dy = c.y - y[k], dz = c.z - z[k];
+                        v[k] = fmaf(c.w, rsqrt_ftz(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), v[k]);
+                    }
                 }
-                sum += (double)v;
-                sumsq = fma((double)v, (double)v, sumsq);
+#pragma unroll
+                for (int k = 0; k < kFwdQ; ++k) {
+                    s32[k] += v[k];
+                    ss32[k] = fmaf(v[k], v[k], ss32[k]);
+                }
+                if (++cnt == kFwdFold) {
+#pragma unroll
+                    for (int k = 0; k < kFwdQ; ++k) {
+                        fsum[k][t] += (double)s32[k];
+                        fsq[k][t] += (double)ss32[k];
+                        s32[k] = ss32[k] = 0.f;
+                    }
+                    cnt = 0;
+                }
             }
         }
-        if (ok) {
-            const double mean = sum / (double)n_paths;
-            est[qi] = mean;
-            var[qi] = n_paths > 1 ? fmax(sumsq - sum * mean, 0.0) / (double)(n_paths - 1) : 0.0;
+#pragma unroll
+        for (int k = 0; k < kFwdQ; ++k) {
+            const int64_t qi = (qb * kFwdQ + k) * kFwdThreads + t;
+            if (qi < Q) {
+                part[(2 * (int64_t)sp) * Q + qi] = fsum[k][t] + (double)s32[k];
+                part[(2 * (int64_t)sp + 1) * Q + qi] = fsq[k][t] + (double)ss32[k];
+            }
         }
     }
+}
+
+__global__ void k_fwd_finish(const double* __restrict__ part, int splits, int64_t Q,
+                             int64_t n_paths, double* __restrict__ est, double* __restrict__ var)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        double sum = 0.0, sumsq = 0.0;
+        for (int sp = 0; sp < splits; ++sp) {
+            sum += part[(2 * (int64_t)sp) * Q + q];
+            sumsq += part[(2 * (int64_t)sp + 1) * Q + q];
+        }
+        const double mean = sum / (double)n_paths;
+        est[q] = mean;
+        var[q] = n_paths > 1 ? fmax(sumsq - sum * mean, 0.0) / (double)(n_paths - 1) : 0.0;
+    }
+}
+
+// Splits of the paths for k_fwd_connect: enough work items to fill every
+// resident block slot, and a count of items close to a whole number of
+// rounds of the persistent grid (the last round is the idle tail).
+static int fwd_splits(int64_t q_blocks, int64_t max_splits, int64_t slots)
+{
+    int best = 1;
+    double best_eff = -1.0;
+    for (int s = 1; s <= 64 && s <= max_splits; ++s) {
+        const int64_t items = q_blocks * s;
+        const int64_t rounds = (items + slots - 1) / slots;
+        const double eff = (double)items / (double)(rounds * slots);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best = s;
+        }
+        if (eff >= 0.95) break;
+    }
+    return best;
 }
 
 // One warp per query: mean and unbiased variance in a fixed order.
@@ -707,12 +819,40 @@ int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double 
     k_fwd_paths<<<grid_for((const void*)k_fwd_paths, threads, 0, n_paths), threads, 0, s>>>(
         p, n_paths, start_mode, buf ? buf + 3 * p.T : nullptr, zpos, zw, flags);
     int rc = cudaGetLastError() == cudaSuccess ? WOB_OK : WOB_ERR_CUDA;
-    if (rc == WOB_OK && Q > 0) {
-        k_fwd_connect<<<grid_for((const void*)k_fwd_connect, threads, 0, Q), threads, 0, s>>>(
-            queries, Q, zpos, zw, n_paths, p.M, est, var);
-        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
-    }
     if (buf) cudaFreeAsync(buf, s);
+    if (rc == WOB_OK && Q > 0) {
+        // packed records and live bytes, then (sum, sum of squares) per split and query
+        const int64_t R = n_paths * p.M;
+        const int64_t q_blocks = (Q + kFwdThreads * kFwdQ - 1) / (kFwdThreads * kFwdQ);
+        const int ppt = kFwdTile / p.M;
+        int dev = 0, sms = 1, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_connect, kFwdThreads,
+                                                          0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        const int64_t slots = (int64_t)sms * per_sm;
+        const int splits = fwd_splits(q_blocks, (n_paths + ppt - 1) / ppt, slots);
+        const int64_t per_split = (n_paths + splits - 1) / splits;
+        const size_t rec_bytes = ((size_t)R * sizeof(float4) + 255) & ~(size_t)255;
+        const size_t live_bytes = ((size_t)n_paths + 255) & ~(size_t)255;
+        char* cb = nullptr;
+        WOB_CUDA_TRY(cudaMallocAsync((void**)&cb,
+                                     rec_bytes + live_bytes + 2 * splits * Q * sizeof(double), s));
+        float4* rec = (float4*)cb;
+        uint8_t* live = (uint8_t*)(cb + rec_bytes);
+        double* part = (double*)(cb + rec_bytes + live_bytes);
+        k_fwd_pack<<<grid_for((const void*)k_fwd_pack, threads, 0, n_paths), threads, 0, s>>>(
+            zpos, zw, n_paths, p.M, rec, live);
+        const int64_t items = q_blocks * splits;
+        k_fwd_connect<<<(int)(items < slots ? items : slots), kFwdThreads, 0, s>>>(
+            queries, Q, rec, live, n_paths, p.M, q_blocks, splits, per_split, part);
+        k_fwd_finish<<<grid_for((const void*)k_fwd_finish, 256, 0, Q), 256, 0, s>>>(
+            part, splits, Q, n_paths, est, var);
+        if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+        cudaFreeAsync(cb, s);
+    }
     if (rc != WOB_OK) set_error("forward paths failed");
     return rc;
 }

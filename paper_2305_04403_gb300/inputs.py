@@ -14,6 +14,9 @@ Workloads (sizes as used by the tests and the benchmark):
     Fourier modes (seeded), quad grid nu x nv -> 2*nu*nv triangles.
   * query points uniform in a ball, on a z = 0 slice clipped to the
     interior, or area-uniform on the boundary.
+  * ``bump_data``: sparse Neumann data, six signed Gaussian bumps on the
+    boundary (the paper's Neumann example with data zero except near six
+    points), integrating to zero.
 """
 from __future__ import annotations
 
@@ -285,6 +288,29 @@ def poly_eval(c, p: np.ndarray) -> np.ndarray:
     x, y, z = p[..., 0], p[..., 1], p[..., 2]
     return (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * x + c[5] * y * y + c[6] * z * z
             + c[7] * x * y + c[8] * y * z + c[9] * z * x)
+
+
+def bump_data(verts: np.ndarray, tris: np.ndarray, n_bumps: int = 6, width: float = 0.05,
+              seed: int = 3) -> np.ndarray:
+    """Sparse Neumann data as vertex values (P1): zero except for Gaussian
+    bumps exp(-(d / width)^2) around ``n_bumps`` area-uniform boundary points
+    (seeded) with alternating signs; the negative bumps are scaled so that
+    the data integrates to zero over the mesh (a solvable interior Neumann
+    problem).  Float32, one value per vertex."""
+    c, _ = boundary_points(verts, tris, n_bumps, seed)
+    v = verts.astype(np.float64)
+    pos = np.zeros(len(v))
+    neg = np.zeros(len(v))
+    for k in range(n_bumps):
+        g = np.exp(-(np.linalg.norm(v - c[k].astype(np.float64), axis=1) / width) ** 2)
+        if k % 2 == 0:
+            pos += g
+        else:
+            neg += g
+    a, b, cc = v[tris[:, 0]], v[tris[:, 1]], v[tris[:, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(b - a, cc - a), axis=1)
+    integral = lambda h: float((area * h[tris].mean(axis=1)).sum())
+    return (pos - neg * (integral(pos) / integral(neg))).astype(np.float32)
 
 
 def point_source_eval(x0, p: np.ndarray, scale: float = 1.0) -> np.ndarray:

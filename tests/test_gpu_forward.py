@@ -4,8 +4,9 @@ wob_solve_forward) against the oracle's fwd_paths / fwd_connect.
 Paths: same counter-based draws on both sides, so on paths neither side
 flags the vertices agree to 1e-9 and the weights to 1e-9 relative (FP64
 refinement; the weighted start's CDF is summed in another order).
-Connection: the GPU sums distances and G in FP32 per path and over paths in
-FP64: per query within 1e-5 of the mean of sum_j |w_j| G(x, z_j)."""
+Connection: the GPU sums distances and G in FP32 per path, over runs of 32
+paths in FP32 and over those runs in FP64: per query within 1e-5 of the
+mean of sum_j |w_j| G(x, z_j)."""
 import numpy as np
 import pytest
 
