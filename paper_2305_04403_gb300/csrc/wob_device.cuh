@@ -204,18 +204,14 @@ __device__ __forceinline__ void keep_min(uint64_t k, uint32_t prim, int pos, uin
     }
 }
 
-// Line-triangle test of leaf triangle p (Woop, Benthin, Wald, "Watertight
-// ray/triangle intersection", JCGT 2013, applied to a line: no parameter
-// range): record a hit, flag near-degenerate configurations.
-template <bool SUM_S>
-__device__ __forceinline__ void test_tri(const float4* __restrict__ tv, const LinePre& L, float3 d,
-                                         float Tthr, float tauL, float graze, int p, Trav& t,
-                                         int* hits, StreamKey key, uint32_t q, uint32_t walk,
-                                         uint32_t step)
+// Line-triangle test (Woop, Benthin, Wald, "Watertight ray/triangle
+// intersection", JCGT 2013, applied to a line: no parameter range) of the
+// triangle (a4, b4, c4) in leaf layout: true on a hit (tl = its line
+// parameter); flag = 1 on a near-degenerate configuration.
+__device__ __forceinline__ bool line_tri(const float4& a4, const float4& b4, const float4& c4,
+                                         const LinePre& L, float Tthr, float tauL, float graze,
+                                         int& flag, float& tl)
 {
-    const float4 a4 = __ldg(tv + 3 * p + 0);
-    const float4 b4 = __ldg(tv + 3 * p + 1);
-    const float4 c4 = __ldg(tv + 3 * p + 2);
     const float3 A = make_float3(a4.x - L.ox, a4.y - L.oy, a4.z - L.oz);
     const float3 B = make_float3(b4.x - L.ox, b4.y - L.oy, b4.z - L.oz);
     const float3 C = make_float3(c4.x - L.ox, c4.y - L.oy, c4.z - L.oz);
@@ -231,15 +227,30 @@ __device__ __forceinline__ void test_tri(const float4* __restrict__ tv, const Li
     const float W = Bx * Ay - By * Ax;
     const bool pos_side = (U > -Tthr) && (V > -Tthr) && (W > -Tthr);
     const bool neg_side = (U < Tthr) && (V < Tthr) && (W < Tthr);
-    if (!(pos_side || neg_side)) return;
+    if (!(pos_side || neg_side)) return false;
     const float det = U + V + W;
     const float mn = fminf(fminf(fabsf(U), fabsf(V)), fabsf(W));
-    if (mn < Tthr || fabsf(det) < graze * b4.w * fabsf(L.Sz)) t.flag = 1;
+    if (mn < Tthr || fabsf(det) < graze * b4.w * fabsf(L.Sz)) flag = 1;
     const bool hit = (U > 0.f && V > 0.f && W > 0.f) || (U < 0.f && V < 0.f && W < 0.f);
-    if (!hit) return;
+    if (!hit) return false;
     const float T = fmaf(U, L.Sz * Akz, fmaf(V, L.Sz * Bkz, W * (L.Sz * Ckz)));
-    const float tl = T / det;
-    if (fabsf(tl) < tauL) t.flag = 1;
+    tl = T / det;
+    if (fabsf(tl) < tauL) flag = 1;
+    return true;
+}
+
+// Test of leaf triangle p for the one-lane traversal: record a hit.
+template <bool SUM_S>
+__device__ __forceinline__ void test_tri(const float4* __restrict__ tv, const LinePre& L, float3 d,
+                                         float Tthr, float tauL, float graze, int p, Trav& t,
+                                         int* hits, StreamKey key, uint32_t q, uint32_t walk,
+                                         uint32_t step)
+{
+    const float4 a4 = __ldg(tv + 3 * p + 0);
+    const float4 b4 = __ldg(tv + 3 * p + 1);
+    const float4 c4 = __ldg(tv + 3 * p + 2);
+    float tl = 0.f;
+    if (!line_tri(a4, b4, c4, L, Tthr, tauL, graze, t.flag, tl)) return;
     if (t.m < kMaxHits) {
         hits[t.m] = p;
     } else {
