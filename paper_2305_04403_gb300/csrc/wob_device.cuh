@@ -293,6 +293,16 @@ __device__ __forceinline__ int pick4(int4 v, int j)
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
+// Leaf triangles are not tested during the node visit that finds them: a
+// lane queues them and keeps visiting nodes until every lane still
+// traversing (the converged set) holds queued triangles or has run out of
+// nodes, then the lanes test their queues together (Aila and Laine,
+// "Understanding the efficiency of ray traversal on GPUs", HPG 2009:
+// postponed leaves, speculative traversal).  A leaf that does not fit in
+// the queue is tested on the spot.  The set of triangles tested is the
+// same as with immediate tests.
+constexpr int kLeafQ = 16;
+
 template <bool COUNT, bool SUM_S>
 __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
                                            const float4* __restrict__ tv, const LinePre& L,
@@ -302,11 +312,28 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
                                            uint32_t step, uint32_t& n_nodes, uint32_t& n_tris,
                                            int& err, int iter_limit)
 {
-    int node = 0, sp = 0, iters = 0;
+    int node = 0, sp = 0, iters = 0, nq = 0;
+    int lq[kLeafQ];
+    bool done = false;
     while (true) {
-        if (node >= 0) {
+        // nodes, until every converged lane holds queued triangles (or is done)
+        while (true) {
+            if (node < 0) {
+                if (sp == 0) {
+                    done = true;
+                    break;
+                }
+                const uint32_t e = (uint32_t)stack[--sp];
+                const int base = (int)(e & 0xFFFFFFu);
+                uint32_t m = e >> 24;
+                const int c = __ffs(m) - 1;
+                m &= m - 1;
+                if (m) stack[sp++] = base | (int)(m << 24);
+                node = base + c;
+            }
             if (++iters > iter_limit) {  // each node is visited at most once per line
                 err |= 2;
+                done = true;
                 break;
             }
             if (COUNT) n_nodes++;
@@ -347,7 +374,7 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
                 if (j < nch && tn <= tf) hit |= 1u << j;
             }
             const int4 r0 = __ldg(reinterpret_cast<const int4*>(nd + 4));
-            uint32_t lm = hit >> nint;  // leaf children
+            uint32_t lm = hit >> nint;  // leaf children: queue their triangles
             if (lm) {
                 const int4 r1 = __ldg(reinterpret_cast<const int4*>(nd + 5));
                 while (lm) {
@@ -357,9 +384,13 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
                     const int first = leaf_first(ref), count = leaf_count(ref);
                     for (int p = first; p < first + count; ++p) {
                         if (p == exclude_pos) continue;
-                        if (COUNT) n_tris++;
-                        test_tri<SUM_S>(tv, L, d, Tthr, tauL, graze, p, t, hits, key, q, walk,
-                                        step);
+                        if (nq < kLeafQ) {
+                            lq[nq++] = p;
+                        } else {
+                            if (COUNT) n_tris++;
+                            test_tri<SUM_S>(tv, L, d, Tthr, tauL, graze, p, t, hits, key, q,
+                                            walk, step);
+                        }
                     }
                 }
             }
@@ -372,18 +403,18 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
                     else err |= 1;
                 }
                 node = r0.x + c;
-                continue;
+            } else {
+                node = -1;
             }
-            node = -1;
+            if (__all_sync(__activemask(), nq > 0)) break;
         }
-        if (sp == 0) break;
-        const uint32_t e = (uint32_t)stack[--sp];
-        const int base = (int)(e & 0xFFFFFFu);
-        uint32_t m = e >> 24;
-        const int c = __ffs(m) - 1;
-        m &= m - 1;
-        if (m) stack[sp++] = base | (int)(m << 24);
-        node = base + c;
+        // the queued triangles, all lanes together
+        for (int i = 0; i < nq; ++i) {
+            if (COUNT) n_tris++;
+            test_tri<SUM_S>(tv, L, d, Tthr, tauL, graze, lq[i], t, hits, key, q, walk, step);
+        }
+        nq = 0;
+        if (done) break;
     }
 }
 
