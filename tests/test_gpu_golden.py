@@ -1,0 +1,33 @@
+"""The CUDA path on the first workload against the stored oracle values
+(tests/golden/config1_oracle.csv): per query within 1e-4 * max|g| wherever
+neither side flagged a walk of that query as near-degenerate."""
+import numpy as np
+import pytest
+
+from paper_2305_04403_gb300 import inputs as I
+from test_golden import load_config1
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_config1_matches_stored_oracle_values():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_04403_gb300 import build as B
+    B.build()
+    import paper_2305_04403_gb300 as wob
+    g = load_config1()
+    v, f = I.icosphere(3)
+    vd = I.poly_eval(I.POLY_CONFIG1, v).astype(np.float32)
+    bvh = wob.build_bvh(wob.build_mesh(v, f))
+    prob = wob.Problem(bvh, data_mode=wob.DATA_VERTEX_P1, vertex_data=torch.from_numpy(vd).cuda())
+    q = g["q"].astype(np.float32)
+    d = {k: t.cpu().numpy() for k, t in wob.solve_debug(prob, q, 64, 4, seed=0, want_lines=False).items()}
+    ok = (g["flagged"] == 0) & (d["flag"].sum(axis=1) == 0)
+    assert ok.mean() > 0.5
+    tol = 1e-4 * np.abs(vd).max()
+    assert np.all(np.abs(d["est"][ok] - g["est"][ok]) <= tol)
+    # the production entry point gives the debug kernel's numbers
+    est, var = wob.solve(prob, q, 64, 4, seed=0)
+    assert np.array_equal(est.cpu().numpy(), d["est"])
