@@ -66,7 +66,9 @@ __global__ void __launch_bounds__(128, 8)
     const int lane = threadIdx.x & 31;
     const uint64_t seed = *seed_dev;
     __shared__ double slots[8 * 128];
+    __shared__ int leafq[kLeafQ * 128];
     const WalkSlot ws{slots + threadIdx.x, 128};
+    const LeafQueue lq{leafq + threadIdx.x, 128};
     int stack[kStackSize];
     int hits[kMaxHits];
     int err = 0;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(128, 8)
                 int wflag = 0;
                 per_walk[P.walk_base + local] =
                     dl_walk<false, false>(G, P.data, (double)P.phi, P.M, key, (uint32_t)qi, w, x,
-                                          -1, ws, stack, hits, err, wflag, nullptr, c);
+                                          -1, ws, stack, hits, err, wflag, nullptr, c, lq);
             }
         }
     }

@@ -44,7 +44,9 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
     const int64_t total = p.Q * (int64_t)p.N;
     const DLGeom G{p.nodes, p.tv, p.iter_limit, p.edge_thr_L, p.tauL, p.graze};
     __shared__ double slots[(GRAD ? 11 : 8) * 128];
+    __shared__ int leafq[kLeafQ * 128];
     const WalkSlot ws{slots + threadIdx.x, 128};
+    const LeafQueue lq{leafq + threadIdx.x, 128};
     int err = 0;
     int stack[kStackSize];
     int hits[kMaxHits];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
         }
         const double v = dl_walk<COUNT, DEBUG, GRAD>(
             G, p.data, (double)p.phi, p.M, key, q, w, x, start, ws, stack, hits, err, wflag,
-            DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c);
+            DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c, lq);
         p.per_walk[idx] = v;
         if (GRAD) {  // gradient of the same walk: first-step factor x walk value
             p.per_walk_grad[idx] = ws.get(8) * v;

@@ -303,17 +303,25 @@ __device__ __forceinline__ int pick4(int4 v, int j)
 // same as with immediate tests.
 constexpr int kLeafQ = 16;
 
+// Where a lane keeps its queued leaf triangles: entry i at base[i * stride]
+// (shared memory, structure of arrays, in the walk kernels; a local array
+// elsewhere).
+struct LeafQueue {
+    int* base;
+    int stride;
+    __device__ __forceinline__ int& operator[](int i) const { return base[i * stride]; }
+};
+
 template <bool COUNT, bool SUM_S>
-__device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
-                                           const float4* __restrict__ tv, const LinePre& L,
-                                           float3 d, float Tthr, float tauL, float graze,
-                                           int exclude_pos, Trav& t, int* hits, int* stack,
-                                           StreamKey key, uint32_t q, uint32_t walk,
-                                           uint32_t step, uint32_t& n_nodes, uint32_t& n_tris,
-                                           int& err, int iter_limit)
+__device__ __forceinline__ void trace_wide_q(const float4* __restrict__ wn,
+                                             const float4* __restrict__ tv, const LinePre& L,
+                                             float3 d, float Tthr, float tauL, float graze,
+                                             int exclude_pos, Trav& t, int* hits, int* stack,
+                                             StreamKey key, uint32_t q, uint32_t walk,
+                                             uint32_t step, uint32_t& n_nodes, uint32_t& n_tris,
+                                             int& err, int iter_limit, LeafQueue lq)
 {
     int node = 0, sp = 0, iters = 0, nq = 0;
-    int lq[kLeafQ];
     bool done = false;
     while (true) {
         // nodes, until every converged lane holds queued triangles (or is done)
@@ -416,6 +424,20 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
         nq = 0;
         if (done) break;
     }
+}
+
+template <bool COUNT, bool SUM_S>
+__device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
+                                           const float4* __restrict__ tv, const LinePre& L,
+                                           float3 d, float Tthr, float tauL, float graze,
+                                           int exclude_pos, Trav& t, int* hits, int* stack,
+                                           StreamKey key, uint32_t q, uint32_t walk,
+                                           uint32_t step, uint32_t& n_nodes, uint32_t& n_tris,
+                                           int& err, int iter_limit)
+{
+    int lq[kLeafQ];
+    trace_wide_q<COUNT, SUM_S>(wn, tv, L, d, Tthr, tauL, graze, exclude_pos, t, hits, stack, key,
+                               q, walk, step, n_nodes, n_tris, err, iter_limit, LeafQueue{lq, 1});
 }
 
 // The picked hit (leaf position) after the traversal; -1 if m == 0.
@@ -602,7 +624,7 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
                                           StreamKey key, uint32_t q, uint32_t w, double3 x0,
                                           int start_pos, const WalkSlot& ws, int* stack,
                                           int* hits, int& err, int& wflag, int32_t* line_m,
-                                          WalkCount& c)
+                                          WalkCount& c, LeafQueue lq)
 {
     enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP, GX, GY, GZ };  // GX..GZ: GRAD only
     if (GRAD) {
@@ -637,9 +659,9 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         Trav t;
         trav_init(t);
         uint32_t nn = 0, nt = 0;
-        trace_wide<COUNT, false>(G.nodes, G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, G.tauL,
-                                 G.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn, nt,
-                                 err, G.iter_limit);
+        trace_wide_q<COUNT, false>(G.nodes, G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, G.tauL,
+                                   G.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn, nt,
+                                   err, G.iter_limit, lq);
         if (COUNT) {
             c.lines++;
             c.nodes += nn;
