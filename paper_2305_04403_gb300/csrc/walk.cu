@@ -327,9 +327,9 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
             Trav t;
             trav_init(t);
             uint32_t nn = 0, nt = 0;
-            trace_wide<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
-                                     p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn,
-                                     nt, err, p.iter_limit);
+            trace_wide_now<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr,
+                                         p.tauL, p.graze, self, t, hits, stack, key, q, w,
+                                         (uint32_t)k, nn, nt, err, p.iter_limit);
             wflag |= t.flag;
             if (DEBUG && lm) lm[k] = t.m;
             if (t.m == 0) break;
