@@ -46,7 +46,7 @@ BYTES_NODE, BYTES_TRI = 96, 48
 # DRAM bytes (read + write) of one full-size k_dl_walks launch of this
 # workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
 # dram__bytes_write.sum (profiles/k_dl_walks_star6_wide.md).
-TRAFFIC_FULL = (29497, 1, 40.09e6 + 224.95e6)
+TRAFFIC_FULL = (29497, 1, 38.04e6 + 230.23e6)
 
 
 def _peaks():
