@@ -13,6 +13,12 @@ its nearest ideas are boundary caching, Sec. 3.2, and path reuse, Sec. 5):
   double-layer recursion of Sec. 4.1 with r in place of 2 phi g (and half of
   it on the last vertex, Sec. 4.1.2).  nu_t = 0 gives plain WoB exactly.
 
+Monte Carlo variant (cv_walks_mc, for meshes too large for quadrature):
+D nu_t (x0) and H nu_t (x_i) are each the mean of K one-line estimates --
+K independent all-hits lines from the point, weights (m/2) s from the query
+and -phi m s from a boundary vertex, the walk's own line weights -- so every
+term stays unbiased; only the variance grows.
+
 Quadrature: Radon's 7-point rule of degree 5 on every triangle; triangles
 whose centroid lies within `near` mesh edge lengths of the target point are
 split into 4^level sub-triangles, each with the same rule.  For H at a
@@ -331,6 +337,87 @@ def cv_walks(verts, tris, queries, walks: int, max_len: int, params, nodes: Node
         Dnt = np.array([quad_D(nodes, node_vals, q[j].astype(np.float64), near)
                         for j in range(Q)])
     return S.reshape(Q, walks), flag.reshape(Q, walks), Dnt
+
+
+MC_WALK_BIT = 0x80000000   # walk-index bit of the extra lines' streams
+
+
+def _mc_lines(verts, tris, x, excl, qi, wi, v, K, nu_t, first, phi, seed, problem, tau):
+    """K independent lines from each point x (its own triangle excl), the
+    pick y_j and its weight: (m/2) s from a query (first), -phi m s from a
+    boundary vertex (Table 1 kernels over the line-pick density, Sec. 4.4.1);
+    returns (1/K) sum_j weight_j nu_t(y_j) and the lines' flags."""
+    n = x.shape[0]
+    acc = np.zeros(n)
+    flag = np.zeros(n, bool)
+    for j in range(K):
+        keys = np.stack([qi, wi | MC_WALK_BIT, np.full(n, v * K + j)], 1).astype(np.uint32)
+        d, _ = O.line_axes(seed, problem, keys)
+        r = O.trace_lines(verts, tris, x, d, exclude=excl, keys=keys, seed=seed,
+                          problem=problem, tau=tau)
+        flag |= r["flag"].astype(bool)
+        hit = r["m"] > 0
+        if not hit.any():
+            continue
+        ms = r["m"][hit].astype(np.float64) * r["s"][hit]
+        wgt = 0.5 * ms if first else -phi * ms
+        acc[hit] += wgt * nu_t(r["y"][hit])
+    return acc / K, flag
+
+
+def cv_walks_mc(verts, tris, queries, walks: int, max_len: int, nu_t, K: int, poly,
+                seed: int = 0, problem: int = 0, phi: int = 1, tau: float = O.TAU):
+    """Residual walks with Monte Carlo estimates of the control variate's
+    integrals (no quadrature; for meshes too large for it):
+        u(x0) ~ D^ nu_t (x0) + sum_k P_k c_k r^(x_k),
+        r^ = 2 phi g - nu_t + H^ nu_t,
+    D^ and H^ the means over K independent all-hits lines from the point,
+    each an unbiased one-sample estimate of D nu_t resp. H nu_t (the walk's
+    own first and later line weights).  The extra lines of vertex v (0 = the
+    query) are the streams (query, walk | 2^31, v K + j).  nu_t: callable on
+    (n, 3) points, or None for nu_t = 0 (plain WoB).  Returns the per-walk
+    values (Q, N) and flags (Q, N) (a walk is flagged if any of its lines,
+    its own or an extra one, is near-degenerate)."""
+    q = np.asarray(queries, np.float32).reshape(-1, 3)
+    Q = q.shape[0]
+    nw = Q * walks
+    qi = np.repeat(np.arange(Q), walks).astype(np.int64)
+    wi = np.tile(np.arange(walks), Q).astype(np.int64)
+    x = q.astype(np.float64)[qi]
+    excl = np.full(nw, -1, np.int32)
+    S = np.zeros(nw)
+    P = np.ones(nw)
+    alive = np.ones(nw, bool)
+    flag = np.zeros(nw, bool)
+    zero = nu_t is None
+    if not zero:
+        S, f0 = _mc_lines(verts, tris, x, excl, qi, wi, 0, K, nu_t, True, phi, seed, problem, tau)
+        flag |= f0
+    for k in range(max_len):
+        idx = np.nonzero(alive)[0]
+        if idx.size == 0:
+            break
+        keys = np.stack([qi[idx], wi[idx], np.full(idx.size, k)], 1)
+        d, _ = O.line_axes(seed, problem, keys)
+        r = O.trace_lines(verts, tris, x[idx], d, exclude=excl[idx], keys=keys, seed=seed,
+                          problem=problem, tau=tau)
+        flag[idx] |= r["flag"].astype(bool)
+        hit = r["m"] > 0
+        alive[idx[~hit]] = False
+        idx, m, s, y, prim = idx[hit], r["m"][hit], r["s"][hit], r["y"][hit], r["prim"][hit]
+        ms = m.astype(np.float64) * s
+        P[idx] = 0.5 * ms if k == 0 else P[idx] * (-phi * ms)
+        src = 2.0 * phi * _poly(poly, y)
+        if not zero:
+            h, fl = _mc_lines(verts, tris, y, prim, qi[idx], wi[idx], k + 1, K, nu_t, False, phi,
+                              seed, problem, tau)
+            flag[idx] |= fl
+            src = src - nu_t(y) + h
+        c = 0.5 if k == max_len - 1 else 1.0
+        S[idx] += P[idx] * c * src
+        x[idx] = y
+        excl[idx] = prim
+    return S.reshape(Q, walks), flag.reshape(Q, walks)
 
 
 def _poly(c, p):
