@@ -413,6 +413,29 @@ int wob_cv_solve(const wob_problem *prob, wob_cv c, const float *params, const f
 void wob_cv_destroy(wob_cv c);
 
 /*
+ * Residual walks with Monte Carlo integrals, for meshes too large for the
+ * quadrature of wob_cv_solve (no wob_cv object: nothing scales with the
+ * mesh size but the traversal).  With nu = nu_t + rho (Table 1, Dirichlet
+ * double layer) the walk value is
+ *     D^ nu_t (x0) + sum_k P_k c_k [2 phi g(x_k) - nu_t(x_k) + H^ nu_t (x_k)],
+ * the walk's own recursion (Sec. 4.1, the 1/2 on the last vertex of
+ * Sec. 4.1.2) with the residual source, where D^ and H^ are means of K
+ * one-line estimates: K independent all-hits lines from the point (Sec.
+ * 4.4.1), each picking y_j with the walk's own line weight -- (m/2) s from
+ * the query, -phi m s from a boundary vertex -- times nu_t(y_j).  Unbiased
+ * for the truncated residual series; nu_t = 0 gives plain WoB.  Extra line
+ * j of vertex v (0 = the query) of walk w draws from the streams
+ * (query, w | 2^31, v K + j).  params: the network (device, wob_mlp_num_params
+ * floats).  sum / sumsq: device Q doubles, accumulated (+=) as in
+ * wob_solve_range; per_walk (device Q x walks, optional).  1 <= K <= 16,
+ * max_len <= 1024, walk indices below 2^31, Q x walks x K < 2^31 per call.
+ * Scratch: about Q x walks x (76 + 20 K) bytes, allocated on `stream`.
+ */
+int wob_cv_solve_mc(const wob_problem *prob, const float *params, const float *queries, int64_t Q,
+                    int64_t walk_begin, int32_t walks, int32_t max_len, int32_t K, uint64_t seed,
+                    double *sum, double *sumsq, double *per_walk, void *stream);
+
+/*
  * Area-uniform points on the mesh (device outputs: points n x 3 float,
  * prims n original triangle ids).  Point i is the area sample of the
  * counter-based stream (query i, walk 0, step 0) under key (seed ^ problem,

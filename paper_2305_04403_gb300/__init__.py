@@ -162,6 +162,8 @@ def load_library() -> ctypes.CDLL:
             "wob_cv_solve": ([ctypes.POINTER(_Problem), P, P, P, I64, I64, I32, I32, U64, P, P, P,
                               P, P], ctypes.c_int),
             "wob_cv_destroy": ([P], None),
+            "wob_cv_solve_mc": ([ctypes.POINTER(_Problem), P, P, I64, I64, I32, I32, I32, U64, P,
+                                 P, P, P], ctypes.c_int),
             "wob_sample_boundary": ([P, I64, U64, U32, P, P, P], ctypes.c_int),
             "wob_cv_train": ([ctypes.POINTER(_Problem), P, ctypes.POINTER(_CvTrainParams), P, P, P,
                               P, P], ctypes.c_int),
@@ -598,6 +600,19 @@ class ControlVariate:
         if h and _lib is not None:
             _lib.wob_cv_destroy(h)
             self._h = None
+
+
+def cv_solve_mc(problem: Problem, params, queries, walk_begin: int, walks: int, max_len: int,
+                K: int, sum_, sumsq, seed: int = 0, per_walk=None, stream=None):
+    """wob_cv_solve_mc: residual walks with Monte Carlo integrals of the
+    control variate (K extra lines per point); sum_ / sumsq accumulated."""
+    import torch
+    pp = _dev(params, torch.float32)
+    q = _dev(queries, torch.float32).reshape(-1, 3)
+    pc = problem._c()
+    _check(load_library().wob_cv_solve_mc(ctypes.byref(pc), _ptr(pp), _ptr(q), q.shape[0],
+                                          walk_begin, walks, max_len, K, seed, _ptr(sum_),
+                                          _ptr(sumsq), _ptr(per_walk), _stream(stream)))
 
 
 def solve_range(problem: Problem, queries, walk_begin: int, walks: int, max_len: int,

@@ -462,6 +462,95 @@ __global__ void __launch_bounds__(kQuadThreads) k_cvw_accum(WalkParams p, CvWalk
     }
 }
 
+// ------------------------------------------- Monte Carlo control variate
+// D nu_t (x0) and H nu_t (x_i) as means of K one-line estimates (no
+// quadrature: meshes of any size): K independent all-hits lines from the
+// point, the pick y_j with the walk's own line weights -- (m/2) s from the
+// query, -phi m s from a boundary vertex -- and nu_t(y_j) from the network.
+// Extra line j of vertex v (0 = the query) draws from the stream
+// (query, walk | 2^31, v K + j).
+constexpr uint32_t kMcWalkBit = 0x80000000u;
+
+struct CvMc {
+    float* pos;  // W x K x 3: picks of the extra lines
+    float* wgt;  // W x K: their weights (0: missed line, or the walk ended)
+    float* nut;  // W x K: the network at the picks
+    int K;
+};
+
+__global__ void __launch_bounds__(128, 4) k_cvmc_lines(WalkParams p, CvWalk st, CvMc mc, int v)
+{
+    const StreamKey key{p.key0, p.key1};
+    int stack[kStackSize];
+    int hits[kMaxHits];
+    int err = 0;
+    const int64_t n = st.W * mc.K;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / mc.K;
+        const int j = (int)(t - i * mc.K);
+        float* pp = mc.pos + 3 * t;
+        if (!st.alive[i]) {
+            mc.wgt[t] = 0.f;
+            pp[0] = pp[1] = pp[2] = 0.f;
+            continue;
+        }
+        const int64_t qi = i / p.N;
+        const uint32_t q = p.q_base + (uint32_t)qi;
+        const uint32_t w = (uint32_t)(p.walk_begin + (i - qi * p.N)) | kMcWalkBit;
+        const uint32_t step = (uint32_t)(v * mc.K + j);
+        const double3 x = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
+        const double3 d = line_axis(key, q, w, step);
+        const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
+                                   make_float3((float)d.x, (float)d.y, (float)d.z));
+        const float Tthr = p.edge_thr_L * fabsf(L.Sz);
+        Trav tr;
+        trav_init(tr);
+        uint32_t nn = 0, nt = 0;
+        trace_wide<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+                                 p.graze, st.self[i], tr, hits, stack, key, q, w, step, nn, nt,
+                                 err, p.iter_limit);
+        if (tr.m == 0) {
+            mc.wgt[t] = 0.f;
+            pp[0] = pp[1] = pp[2] = 0.f;
+            continue;
+        }
+        const int pos = select_hit(p.tv, tr, hits, key, q, w, step);
+        const Refined r = refine_hit(p.tv, pos, x, d);
+        const float ms = (float)(tr.m * r.s);
+        mc.wgt[t] = v == 0 ? 0.5f * ms : -(float)p.phi * ms;
+        pp[0] = (float)r.y.x;
+        pp[1] = (float)r.y.y;
+        pp[2] = (float)r.y.z;
+    }
+    if (err) atomicOr(p.error_word, err);
+}
+
+// k < 0: S = D^ nu_t (x0), the walk's start value.  k >= 0: the source
+// r^ = 2 phi g - nu_t + H^ nu_t at the vertex reached at step k, halved on
+// the last vertex (Sec. 4.1.2), times the weight product.
+__global__ void k_cvmc_accum(WalkParams p, CvWalk st, CvMc mc, int k)
+{
+    const double phi = (double)p.phi;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < st.W;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (k >= 0 && !st.alive[i]) continue;
+        double acc = 0.0;
+        for (int j = 0; j < mc.K; ++j)
+            acc += (double)mc.wgt[i * mc.K + j] * (double)mc.nut[i * mc.K + j];
+        acc /= (double)mc.K;
+        if (k < 0) {
+            st.S[i] = acc;
+            continue;
+        }
+        const double3 y = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
+        const double g = (double)dl_data(p.data, p.tv, st.self[i], y);
+        const double r = 2.0 * phi * g - (double)st.nut[i] + acc;
+        const double cw = (k == p.M - 1) ? 0.5 : 1.0;
+        st.S[i] = fma(st.P[i] * cw, r, st.S[i]);
+    }
+}
+
 // Area-uniform boundary points: point i is the area sample of the stream
 // (query i, walk 0, step 0) -- triangle by inverse CDF of the areas, then a
 // square-root-warped uniform point on it -- the same draw the single-layer
@@ -779,6 +868,85 @@ int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const f
     }
     cudaFreeAsync(buf, s);
     if (rc != WOB_OK) set_error("wob_cv_solve failed");
+    return rc;
+}
+
+int wob_cv_solve_mc(const wob_problem* prob, const float* params, const float* queries, int64_t Q,
+                    int64_t walk_begin, int32_t walks, int32_t max_len, int32_t K, uint64_t seed,
+                    double* sum, double* sumsq, double* per_walk, void* stream)
+{
+    clear_error();
+    if (!params || (Q > 0 && (!queries || !sum || !sumsq))) {
+        set_error("wob_cv_solve_mc: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    WOB_TRY(check_problem(prob));
+    WOB_TRY(check_sizes(Q, walk_begin, walks, max_len));
+    if (prob->kind != WOB_DIRICHLET_DL) {
+        set_error("wob_cv_solve_mc: needs WOB_DIRICHLET_DL");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    if (K < 1 || K > 16 || max_len > 1024 || walk_begin + walks > (int64_t)kMcWalkBit) {
+        set_error("wob_cv_solve_mc: 1 <= K <= 16, max_len <= 1024, walk indices below 2^31");
+        return WOB_ERR_INVALID_ARG;
+    }
+    if (Q == 0) return WOB_OK;
+    if (Q * (int64_t)walks * K > INT32_MAX) {
+        set_error("wob_cv_solve_mc: Q x walks x K must be below 2^31 per call");
+        return WOB_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    WalkParams p;
+    fill_params(p, prob, queries, nullptr, Q, walk_begin, walks, max_len, seed);
+    CvWalk st{};
+    st.W = Q * (int64_t)walks;
+    st.T = (int)p.T;
+    const size_t W = (size_t)st.W, WK = W * (size_t)K;
+    char* buf = nullptr;
+    const size_t bytes = W * (8 * 5 + 4 * 2 + 4 * 4 + 4) + WK * 4 * 5 + 256;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
+    st.x = (double*)buf;
+    st.S = st.x + 3 * W;
+    st.P = st.S + W;
+    st.self = (int*)(st.P + W);
+    st.alive = st.self + W;
+    st.vpos = (float*)(st.alive + W);
+    st.nut = st.vpos + 3 * W;
+    st.own = (int*)(st.nut + W);
+    CvMc mc;
+    mc.pos = (float*)(st.own + W);
+    mc.wgt = mc.pos + 3 * WK;
+    mc.nut = mc.wgt + WK;
+    mc.K = K;
+    int* err = (int*)(mc.nut + WK);
+    int rc = WOB_OK;
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    p.error_word = err;
+    const int threads = 128;
+    k_cvw_init<<<grid_for((const void*)k_cvw_init, threads, 0, st.W), threads, 0, s>>>(p, st);
+    const int g_trace = grid_for((const void*)k_cvw_trace, threads, 0, st.W);
+    const int g_lines = grid_for((const void*)k_cvmc_lines, threads, 0, (int64_t)WK);
+    const int g_acc = grid_for((const void*)k_cvmc_accum, threads, 0, st.W);
+    // D^ nu_t at the queries
+    k_cvmc_lines<<<g_lines, threads, 0, s>>>(p, st, mc, 0);
+    rc = mlp_forward(params, mc.pos, (int64_t)WK, mc.nut, s, 3);
+    if (rc == WOB_OK) k_cvmc_accum<<<g_acc, threads, 0, s>>>(p, st, mc, -1);
+    for (int k = 0; k < max_len && rc == WOB_OK; ++k) {
+        k_cvw_trace<<<g_trace, threads, 0, s>>>(p, st, k);
+        rc = mlp_forward(params, st.vpos, st.W, st.nut, s, 3);
+        if (rc != WOB_OK) break;
+        k_cvmc_lines<<<g_lines, threads, 0, s>>>(p, st, mc, k + 1);
+        rc = mlp_forward(params, mc.pos, (int64_t)WK, mc.nut, s, 3);
+        if (rc != WOB_OK) break;
+        k_cvmc_accum<<<g_acc, threads, 0, s>>>(p, st, mc, k);
+    }
+    if (rc == WOB_OK && cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
+    if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s);
+    if (rc == WOB_OK && per_walk)
+        if (cudaMemcpyAsync(per_walk, st.S, W * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            rc = WOB_ERR_CUDA;
+    cudaFreeAsync(buf, s);
+    if (rc != WOB_OK) set_error("wob_cv_solve_mc failed");
     return rc;
 }
 

@@ -263,3 +263,60 @@ def test_cv_estimate_is_unbiased_with_lower_variance(wob, sphere_cv, trained):
     plain = wob.solve_debug(prob, q, N, M, seed=0, want_lines=False)["per_walk"].cpu().numpy()
     ratio = pw.var(1, ddof=1).mean() / plain.var(1, ddof=1).mean()
     assert ratio < 0.05, ratio
+
+
+# ---- control variate with Monte Carlo integrals (wob_cv_solve_mc) ----------
+def _mc_run(wob, prob, params, q, walks, M, K, seed):
+    Q = len(q)
+    s = torch.zeros(Q, dtype=torch.float64, device="cuda")
+    ss = torch.zeros_like(s)
+    pw = torch.empty((Q, walks), dtype=torch.float64, device="cuda")
+    wob.cv_solve_mc(prob, params, q, 0, walks, M, K, s, ss, seed=seed, per_walk=pw)
+    return pw.cpu().numpy(), s.cpu().numpy(), ss.cpu().numpy()
+
+
+def test_cv_mc_zero_network_is_plain_wob(wob):
+    v, f, sh = I.star_mesh(4, 0.3, 6, 3, 0.5)
+    bvh = wob.build_bvh(wob.build_mesh(v, f))
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    q = I.ball_queries(40, 0.4, 6)
+    zero = np.zeros(wob.mlp_num_params(), np.float32)
+    pw, s, ss = _mc_run(wob, prob, zero, q, 33, 5, 3, 7)
+    plain = wob.solve_debug(prob, q, 33, 5, seed=7, want_lines=False)["per_walk"].cpu().numpy()
+    assert np.allclose(pw, plain, rtol=0, atol=1e-12 * np.abs(plain).max())
+    assert np.allclose(s, pw.sum(1), rtol=1e-12) and np.allclose(ss, (pw * pw).sum(1), rtol=1e-12)
+
+
+def test_cv_mc_random_network_vs_oracle(wob, sphere_cv):
+    """Same streams, same picks; the GPU network is BF16 (2e-2 relative), so
+    each of the 1 + K network values per vertex may differ by that much:
+    per walk within 3e-2 x 2 (M + 1) x max|nu_t| on the convex mesh (|P| = 1)."""
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1, tau=O.TAU)
+    flat, params = _params32(5)
+    q = I.ball_queries(7, 0.8, 12)
+    M, N, K = 3, 24, 3
+    pw, _, _ = _mc_run(wob, prob, flat, q, N, M, K, 13)
+    S, flag = C.cv_walks_mc(v, f, q, N, M, lambda y: C.mlp_forward(params, y)[0], K,
+                            I.POLY_CONFIG1, seed=13)
+    y, _ = O.area_points(v, f, 2000, seed=1)
+    scale = np.abs(C.mlp_forward(params, y)[0]).max()
+    ok = ~flag
+    assert ok.mean() > 0.8
+    err = np.abs(pw - S)[ok]
+    assert np.all(err <= 3e-2 * 2 * (M + 1) * scale), err.max() / scale
+
+
+def test_cv_mc_trained_network_unbiased_with_lower_variance(wob, sphere_cv, trained):
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob, p, _ = trained
+    q = I.ball_queries(256, 0.9, 1)
+    N, M, K = 256, 2, 4
+    pw, _, _ = _mc_run(wob, prob, p, q, N, M, K, 0)
+    exact = I.poly_eval(I.POLY_CONFIG1, q.astype(np.float64))
+    se = pw.std(1, ddof=1) / np.sqrt(N)
+    # the network carries the tail: no visible truncation bias at M = 2
+    assert np.all(np.abs(pw.mean(1) - exact) <= 5 * se + 3e-3), np.abs(pw.mean(1) - exact).max()
+    plain = wob.solve_debug(prob, q, N, M, seed=0, want_lines=False)["per_walk"].cpu().numpy()
+    ratio = pw.var(1, ddof=1).mean() / plain.var(1, ddof=1).mean()
+    assert ratio < 0.6, ratio
