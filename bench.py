@@ -705,6 +705,9 @@ def run_cv(args):
         cvo.solve_range(prob, p, q, 0, args.cv_batch, args.cv_len, s_, torch.zeros_like(s_),
                         dnt=d_)
         rmse(d_.double() + s_ / args.cv_batch)
+        if args.cv_mc:
+            wob.cv_solve_mc(prob, p, q, 0, args.cv_batch, args.cv_len, args.cv_mc, s_,
+                            torch.zeros_like(s_))
         wob.solve_range(prob, q, 0, 512, 4, s_, torch.zeros_like(s_))
         rmse(s_ / 512)
         lap(ev())
@@ -729,16 +732,29 @@ def run_cv(args):
         curve, n_cv = [], 0
         t0 = ev()
         while True:
-            cvo.solve_range(prob, p, q, n_cv, args.cv_batch, args.cv_len, s_, ss, seed=SEED,
-                            dnt=dnt if n_cv == 0 else None)
-            launches += 2 + 3 * args.cv_len + (1 if n_cv == 0 else 0)
-            n_cv += args.cv_batch
-            e = rmse(dnt.double() + s_ / n_cv)
+            if args.cv_mc:   # Monte Carlo integrals: D nu_t is inside the walk values
+                wob.cv_solve_mc(prob, p, q, n_cv, args.cv_batch, args.cv_len, args.cv_mc, s_, ss,
+                                seed=SEED)
+                launches += 5 + 4 * args.cv_len
+                n_cv += args.cv_batch
+                e = rmse(s_ / n_cv)
+            else:
+                cvo.solve_range(prob, p, q, n_cv, args.cv_batch, args.cv_len, s_, ss, seed=SEED,
+                                dnt=dnt if n_cv == 0 else None)
+                launches += 2 + 3 * args.cv_len + (1 if n_cv == 0 else 0)
+                n_cv += args.cv_batch
+                e = rmse(dnt.double() + s_ / n_cv)
             curve.append([lap(t0), n_cv, e])
             if e <= target or n_cv >= args.cv_max_walks:
                 break
         cv_s = curve[-1][0]
         cv_var = float(((ss - s_ * s_ / n_cv) / (n_cv - 1)).mean().item())
+        cv_projection = None
+        if curve[-1][2] > target:  # cap reached: project as for plain WoB
+            b2 = max(curve[-1][2] ** 2 - cv_var / n_cv, 0.0)
+            need = cv_var / (target ** 2 - b2) if b2 < target ** 2 else None
+            cv_projection = {"bias2_estimate": b2, "walks_needed": need,
+                             "time_to_rmse_s": cv_s * need / n_cv if need else None}
 
         # ---- plain WoB: rate and variance on all queries, bias on a subset
         plain = {}
@@ -800,11 +816,12 @@ def run_cv(args):
                                "densities (64 walks, M = 4)",
                    "cv_len": args.cv_len, "cv_batch": args.cv_batch,
                    "cv_epochs": args.cv_epochs, "cv_lr": f"1e-3, last {args.cv_tail} epochs 1e-4",
-                   "quadrature": "Radon 7-point, level-2 near "
-                   "field within 2 edge lengths"},
+                   "quadrature": ("none: D nu_t and H nu_t from %d extra all-hits lines per "
+                                  "point (Monte Carlo)" % args.cv_mc) if args.cv_mc else
+                                 "Radon 7-point, level-2 near field within 2 edge lengths"},
         "cv": {"train_s": train_s, "solve_s": cv_s, "walks": n_cv, "rmse": curve[-1][2],
                "per_walk_var": cv_var, "final_train_loss": float(loss[-1].mean().item()),
-               "curve": curve},
+               "curve": curve, "projection_if_capped": cv_projection},
         "plain": plain,
         "best_plain": {"M": Mb, "time_to_rmse_s": best_t, "projected": True,
                        "direct_check": {"walks": n_pl, "seconds": el, "rmse": e_pl,
@@ -880,6 +897,9 @@ def main():
     ap.add_argument("--cv-queries", type=int, default=65536,
                     help="queries of the cv workload (the metric is defined at 65,536)")
     ap.add_argument("--cv-batch", type=int, default=64)
+    ap.add_argument("--cv-mc", type=int, default=0,
+                    help="cv workload: Monte Carlo integrals with this many extra lines per "
+                         "point instead of quadrature (0 = quadrature)")
     ap.add_argument("--cv-epochs", type=int, default=23)
     ap.add_argument("--cv-tail", type=int, default=3, help="final epochs at lr 1e-4")
     ap.add_argument("--cv-max-walks", type=int, default=1 << 16)
