@@ -114,6 +114,26 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+def _l2_probe(mb: int = 64, reps: int = 20) -> float:
+    """L2 read bandwidth (GB/s): a streaming reduction over a buffer that
+    fits in the 129 MB L2, timed with CUDA events after a warm-up pass."""
+    import torch
+    buf = torch.ones(mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    out = torch.empty((), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        torch.sum(buf, out=out)
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        torch.sum(buf, out=out)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return buf.numel() * 4 / (float(np.median(ms)) / 1e3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -209,6 +229,7 @@ def run_ours(args):
         return None
 
     peaks, which = _peaks()
+    l2_gbs = _l2_probe()
     per_launch_s = total_ms / 1e3 / args.steps
     ops = (st["node_visits"] * OPS_NODE + st["tri_tests"] * OPS_TRI + st["hits"] * OPS_HIT
            + st["lines"] * OPS_LINE)
@@ -240,6 +261,10 @@ def run_ours(args):
                                     f"({which} sm_max_mhz)"},
         "memory": {"l1_l2_bytes_per_step": bytes_step,
                    "achieved_gbs": bytes_step / per_launch_s / 1e9,
+                   "l2_probe_gbs": l2_gbs,
+                   "frac_of_l2_probe": bytes_step / per_launch_s / 1e9 / l2_gbs,
+                   "l2_probe": "streaming read (torch sum) of a 64 MB float32 buffer, "
+                               "L2-resident after a first pass; median of 20",
                    "hbm_peak_gbs": peaks.get("hbm_gbs"),
                    "per_line": {"nodes": st["node_visits"] / lines, "tris": st["tri_tests"] / lines,
                                 "hits": st["hits"] / lines, "flagged": st["flagged"] / lines}},
