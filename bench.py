@@ -119,15 +119,14 @@ def _l2_probe(mb: int = 64, reps: int = 20) -> float:
     fits in the 129 MB L2, timed with CUDA events after a warm-up pass."""
     import torch
     buf = torch.ones(mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
-    out = torch.empty((), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(3):
-        torch.sum(buf, out=out)
+        buf.sum()
     ms = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        torch.sum(buf, out=out)
+        buf.sum()
         b.record(stream)
         b.synchronize()
         ms.append(a.elapsed_time(b))
