@@ -138,11 +138,14 @@ __device__ __forceinline__ AreaPoint area_point(const WalkParams& p, StreamKey k
 {
     AreaPoint a;
     const u32x4 u = stream_block(key, q, w, step, kPurposeArea, attempt, 0u);
-    const double target = u53(u.x, u.y) * p.area;
+    // Non-negative doubles order as their bit patterns: the search compares
+    // 64-bit integers (the same decisions as double compares, off the FP64
+    // pipe, which issues at 1/64 of the FP32 rate on this GPU).
+    const long long target = __double_as_longlong(u53(u.x, u.y) * p.area);
     int64_t lo = 0, hi = p.T - 1;
     while (lo < hi) {
         const int64_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(p.cdf + mid) > target) hi = mid; else lo = mid + 1;
+        if (__double_as_longlong(__ldg(p.cdf + mid)) > target) hi = mid; else lo = mid + 1;
     }
     const double su = sqrt(u24(u.z)), u2 = u24(u.w);
     a.b0 = 1.0 - su;
@@ -181,6 +184,56 @@ __device__ __forceinline__ double sl_kernel(const WalkParams& p, int bx, double3
     const double phi = (double)p.phi;
     if (bx == WOB_BC_NEUMANN) return -2.0 * phi * dgdn;
     return -2.0 * phi * (dgdn + (double)p.alpha * G);
+}
+
+// The same kernel with the FP64 difference vector, squared distance and
+// r . n_x (r . n_x ~ r^2 / 2 for nearby points of a smooth surface: it
+// cancels, and in FP32 its relative error would grow as 1 / r) and the rest
+// in FP32: 1 / r by rsqrt, G, dG/dn_x.  Relative error about 1e-6 -- inside
+// the 1e-5 walk tolerance -- at a fraction of the FP64 cost (an FP64 sqrt
+// and two FP64 divides).  Caller guarantees r >= rmin.  Used where the
+// kernel value only weights a sample; resampling (whose pick compares
+// running sums) keeps sl_kernel.
+__device__ __forceinline__ double sl_kernel32(const WalkParams& p, int bx, double3 r, double r2,
+                                              double3 nx)
+{
+    constexpr float kInv4Pi = 0.0795774715459476678f;
+    const float ri = rsqrtf((float)r2);
+    const float G = kInv4Pi * ri;
+    if (bx < 0) return (double)G;
+    if (bx == WOB_BC_DIRICHLET) return -(double)(p.kmix / p.pk * G);
+    const double rn = r.x * nx.x + r.y * nx.y + r.z * nx.z;
+    const double phi = (double)p.phi;
+    if (bx == WOB_BC_NEUMANN) return -2.0 * phi * (double)((float)rn * ri * ri * G);
+    // Robin: G (alpha + r.n / r^2), the bracket in FP64 (its terms can cancel,
+    // and the walk's later terms inherit its relative error); 1 / r^2 from
+    // the FP32 rsqrt and one FP64 Newton step (relative error ~1e-13).
+    double ri2 = (double)ri * (double)ri;
+    ri2 = ri2 * (2.0 - r2 * ri2);
+    return -2.0 * phi * (double)G * ((double)p.alpha + rn * ri2);
+}
+
+// sl_data with the point-source field in FP32 from an FP64 difference and
+// the normal derivative n . grad h in FP64 (it cancels where the field runs
+// along the surface); polynomial and P1 data as sl_data (a polynomial's
+// monomials cancel, and its FP64 evaluation costs little).
+__device__ __forceinline__ double sl_data32(const WalkParams& p, int64_t j, double3 y, double b0,
+                                            double b1, double b2, double3 n, int bc)
+{
+    const DataDev& D = p.data;
+    if (D.mode == WOB_DATA_VERTEX_P1) {
+        const int32_t* t = D.tris + 3 * j;
+        return b0 * __ldg(D.vdata + t[0]) + b1 * __ldg(D.vdata + t[1]) + b2 * __ldg(D.vdata + t[2]);
+    }
+    if (D.mode == WOB_DATA_POLY) return sl_data(p, j, y, b0, b1, b2, n, bc);
+    const double dx = y.x - D.x0[0], dy = y.y - D.x0[1], dz = y.z - D.x0[2];
+    const float ri = rsqrtf((float)(dx * dx + dy * dy + dz * dz));
+    const float h = D.scale * ri;
+    const float f = -h * ri * ri;
+    const float gx = f * (float)dx, gy = f * (float)dy, gz = f * (float)dz;
+    if (bc == WOB_BC_DIRICHLET) return (double)h;
+    const double dhdn = n.x * (double)gx + n.y * (double)gy + n.z * (double)gz;
+    return bc == WOB_BC_ROBIN ? dhdn + (double)p.alpha * (double)h : dhdn;
 }
 
 // Single-layer walks (Table 1, Sec. 4.3), one thread per walk:
@@ -228,9 +281,10 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
                 wfac = 1.0 / (1.0 - (double)p.pk);
             } else if (p.ris <= 1) {
                 a = area_point(p, key, q, w, (uint32_t)k);
-                const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
-                if (sqrt(rx * rx + ry * ry + rz * rz) < rmin) break;  // empty sample
-                wfac = area * sl_kernel(p, bx, x, nx, a.y, rmin);
+                const double3 r = make_double3(a.y.x - x.x, a.y.y - x.y, a.y.z - x.z);
+                const double r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                if (r2 < rmin * rmin) break;  // empty sample
+                wfac = area * sl_kernel32(p, bx, r, r2, nx);
             } else {
                 double sumw = 0.0;
                 for (int c = 0; c < p.ris; ++c) {
@@ -256,9 +310,8 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
             }
             if (k == 0) W0 = wfac; else P *= wfac;
             const int by = p.bc_type ? (int)__ldg(p.bc_type + a.j) : uniform_bc;
-            double src = by == WOB_BC_DIRICHLET
-                             ? (double)p.kmix * sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by)
-                             : 2.0 * phi * sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by);
+            const double dat = sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by);
+            double src = by == WOB_BC_DIRICHLET ? (double)p.kmix * dat : 2.0 * phi * dat;
             if (k == p.M - 1) src *= 0.5;
             S = fma(P, src, S);
             x = a.y;
@@ -311,12 +364,14 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
             // source at vertex k
             const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
             const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
-            const double rl = sqrt(rx * rx + ry * ry + rz * rz);
-            if (rl >= rmin) {
-                const double f = sl_data(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 >= rmin * rmin) {
+                const double f =
+                    sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
                 double c = (k == 0) ? phi : 2.0 * phi;
                 if (k == p.M) c *= 0.5;
-                S = fma(P * c * p.area / (kFourPi * rl), f, S);
+                const double G = (double)(0.0795774715459476678f * rsqrtf((float)r2));
+                S = fma(P * c * p.area * G, f, S);
             }
             if (k == p.M) break;
             // line from vertex k to vertex k + 1
