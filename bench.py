@@ -133,6 +133,18 @@ def _l2_probe(mb: int = 64, reps: int = 20) -> float:
     return buf.numel() * 4 / (float(np.median(ms)) / 1e3) / 1e9
 
 
+def _over_ranks(dist, x: float, op: str, device) -> float:
+    """Max or sum of a per-rank number over the ranks (x itself without a
+    process group): the timed region is the slowest rank's, the work is
+    every rank's."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -184,11 +196,9 @@ def run_ours(args):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = _over_ranks(dist, sum(step_ms), "max", "cuda")
+    lines_all = _over_ranks(dist, float(lines), "sum", "cuda")  # every replica's line queries
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     clocks = clk.summary()
 
@@ -216,11 +226,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         host_step()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _over_ranks(dist, time.perf_counter() - t0, "max", "cuda")
 
     if rank != 0:
         if dist:
@@ -236,7 +242,7 @@ def run_ours(args):
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
     achieved_ops = ops / per_launch_s / 1e12
     bytes_step = st["node_visits"] * BYTES_NODE + st["tri_tests"] * BYTES_TRI
-    value = ws * lines * args.steps / (total_ms / 1e3)
+    value = lines_all * args.steps / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -248,7 +254,7 @@ def run_ours(args):
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": f"{ws} independent replica(s)"},
         "clocks": clocks,
-        "e2e": {"value": ws * lines * e2e_steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": lines_all * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": Q * 12, "d2h_bytes_per_step": Q * 16},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
