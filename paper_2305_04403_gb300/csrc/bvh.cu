@@ -455,7 +455,7 @@ int build_wide(BvhDev& b, const MeshDev& m, cudaStream_t s)
     WOB_CUDA_TRY(cudaMallocAsync((void**)&counter, sizeof(int), s));
     const int one = 1;
     WOB_CUDA_TRY(cudaMemcpyAsync(counter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-    const float pad = (float)(4e-6 * m.L);
+    const float pad = (float)(kBoxPad * m.L);
     const float3 rlo = make_float3((float)m.lo[0] - pad, (float)m.lo[1] - pad, (float)m.lo[2] - pad);
     const float3 rhi = make_float3((float)m.hi[0] + pad, (float)m.hi[1] + pad, (float)m.hi[2] + pad);
     int64_t w_begin = 0, w_end = 1;
@@ -557,7 +557,7 @@ int build_bvh_impl(MeshDev& m, int leaf_size, cudaStream_t s, BvhDev& b)
         WOB_CUDA_TRY(cudaGetLastError());
     }
     // pad boxes so that FP32 slab tests never cull a triangle the line meets
-    const float pad = (float)(4e-6 * m.L);
+    const float pad = (float)(kBoxPad * m.L);
     k_refit<<<grid_for((const void*)k_refit, threads, 0, n), threads, 0, s>>>(
         m.verts, m.tris, b.order, n, pad, left, right, parent_node, parent_leaf, leaf_boxes,
         node_boxes, visits);

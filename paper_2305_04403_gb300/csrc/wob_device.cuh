@@ -281,11 +281,16 @@ __device__ __forceinline__ void test_tri(const float4* __restrict__ tv, const Li
 // entry is a group (first interior child, mask of children still to visit),
 // at most one per level.
 // ---------------------------------------------------------------------------
-// Byte b of w as an exact float: the byte is placed in the low mantissa of
-// 2^23 (one byte permute), then 2^23 is subtracted.
+// Byte q = b of w as the exact float 1 + q 2^-15 (one byte permute: q into
+// the second mantissa byte under the exponent of 1.0).  A plane q of a node
+// with quantisation step s lies at t = q s / d + b = (1 + q 2^-15) a + (b - a)
+// with a = 2^15 s / d: one FMA per plane with a and b - a fixed per node.
+// Rounding b - a costs up to s / 512 in position (1.53e-5 of the node's
+// extent, below the boxes' padding of 2e-5 L), so the box test stays
+// conservative.
 __device__ __forceinline__ float dequant(uint32_t w, int b)
 {
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u | (uint32_t)b)) - 8388608.0f;
+    return __uint_as_float(__byte_perm(w, 0x3F800000u, 0x7604u | ((uint32_t)b << 4)));
 }
 
 __device__ __forceinline__ int pick4(int4 v, int j)
@@ -349,12 +354,13 @@ __device__ __forceinline__ void trace_wide_q(const float4* __restrict__ wn,
             const float4 h = __ldg(nd);
             const uint32_t hdr = __float_as_uint(h.w);
             const int nint = (hdr >> 24) & 15, nch = hdr >> 28;
-            // slab parameter of a quantised plane: (origin + q s - o) / d = q a + b
-            const float ax = __uint_as_float((hdr & 255u) << 23) * L.ix;
-            const float ay = __uint_as_float(((hdr >> 8) & 255u) << 23) * L.iy;
-            const float az = __uint_as_float(((hdr >> 16) & 255u) << 23) * L.iz;
-            const float bx = fmaf(h.x, L.ix, -L.oix), by = fmaf(h.y, L.iy, -L.oiy),
-                        bz = fmaf(h.z, L.iz, -L.oiz);
+            // slab parameter of a quantised plane: (origin + q s - o) / d
+            // = (1 + q 2^-15) a + b with a = 2^15 s / d (see dequant)
+            const float ax = __uint_as_float(((hdr & 255u) + 15u) << 23) * L.ix;
+            const float ay = __uint_as_float((((hdr >> 8) & 255u) + 15u) << 23) * L.iy;
+            const float az = __uint_as_float((((hdr >> 16) & 255u) + 15u) << 23) * L.iz;
+            const float bx = fmaf(h.x, L.ix, -L.oix) - ax, by = fmaf(h.y, L.iy, -L.oiy) - ay,
+                        bz = fmaf(h.z, L.iz, -L.oiz) - az;
             const uint4 qx = __ldg(reinterpret_cast<const uint4*>(nd + 1));
             const uint4 qy = __ldg(reinterpret_cast<const uint4*>(nd + 2));
             const uint4 qz = __ldg(reinterpret_cast<const uint4*>(nd + 3));
@@ -465,12 +471,13 @@ __device__ __forceinline__ void trace_wide_now(const float4* __restrict__ wn,
             const float4 h = __ldg(nd);
             const uint32_t hdr = __float_as_uint(h.w);
             const int nint = (hdr >> 24) & 15, nch = hdr >> 28;
-            // slab parameter of a quantised plane: (origin + q s - o) / d = q a + b
-            const float ax = __uint_as_float((hdr & 255u) << 23) * L.ix;
-            const float ay = __uint_as_float(((hdr >> 8) & 255u) << 23) * L.iy;
-            const float az = __uint_as_float(((hdr >> 16) & 255u) << 23) * L.iz;
-            const float bx = fmaf(h.x, L.ix, -L.oix), by = fmaf(h.y, L.iy, -L.oiy),
-                        bz = fmaf(h.z, L.iz, -L.oiz);
+            // slab parameter of a quantised plane: (origin + q s - o) / d
+            // = (1 + q 2^-15) a + b with a = 2^15 s / d (see dequant)
+            const float ax = __uint_as_float(((hdr & 255u) + 15u) << 23) * L.ix;
+            const float ay = __uint_as_float((((hdr >> 8) & 255u) + 15u) << 23) * L.iy;
+            const float az = __uint_as_float((((hdr >> 16) & 255u) + 15u) << 23) * L.iz;
+            const float bx = fmaf(h.x, L.ix, -L.oix) - ax, by = fmaf(h.y, L.iy, -L.oiy) - ay,
+                        bz = fmaf(h.z, L.iz, -L.oiz) - az;
             const uint4 qx = __ldg(reinterpret_cast<const uint4*>(nd + 1));
             const uint4 qy = __ldg(reinterpret_cast<const uint4*>(nd + 2));
             const uint4 qz = __ldg(reinterpret_cast<const uint4*>(nd + 3));

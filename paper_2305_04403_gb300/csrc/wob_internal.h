@@ -22,6 +22,9 @@ constexpr int64_t kMaxTriangles = (int64_t(1) << 28) - 2;
 constexpr float kDefaultTau = 2e-6f;
 constexpr float kGraze = 1e-4f;
 constexpr int kMaxLen = 4096;
+// Box padding in units of the mesh diagonal L: above the slab test's
+// rounding (at most 1.53e-5 of a node's extent, see dequant).
+constexpr double kBoxPad = 2e-5;
 
 // Per-triangle unit normal and area, FP64 (32 bytes, read as two 16-byte loads).
 struct alignas(32) NormalArea {
