@@ -46,7 +46,7 @@ BYTES_NODE, BYTES_TRI = 96, 48
 # DRAM bytes (read + write) of one full-size k_dl_walks launch of this
 # workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
 # dram__bytes_write.sum (profiles/k_dl_walks_star6_wide.md).
-TRAFFIC_FULL = (29497, 1, 38.04e6 + 230.23e6)
+TRAFFIC_FULL = (29497, 1, 35.49e6 + 228.46e6)
 
 
 def _peaks():
@@ -114,22 +114,25 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
-def _l2_probe(mb: int = 64, reps: int = 20) -> float:
-    """L2 read bandwidth (GB/s): a streaming reduction over a buffer that
-    fits in the 129 MB L2, timed with CUDA events after a warm-up pass."""
+def _l2_probe(mb: int = 96, passes: int = 20, reps: int = 5) -> float:
+    """L2 read bandwidth (GB/s): the library's streaming-read probe (16-byte
+    loads that bypass L1, every SM) over a buffer that fits in the 129 MB
+    L2, `passes` reads per call, CUDA events, median of `reps` calls after a
+    warm-up call."""
     import torch
+    import paper_2305_04403_gb300 as wob
     buf = torch.ones(mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(3):
-        buf.sum()
+    wob.probe_l2_read(buf, passes, out)
     ms = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        buf.sum()
+        wob.probe_l2_read(buf, passes, out)
         b.record(stream)
         b.synchronize()
-        ms.append(a.elapsed_time(b))
+        ms.append(a.elapsed_time(b) / passes)
     return buf.numel() * 4 / (float(np.median(ms)) / 1e3) / 1e9
 
 
@@ -268,8 +271,9 @@ def run_ours(args):
                    "achieved_gbs": bytes_step / per_launch_s / 1e9,
                    "l2_probe_gbs": l2_gbs,
                    "frac_of_l2_probe": bytes_step / per_launch_s / 1e9 / l2_gbs,
-                   "l2_probe": "streaming read (torch sum) of a 64 MB float32 buffer, "
-                               "L2-resident after a first pass; median of 20",
+                   "l2_probe": "wob_probe_l2_read: 20 streaming reads (16-byte loads, L1 "
+                               "bypassed) of a 96 MB buffer, L2-resident after a warm-up "
+                               "call; median of 5 calls",
                    "hbm_peak_gbs": peaks.get("hbm_gbs"),
                    "per_line": {"nodes": st["node_visits"] / lines, "tris": st["tri_tests"] / lines,
                                 "hits": st["hits"] / lines, "flagged": st["flagged"] / lines}},

@@ -522,6 +522,17 @@ int wob_line_axes(uint64_t seed, uint32_t problem, const uint32_t *qws, int64_t 
 int wob_philox4x32_10(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out,
                       void *stream);
 
+/*
+ * Measurement probe (the paper has no counterpart): `passes` streaming reads
+ * of the device buffer buf (bytes, a multiple of 16, 16-byte aligned) with
+ * 16-byte loads that bypass L1, by a grid of resident blocks on every SM;
+ * the sum of the read floats goes to *out (device float, overwritten).  Timed
+ * around the call on a buffer that fits in L2, it gives the L2 read
+ * bandwidth the line traversal's node fetches are measured against.
+ * Errors: WOB_ERR_INVALID_ARG (bad size or alignment), WOB_ERR_CUDA.
+ */
+int wob_probe_l2_read(const void *buf, int64_t bytes, int32_t passes, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

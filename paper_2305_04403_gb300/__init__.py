@@ -162,6 +162,7 @@ def load_library() -> ctypes.CDLL:
             "wob_cv_solve": ([ctypes.POINTER(_Problem), P, P, P, I64, I64, I32, I32, U64, P, P, P,
                               P, P], ctypes.c_int),
             "wob_cv_destroy": ([P], None),
+            "wob_probe_l2_read": ([P, I64, I32, P, P], ctypes.c_int),
             "wob_cv_solve_mc": ([ctypes.POINTER(_Problem), P, P, I64, I64, I32, I32, I32, U64, P,
                                  P, P, P], ctypes.c_int),
             "wob_sample_boundary": ([P, I64, U64, U32, P, P, P], ctypes.c_int),
@@ -600,6 +601,13 @@ class ControlVariate:
         if h and _lib is not None:
             _lib.wob_cv_destroy(h)
             self._h = None
+
+
+def probe_l2_read(buf, passes: int, out, stream=None):
+    """wob_probe_l2_read: `passes` streaming reads of the CUDA tensor buf
+    (L1 bypassed); out (CUDA float32 scalar) receives the sum."""
+    _check(load_library().wob_probe_l2_read(_ptr(buf), buf.numel() * buf.element_size(), passes,
+                                            _ptr(out), _stream(stream)))
 
 
 def cv_solve_mc(problem: Problem, params, queries, walk_begin: int, walks: int, max_len: int,

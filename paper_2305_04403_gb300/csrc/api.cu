@@ -612,6 +612,17 @@ int wob_line_axes(uint64_t seed, uint32_t problem, const uint32_t* qws, int64_t 
                             (cudaStream_t)stream);
 }
 
+int wob_probe_l2_read(const void* buf, int64_t bytes, int32_t passes, float* out, void* stream)
+{
+    clear_error();
+    if (!buf || !out || bytes < 16 || bytes % 16 != 0 || ((uintptr_t)buf & 15) != 0 ||
+        passes < 1) {
+        set_error("wob_probe_l2_read: invalid arguments");
+        return WOB_ERR_INVALID_ARG;
+    }
+    return launch_probe_read((const float4*)buf, bytes / 16, passes, out, (cudaStream_t)stream);
+}
+
 int wob_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                       void* stream)
 {

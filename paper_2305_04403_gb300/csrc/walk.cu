@@ -957,6 +957,31 @@ int launch_line_axes(uint32_t key0, uint32_t key1, const uint32_t* qws, int64_t 
     return WOB_OK;
 }
 
+// Streaming read of n float4 (L1 bypassed), `passes` times; one atomic per
+// warp keeps the loads.
+__global__ void __launch_bounds__(256) k_probe_read(const float4* __restrict__ buf, int64_t n,
+                                                    int passes, float* __restrict__ out)
+{
+    float acc = 0.f;
+    for (int r = 0; r < passes; ++r)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const float4 v = __ldcg(buf + i);
+            acc += (v.x + v.y) + (v.z + v.w);
+        }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+int launch_probe_read(const float4* buf, int64_t n, int passes, float* out, cudaStream_t s)
+{
+    WOB_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(float), s));
+    const int grid = grid_for((const void*)k_probe_read, 256, 0, (int64_t)1 << 40);
+    k_probe_read<<<grid, 256, 0, s>>>(buf, n, passes, out);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
 int launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                   cudaStream_t s)
 {

@@ -55,6 +55,8 @@ int launch_dl_walks(const WalkParams& p, bool counted, bool debug, cudaStream_t 
 int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s);
 int launch_nd_walks(const WalkParams& p, bool debug, cudaStream_t s);
 // forward single-layer Neumann paths and their connection to the queries
+// streaming read probe (wob_probe_l2_read)
+int launch_probe_read(const float4* buf, int64_t n, int passes, float* out, cudaStream_t s);
 int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double beta,
                    const float* queries, int64_t Q, double* zpos, double* zw, uint8_t* flags,
                    double* est, double* var, cudaStream_t s);
