@@ -114,6 +114,7 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     p.inv_order = b.inv_order;
     p.iter_limit = (int)(4 * b.n_wide + 64);
     p.verts = m.verts;
+    p.verts_d = m.verts_d;
     p.tris = m.tris;
     p.tri_n = m.tri_n;
     p.cdf = m.cdf;

@@ -215,13 +215,24 @@ int inclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s)
 template int inclusive_scan<double>(const double*, double*, int64_t, cudaStream_t);
 template int inclusive_scan<int>(const int*, int*, int64_t, cudaStream_t);
 
+// FP64 copy of the vertex positions: area samples are formed in FP64 from
+// it without a conversion per coordinate (exact: every float is a double).
+__global__ void k_to_f64(const float* __restrict__ in, int64_t n, double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
 void free_mesh(MeshDev& m)
 {
     cudaFree(m.verts);
+    cudaFree(m.verts_d);
     cudaFree(m.tris);
     cudaFree(m.tri_n);
     cudaFree(m.cdf);
     m.verts = nullptr;
+    m.verts_d = nullptr;
     m.tris = nullptr;
     m.tri_n = nullptr;
     m.cdf = nullptr;
@@ -234,6 +245,7 @@ int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t 
     m.V = V;
     m.T = T;
     WOB_CUDA_TRY(cudaMalloc((void**)&m.verts, V * 3 * sizeof(float)));
+    WOB_CUDA_TRY(cudaMalloc((void**)&m.verts_d, V * 3 * sizeof(double)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.tris, T * 3 * sizeof(int32_t)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.tri_n, T * sizeof(NormalArea)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.cdf, T * sizeof(double)));
@@ -262,6 +274,9 @@ int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t 
     init.volume = 0.0;
     WOB_CUDA_TRY(cudaMemcpyAsync(sc, &init, sizeof(Scratch), cudaMemcpyHostToDevice, s));
     const int threads = 256;
+    k_to_f64<<<grid_for((const void*)k_to_f64, threads, 0, 3 * V), threads, 0, s>>>(m.verts, 3 * V,
+                                                                                  m.verts_d);
+    WOB_CUDA_TRY(cudaGetLastError());
     k_vertex_bounds<<<grid_for((const void*)k_vertex_bounds, threads, 0, V), threads, 0, s>>>(
         m.verts, V, sc->bounds, &sc->err);
     WOB_CUDA_TRY(cudaGetLastError());

@@ -152,9 +152,9 @@ __device__ __forceinline__ AreaPoint area_point(const WalkParams& p, StreamKey k
     a.b1 = su * (1.0 - u2);
     a.b2 = su * u2;
     const int32_t* t = p.tris + 3 * lo;
-    const float* v0 = p.verts + 3 * (int64_t)__ldg(t);
-    const float* v1 = p.verts + 3 * (int64_t)__ldg(t + 1);
-    const float* v2 = p.verts + 3 * (int64_t)__ldg(t + 2);
+    const double* v0 = p.verts_d + 3 * (int64_t)__ldg(t);
+    const double* v1 = p.verts_d + 3 * (int64_t)__ldg(t + 1);
+    const double* v2 = p.verts_d + 3 * (int64_t)__ldg(t + 2);
     a.y = make_double3(a.b0 * __ldg(v0) + a.b1 * __ldg(v1) + a.b2 * __ldg(v2),
                        a.b0 * __ldg(v0 + 1) + a.b1 * __ldg(v1 + 1) + a.b2 * __ldg(v2 + 1),
                        a.b0 * __ldg(v0 + 2) + a.b1 * __ldg(v1 + 2) + a.b2 * __ldg(v2 + 2));

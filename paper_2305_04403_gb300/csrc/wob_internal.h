@@ -33,6 +33,7 @@ struct alignas(32) NormalArea {
 
 struct MeshDev {
     float* verts = nullptr;   // V x 3
+    double* verts_d = nullptr;  // V x 3, the same positions in FP64 (area sampling)
     int32_t* tris = nullptr;  // T x 3
     NormalArea* tri_n = nullptr;  // unit normal (FP64), area
     double* cdf = nullptr;    // inclusive prefix sums of areas
@@ -75,6 +76,7 @@ struct WalkParams {
     const int32_t* inv_order;
     int iter_limit;  // traversal loop bound (4 x wide nodes + 64)
     const float* verts;
+    const double* verts_d;  // FP64 copy of verts
     const int32_t* tris;
     const NormalArea* tri_n;
     const double* cdf;
