@@ -339,6 +339,13 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
     const int64_t total = p.Q * (int64_t)p.N;
     const double phi = (double)p.phi;
     const double rmin = 1e-12 * p.L;
+    // FP64 walk state parked in shared memory during the traversal (as in
+    // k_dl_walks), which leaves the postponed-leaf traversal its registers
+    __shared__ double slots[8 * 128];
+    __shared__ int leafq[kLeafQ * 128];
+    const WalkSlot ws{slots + threadIdx.x, 128};
+    const LeafQueue lq{leafq + threadIdx.x, 128};
+    enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP };
     int err = 0;
     int stack[kStackSize];
     int hits[kMaxHits];
@@ -347,7 +354,11 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
         const int64_t qi = idx / p.N;
         const uint32_t q = p.q_base + (uint32_t)qi;
         const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
-        double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+        ws.set(X0, p.queries[3 * qi]);
+        ws.set(X1, p.queries[3 * qi + 1]);
+        ws.set(X2, p.queries[3 * qi + 2]);
+        ws.set(SS, 0.0);
+        ws.set(PP, 1.0);
         int32_t* lm = DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr;
         if (DEBUG && lm)
             for (int k = 0; k < p.M; ++k) lm[k] = -1;
@@ -359,43 +370,55 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
                 k0 = 1;
             }
         }
-        double S = 0.0, P = 1.0;
         for (int k = k0; k <= p.M; ++k) {
             // source at vertex k
-            const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
-            const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
-            const double r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 >= rmin * rmin) {
-                const double f =
-                    sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
-                double c = (k == 0) ? phi : 2.0 * phi;
-                if (k == p.M) c *= 0.5;
-                const double G = (double)(0.0795774715459476678f * rsqrtf((float)r2));
-                S = fma(P * c * p.area * G, f, S);
+            {
+                const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
+                const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
+                const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
+                const double r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 >= rmin * rmin) {
+                    const double f =
+                        sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
+                    double c = (k == 0) ? phi : 2.0 * phi;
+                    if (k == p.M) c *= 0.5;
+                    const double G = (double)(0.0795774715459476678f * rsqrtf((float)r2));
+                    ws.set(SS, fma(ws.get(PP) * c * p.area * G, f, ws.get(SS)));
+                }
             }
             if (k == p.M) break;
             // line from vertex k to vertex k + 1
-            const double3 d = line_axis(key, q, w, (uint32_t)k);
-            const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
-                                       make_float3((float)d.x, (float)d.y, (float)d.z));
+            LinePre L;
+            {
+                const double3 d = line_axis(key, q, w, (uint32_t)k);
+                ws.set(D0, d.x);
+                ws.set(D1, d.y);
+                ws.set(D2, d.z);
+                L = line_pre(make_float3((float)ws.get(X0), (float)ws.get(X1), (float)ws.get(X2)),
+                             make_float3((float)d.x, (float)d.y, (float)d.z));
+            }
             const float Tthr = p.edge_thr_L * fabsf(L.Sz);
             Trav t;
             trav_init(t);
             uint32_t nn = 0, nt = 0;
-            trace_wide_now<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr,
-                                         p.tauL, p.graze, self, t, hits, stack, key, q, w,
-                                         (uint32_t)k, nn, nt, err, p.iter_limit);
+            trace_wide_q<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+                                       p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn,
+                                       nt, err, p.iter_limit, lq);
             wflag |= t.flag;
             if (DEBUG && lm) lm[k] = t.m;
             if (t.m == 0) break;
             const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
+            const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
+            const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
             const Refined r = refine_hit(p.tv, pos, x, d);
             const double ms = (double)t.m * (double)r.s;
-            P *= (k == 0) ? 0.5 * phi * ms : phi * ms;
-            x = r.y;
+            ws.set(PP, ws.get(PP) * ((k == 0) ? 0.5 * phi * ms : phi * ms));
+            ws.set(X0, r.y.x);
+            ws.set(X1, r.y.y);
+            ws.set(X2, r.y.z);
             self = pos;
         }
-        p.per_walk[idx] = S;
+        p.per_walk[idx] = ws.get(SS);
         if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
     }
     if (err) atomicOr(p.error_word, err);

@@ -305,7 +305,7 @@ __device__ __forceinline__ int pick4(int4 v, int j)
 // "Understanding the efficiency of ray traversal on GPUs", HPG 2009:
 // postponed leaves, speculative traversal).  A leaf that does not fit in
 // the queue is tested on the spot.  The set of triangles tested is the
-// same as with immediate tests (trace_wide_now below).
+// same as with immediate tests.
 constexpr int kLeafQ = 16;
 
 // Where a lane keeps its queued leaf triangles: entry i at base[i * stride]
@@ -444,105 +444,6 @@ __device__ __forceinline__ void trace_wide(const float4* __restrict__ wn,
     int lq[kLeafQ];
     trace_wide_q<COUNT, SUM_S>(wn, tv, L, d, Tthr, tauL, graze, exclude_pos, t, hits, stack, key,
                                q, walk, step, n_nodes, n_tris, err, iter_limit, LeafQueue{lq, 1});
-}
-
-// The same traversal with every leaf tested during the node visit that
-// finds it (no queue, fewer live values): for kernels that hold their walk
-// state in registers across the traversal, where the queued loop spills
-// (k_nd_walks: 5.5x slower with it).
-template <bool COUNT, bool SUM_S>
-__device__ __forceinline__ void trace_wide_now(const float4* __restrict__ wn,
-                                           const float4* __restrict__ tv, const LinePre& L,
-                                           float3 d, float Tthr, float tauL, float graze,
-                                           int exclude_pos, Trav& t, int* hits, int* stack,
-                                           StreamKey key, uint32_t q, uint32_t walk,
-                                           uint32_t step, uint32_t& n_nodes, uint32_t& n_tris,
-                                           int& err, int iter_limit)
-{
-    int node = 0, sp = 0, iters = 0;
-    while (true) {
-        if (node >= 0) {
-            if (++iters > iter_limit) {  // each node is visited at most once per line
-                err |= 2;
-                break;
-            }
-            if (COUNT) n_nodes++;
-            const float4* nd = wn + 6 * node;
-            const float4 h = __ldg(nd);
-            const uint32_t hdr = __float_as_uint(h.w);
-            const int nint = (hdr >> 24) & 15, nch = hdr >> 28;
-            // slab parameter of a quantised plane: (origin + q s - o) / d
-            // = (1 + q 2^-15) a + b with a = 2^15 s / d (see dequant)
-            const float ax = __uint_as_float(((hdr & 255u) + 15u) << 23) * L.ix;
-            const float ay = __uint_as_float((((hdr >> 8) & 255u) + 15u) << 23) * L.iy;
-            const float az = __uint_as_float((((hdr >> 16) & 255u) + 15u) << 23) * L.iz;
-            const float bx = fmaf(h.x, L.ix, -L.oix) - ax, by = fmaf(h.y, L.iy, -L.oiy) - ay,
-                        bz = fmaf(h.z, L.iz, -L.oiz) - az;
-            const uint4 qx = __ldg(reinterpret_cast<const uint4*>(nd + 1));
-            const uint4 qy = __ldg(reinterpret_cast<const uint4*>(nd + 2));
-            const uint4 qz = __ldg(reinterpret_cast<const uint4*>(nd + 3));
-            // per axis the near plane is the low one when the axis component
-            // is positive (t = q a + b is monotone in q): pick near / far
-            // byte words once, so a slab test is max of 3 nears <= min of 3 fars
-            const bool px_ = L.ix >= 0.f, py_ = L.iy >= 0.f, pz_ = L.iz >= 0.f;
-            const uint32_t nx0 = px_ ? qx.x : qx.z, nx1 = px_ ? qx.y : qx.w;
-            const uint32_t fx0 = px_ ? qx.z : qx.x, fx1 = px_ ? qx.w : qx.y;
-            const uint32_t ny0 = py_ ? qy.x : qy.z, ny1 = py_ ? qy.y : qy.w;
-            const uint32_t fy0 = py_ ? qy.z : qy.x, fy1 = py_ ? qy.w : qy.y;
-            const uint32_t nz0 = pz_ ? qz.x : qz.z, nz1 = pz_ ? qz.y : qz.w;
-            const uint32_t fz0 = pz_ ? qz.z : qz.x, fz1 = pz_ ? qz.w : qz.y;
-            uint32_t hit = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float tnx = fmaf(dequant(j < 4 ? nx0 : nx1, j & 3), ax, bx);
-                const float tfx = fmaf(dequant(j < 4 ? fx0 : fx1, j & 3), ax, bx);
-                const float tny = fmaf(dequant(j < 4 ? ny0 : ny1, j & 3), ay, by);
-                const float tfy = fmaf(dequant(j < 4 ? fy0 : fy1, j & 3), ay, by);
-                const float tnz = fmaf(dequant(j < 4 ? nz0 : nz1, j & 3), az, bz);
-                const float tfz = fmaf(dequant(j < 4 ? fz0 : fz1, j & 3), az, bz);
-                const float tn = fmaxf(fmaxf(tnx, tny), tnz);
-                const float tf = fminf(fminf(tfx, tfy), tfz);
-                if (j < nch && tn <= tf) hit |= 1u << j;
-            }
-            const int4 r0 = __ldg(reinterpret_cast<const int4*>(nd + 4));
-            uint32_t lm = hit >> nint;  // leaf children
-            if (lm) {
-                const int4 r1 = __ldg(reinterpret_cast<const int4*>(nd + 5));
-                while (lm) {
-                    const int j = nint + __ffs(lm) - 1;
-                    lm &= lm - 1;
-                    const int ref = j < 4 ? pick4(r0, j) : pick4(r1, j - 4);
-                    const int first = leaf_first(ref), count = leaf_count(ref);
-                    for (int p = first; p < first + count; ++p) {
-                        if (p == exclude_pos) continue;
-                        if (COUNT) n_tris++;
-                        test_tri<SUM_S>(tv, L, d, Tthr, tauL, graze, p, t, hits, key, q, walk,
-                                        step);
-                    }
-                }
-            }
-            uint32_t im = hit & ((1u << nint) - 1u);  // interior children
-            if (im) {
-                const int c = __ffs(im) - 1;
-                im &= im - 1;
-                if (im) {
-                    if (sp < kStackSize) stack[sp++] = r0.x | (int)(im << 24);
-                    else err |= 1;
-                }
-                node = r0.x + c;
-                continue;
-            }
-            node = -1;
-        }
-        if (sp == 0) break;
-        const uint32_t e = (uint32_t)stack[--sp];
-        const int base = (int)(e & 0xFFFFFFu);
-        uint32_t m = e >> 24;
-        const int c = __ffs(m) - 1;
-        m &= m - 1;
-        if (m) stack[sp++] = base | (int)(m << 24);
-        node = base + c;
-    }
 }
 
 // The picked hit (leaf position) after the traversal; -1 if m == 0.
