@@ -46,7 +46,11 @@ extern "C" {
                                         triangle or inward orientation */
 #define WOB_ERR_UNSUPPORTED (-6)     /* combination not implemented */
 #define WOB_ERR_DEVICE_CHECK (-7)    /* a device-side check fired (traversal
-                                        stack overflow) */
+                                        stack overflow or iteration bound);
+                                        returned by calls that read the check
+                                        back (wob_solve_counted); in every
+                                        solve the estimates of a call in
+                                        which a check fired are NaN */
 
 /* Boundary-integral formulation (Table 1 of the paper). */
 typedef enum {
@@ -119,6 +123,14 @@ typedef struct {
  *   ris:       single-layer kinds: 0 or 1 = area-uniform next points; 2..64 =
  *              resampled importance sampling from `ris` uniform candidates
  *              with target |kernel| (the paper uses 16).
+ *   iter_limit: 0 = automatic (4 x wide BVH nodes + 64 node visits per
+ *              line, which a line never needs: each node is visited at most
+ *              once); a positive value bounds the visits per line lower.  A
+ *              line that reaches the bound (or overflows the traversal stack)
+ *              stops and sets the solve's check word: every estimate of that
+ *              call is NaN and wob_solve_counted returns
+ *              WOB_ERR_DEVICE_CHECK.  Small values exercise that path without
+ *              any fault.
  */
 typedef struct {
     wob_bvh bvh;
@@ -136,6 +148,7 @@ typedef struct {
     float k_mix;
     float p_k;
     int32_t ris;
+    int32_t iter_limit;
 } wob_problem;
 
 /* Per-walk outputs for parity checks (each pointer device, may be NULL). */

@@ -64,7 +64,7 @@ class _Problem(ctypes.Structure):
                 ("x0", ctypes.c_float * 3), ("scale", ctypes.c_float),
                 ("problem", ctypes.c_uint32), ("tau", ctypes.c_float),
                 ("bc_type", ctypes.c_void_p), ("k_mix", ctypes.c_float), ("p_k", ctypes.c_float),
-                ("ris", ctypes.c_int32)]
+                ("ris", ctypes.c_int32), ("iter_limit", ctypes.c_int32)]
 
 
 class _BatchParams(ctypes.Structure):
@@ -296,6 +296,7 @@ class Problem:
     k_mix: float = 0.0
     p_k: float = 0.0
     ris: int = 0
+    iter_limit: int = 0                 # 0: automatic traversal bound
     _keep: list = field(default_factory=list, repr=False)
 
     def _c(self) -> _Problem:
@@ -318,6 +319,7 @@ class Problem:
             self._keep.append(bc)
             p.bc_type = bc.data_ptr()
         p.k_mix, p.p_k, p.ris = self.k_mix, self.p_k, self.ris
+        p.iter_limit = self.iter_limit
         return p
 
 

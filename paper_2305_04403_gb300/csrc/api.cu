@@ -55,6 +55,10 @@ int check_problem(const wob_problem* prob)
         set_error("unknown kind %d", prob->kind);
         return WOB_ERR_INVALID_ARG;
     }
+    if (prob->iter_limit < 0) {
+        set_error("iter_limit = %d is negative", prob->iter_limit);
+        return WOB_ERR_INVALID_ARG;
+    }
     if (prob->kind == WOB_MIXED_SL &&
         (!prob->bc_type || !(prob->k_mix > 0.0f) || !(prob->p_k > 0.0f && prob->p_k < 1.0f) ||
          prob->data_mode == WOB_DATA_VERTEX_P1)) {
@@ -112,7 +116,7 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     p.nodes = b.wnodes;
     p.tv = b.tv;
     p.inv_order = b.inv_order;
-    p.iter_limit = (int)(4 * b.n_wide + 64);
+    p.iter_limit = prob->iter_limit > 0 ? prob->iter_limit : (int)(4 * b.n_wide + 64);
     p.verts = m.verts;
     p.verts_d = m.verts_d;
     p.tris = m.tris;
@@ -226,8 +230,8 @@ int solve_common(const wob_problem* prob, const float* queries, const int32_t* q
     }
     p.per_walk = per_walk;
     WOB_TRY(run_walks(p, dbg, stats != nullptr, s, &sc.err->err));
-    if (est) WOB_TRY(launch_reduce(per_walk, Q, walks, est, var, s));
-    if (sum) WOB_TRY(launch_reduce_accum(per_walk, Q, walks, sum, sumsq, s));
+    if (est) WOB_TRY(launch_reduce(per_walk, Q, walks, est, var, s, &sc.err->err));
+    if (sum) WOB_TRY(launch_reduce_accum(per_walk, Q, walks, sum, sumsq, s, &sc.err->err));
     if (stats) {
         unsigned long long h[5];
         int herr = 0;
@@ -459,9 +463,10 @@ int wob_solve_grad(const wob_problem* prob, const float* queries, int64_t Q, int
     p.per_walk = sc.per_walk;
     p.per_walk_grad = g;
     int rc = run_walks(p, nullptr, false, s, &sc.err->err);
-    if (rc == WOB_OK) rc = launch_reduce(sc.per_walk, Q, walks, est, var, s);
+    if (rc == WOB_OK) rc = launch_reduce(sc.per_walk, Q, walks, est, var, s, &sc.err->err);
     for (int c = 0; c < 3 && rc == WOB_OK; ++c)
-        rc = launch_reduce(g + c * W, Q, walks, grad_est + c * Q, grad_var + c * Q, s);
+        rc = launch_reduce(g + c * W, Q, walks, grad_est + c * Q, grad_var + c * Q, s,
+                           &sc.err->err);
     if (g_owned) cudaFreeAsync(g_owned, s);
     return rc;
 }

@@ -106,8 +106,10 @@ __global__ void k_reduce_batched(const double* __restrict__ per_walk,
                                  const int64_t* __restrict__ qoff,
                                  const int64_t* __restrict__ walk_base,
                                  const int32_t* __restrict__ walks, int32_t P, int64_t Qt,
-                                 double* __restrict__ est, double* __restrict__ var)
+                                 double* __restrict__ est, double* __restrict__ var,
+                                 const int* __restrict__ err)
 {
+    const bool bad = *err != 0;  // a traversal check fired in this replay
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t gq = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); gq < Qt;
@@ -130,8 +132,9 @@ __global__ void k_reduce_batched(const double* __restrict__ per_walk,
         }
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
         if (lane == 0) {
-            est[gq] = mean;
-            var[gq] = N > 1 ? ss / (N - 1) : 0.0;
+            est[gq] = bad ? __longlong_as_double(0x7FF8000000000000ll) : mean;
+            var[gq] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                          : (N > 1 ? ss / (N - 1) : 0.0);
         }
     }
 }
@@ -255,6 +258,7 @@ int launch_batch_kernels(wob_batch_s& b, const BatchProblem* probs, const Tile* 
                          int64_t n_tiles, int rounds, int grid, double* per_walk, cudaStream_t s)
 {
     WOB_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(unsigned long long), s));
+    WOB_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int), s));  // this run's checks
     const int threads = 128;
     if (rounds == 4)
         k_dl_batched<4><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, per_walk, b.err);
@@ -492,7 +496,7 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
     if (rc == WOB_OK && b->Qt > 0)
         k_reduce_batched<<<g_red, 256, 0, b->cap_stream>>>(b->per_walk, b->qoff_dev,
                                                            b->walk_base_dev, b->walks_dev, P,
-                                                           b->Qt, est, var);
+                                                           b->Qt, est, var, b->err);
     const cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &b->graph);
     if (rc != WOB_OK || ce != cudaSuccess ||
         cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {

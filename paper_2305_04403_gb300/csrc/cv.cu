@@ -857,7 +857,7 @@ int wob_cv_solve(const wob_problem* prob, wob_cv c, const float* params, const f
         k_cvw_accum<<<g_acc, kQuadThreads, 0, s>>>(p, st, g, k);
     }
     if (rc == WOB_OK && cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
-    if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s);
+    if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s, err);
     if (rc == WOB_OK && per_walk)
         if (cudaMemcpyAsync(per_walk, st.S, W * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             rc = WOB_ERR_CUDA;
@@ -941,7 +941,7 @@ int wob_cv_solve_mc(const wob_problem* prob, const float* params, const float* q
         k_cvmc_accum<<<g_acc, threads, 0, s>>>(p, st, mc, k);
     }
     if (rc == WOB_OK && cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
-    if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s);
+    if (rc == WOB_OK) rc = launch_reduce_accum(st.S, Q, walks, sum, sumsq, s, err);
     if (rc == WOB_OK && per_walk)
         if (cudaMemcpyAsync(per_walk, st.S, W * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             rc = WOB_ERR_CUDA;

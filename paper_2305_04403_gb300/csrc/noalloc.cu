@@ -112,5 +112,5 @@ extern "C" int wob_solve_noalloc(const wob_problem* prob, const float* queries,
         WOB_TRY(launch_nd_walks(p, false, s));
     else
         WOB_TRY(launch_sl_walks(p, false, s));
-    return launch_reduce(values, Q, walks, est, var, s);
+    return launch_reduce(values, Q, walks, est, var, s, check);
 }

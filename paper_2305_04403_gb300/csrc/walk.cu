@@ -671,8 +671,10 @@ __global__ void __launch_bounds__(kFwdThreads)
 }
 
 __global__ void k_fwd_finish(const double* __restrict__ part, int splits, int64_t Q,
-                             int64_t n_paths, double* __restrict__ est, double* __restrict__ var)
+                             int64_t n_paths, double* __restrict__ est, double* __restrict__ var,
+                             const int* __restrict__ err)
 {
+    const bool bad = err && *err != 0;  // a path's line gave up
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
          q += (int64_t)gridDim.x * blockDim.x) {
         double sum = 0.0, sumsq = 0.0;
@@ -681,8 +683,10 @@ __global__ void k_fwd_finish(const double* __restrict__ part, int splits, int64_
             sumsq += part[(2 * (int64_t)sp + 1) * Q + q];
         }
         const double mean = sum / (double)n_paths;
-        est[q] = mean;
-        var[q] = n_paths > 1 ? fmax(sumsq - sum * mean, 0.0) / (double)(n_paths - 1) : 0.0;
+        est[q] = bad ? __longlong_as_double(0x7FF8000000000000ll) : mean;
+        var[q] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                     : (n_paths > 1 ? fmax(sumsq - sum * mean, 0.0) / (double)(n_paths - 1)
+                                    : 0.0);
     }
 }
 
@@ -707,9 +711,17 @@ static int fwd_splits(int64_t q_blocks, int64_t max_splits, int64_t slots)
 }
 
 // One warp per query: mean and unbiased variance in a fixed order.
+// err (may be NULL): the solve's device check word; when a traversal check
+// fired during the solve, every estimate of the call is NaN (the walk
+// kernels themselves carry no per-walk check: it would cost registers in
+// the traversal loop).
+__device__ __forceinline__ bool solve_failed(const int* err) { return err && *err != 0; }
+
 __global__ void k_reduce(const double* __restrict__ per_walk, int64_t Q, int32_t N,
-                         double* __restrict__ est, double* __restrict__ var)
+                         double* __restrict__ est, double* __restrict__ var,
+                         const int* __restrict__ err)
 {
+    const bool bad = solve_failed(err);
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < Q;
@@ -726,15 +738,18 @@ __global__ void k_reduce(const double* __restrict__ per_walk, int64_t Q, int32_t
         }
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
         if (lane == 0) {
-            est[q] = mean;
-            var[q] = N > 1 ? ss / (N - 1) : 0.0;
+            est[q] = bad ? __longlong_as_double(0x7FF8000000000000ll) : mean;
+            var[q] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                         : (N > 1 ? ss / (N - 1) : 0.0);
         }
     }
 }
 
 __global__ void k_reduce_accum(const double* __restrict__ per_walk, int64_t Q, int32_t N,
-                               double* __restrict__ sum, double* __restrict__ sumsq)
+                               double* __restrict__ sum, double* __restrict__ sumsq,
+                               const int* __restrict__ err)
 {
+    const double bad = solve_failed(err) ? __longlong_as_double(0x7FF8000000000000ll) : 0.0;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < Q;
@@ -750,8 +765,8 @@ __global__ void k_reduce_accum(const double* __restrict__ per_walk, int64_t Q, i
             ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
         }
         if (lane == 0) {
-            sum[q] += s;
-            sumsq[q] += ss;
+            sum[q] += s + bad;
+            sumsq[q] += ss + bad;
         }
     }
 }
@@ -929,7 +944,7 @@ int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double 
         k_fwd_connect<<<(int)(items < slots ? items : slots), kFwdThreads, 0, s>>>(
             queries, Q, rec, live, n_paths, p.M, q_blocks, splits, per_split, part);
         k_fwd_finish<<<grid_for((const void*)k_fwd_finish, 256, 0, Q), 256, 0, s>>>(
-            part, splits, Q, n_paths, est, var);
+            part, splits, Q, n_paths, est, var, p.error_word);
         if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
         cudaFreeAsync(cb, s);
     }
@@ -938,20 +953,21 @@ int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double 
 }
 
 int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
-                  cudaStream_t s)
+                  cudaStream_t s, const int* err)
 {
     const int threads = 256;
-    k_reduce<<<grid_for((const void*)k_reduce, threads, 0, Q * 32), threads, 0, s>>>(per_walk, Q, N, est, var);
+    k_reduce<<<grid_for((const void*)k_reduce, threads, 0, Q * 32), threads, 0, s>>>(
+        per_walk, Q, N, est, var, err);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
 
 int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum, double* sumsq,
-                        cudaStream_t s)
+                        cudaStream_t s, const int* err)
 {
     const int threads = 256;
     k_reduce_accum<<<grid_for((const void*)k_reduce_accum, threads, 0, Q * 32), threads, 0, s>>>(
-        per_walk, Q, N, sum, sumsq);
+        per_walk, Q, N, sum, sumsq, err);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }

@@ -60,10 +60,11 @@ int launch_probe_read(const float4* buf, int64_t n, int passes, float* out, cuda
 int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double beta,
                    const float* queries, int64_t Q, double* zpos, double* zw, uint8_t* flags,
                    double* est, double* var, cudaStream_t s);
+// err: the solve's device check word (NULL: none); when set, the outputs are NaN
 int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
-                  cudaStream_t s);
+                  cudaStream_t s, const int* err);
 int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum,
-                        double* sumsq, cudaStream_t s);
+                        double* sumsq, cudaStream_t s, const int* err);
 int launch_trace_lines(const BvhDev& b, const double* o, const double* d, const int32_t* exclude,
                        const uint32_t* keys, int64_t n, uint32_t key0, uint32_t key1,
                        float tauL, float edge_thr_L, int32_t* m, int32_t* sum_s, int32_t* prim,
