@@ -495,6 +495,9 @@ int wob_solve_forward(const wob_problem* prob, const float* queries, int64_t Q, 
     Scratch sc;
     sc.s = s;
     const int64_t R = (int64_t)paths * max_len;
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(Control), s));  // freed by sc
+    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(Control), s));
+    p.error_word = &sc.err->err;
     double* zp = zpos;
     double* w = zw;
     double* own = nullptr;
@@ -503,9 +506,6 @@ int wob_solve_forward(const wob_problem* prob, const float* queries, int64_t Q, 
         if (!zp) zp = own;
         if (!w) w = own + 3 * R;
     }
-    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(Control), s));
-    WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(Control), s));
-    p.error_word = &sc.err->err;
     int rc = launch_forward(p, paths, start_mode, (double)beta, queries, Q, zp, w, path_flag, est,
                             var, s);
     if (own) cudaFreeAsync(own, s);
