@@ -66,6 +66,18 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib_path):
     lib.wob_solve.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_int32,
                                                       ctypes.c_int32, ctypes.c_uint64] + [ctypes.c_void_p] * 3
     assert lib.wob_solve(None, None, None, 4, 1, 4, 0, None, None, None) == -1
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    # forward paths, Monte Carlo control variate, L2 probe: NULL problem,
+    # parameters or buffers are refused before anything reaches the GPU
+    lib.wob_solve_forward.argtypes = [P, P, I64, I32, I32, ctypes.c_uint64, I32, ctypes.c_float,
+                                      P, P, P, P, P, P]
+    assert lib.wob_solve_forward(None, None, 4, 64, 3, 0, 1, 0.1, None, None, None, None, None,
+                                 None) == -1
+    lib.wob_cv_solve_mc.argtypes = [P, P, P, I64, I64, I32, I32, I32, ctypes.c_uint64, P, P, P, P]
+    assert lib.wob_cv_solve_mc(None, None, None, 4, 0, 8, 2, 4, 0, None, None, None, None) == -1
+    lib.wob_probe_l2_read.argtypes = [P, I64, I32, P, P]
+    assert lib.wob_probe_l2_read(None, 1 << 20, 1, None, None) == -1
+    assert b"wob_probe_l2_read" in lib.wob_last_error()
 
 
 def _ptxas_functions(log):
