@@ -52,8 +52,10 @@
  * the last double-layer term; 2: first double-layer weight negated; 3:
  * double-layer recursion sign flipped; 4: hit sign s negated; 5: Robin term
  * of the single layer with the wrong sign; 6: direct-Neumann first line
- * without the 1/2; 7: direct-Neumann last source not halved).  0 (the
- * default) is the oracle. */
+ * without the 1/2; 7: direct-Neumann last source not halved; 8: forward
+ * start weight without the 2 of f = 2 phi q; 9: forward step weight with the
+ * wrong sign; 10: forward last vertex not halved; 11: weighted start density
+ * not divided by the triangle's area).  0 (the default) is the oracle. */
 #ifndef ORACLE_PLANT
 #define ORACLE_PLANT 0
 #endif
@@ -977,14 +979,26 @@ static void fwd_path(const mesh_t *M, const oracle_data *D, int32_t phi, const d
         tri_normal(M, lo, N);
         double A = 0.5 * norm3(N);
         double w = cdf[lo] - (lo > 0 ? cdf[lo - 1] : 0.0);
+#if ORACLE_PLANT == 11
+        pdf = w / tot;
+#else
         pdf = (w / A) / tot;
+#endif
     } else {
         pdf = 1.0 / M->area;
     }
+#if ORACLE_PLANT == 8
+    double a = (double)phi * boundary_data(D, M, lo, z, b, n, KIND_NEUMANN_SL, 0.0) / pdf;
+#else
     double a = 2.0 * (double)phi * boundary_data(D, M, lo, z, b, n, KIND_NEUMANN_SL, 0.0) / pdf;
+#endif
     int64_t prim = lo;
     for (int32_t j = 0; j < Mlen; ++j) {
+#if ORACLE_PLANT == 10
+        double c = 1.0;
+#else
         double c = (j == Mlen - 1) ? 0.5 : 1.0;
+#endif
         zpos[3 * j] = z[0]; zpos[3 * j + 1] = z[1]; zpos[3 * j + 2] = z[2];
         zw[j] = c * a;
         if (j == Mlen - 1) break;
@@ -994,7 +1008,11 @@ static void fwd_path(const mesh_t *M, const oracle_data *D, int32_t phi, const d
         trace_line(M, z, d, prim, seed, problem, path, FORWARD_WALK, (uint32_t)j, tauL, graze, &r);
         if (r.flag) *flag = 1;
         if (r.m == 0) break;
+#if ORACLE_PLANT == 9
+        a *= -(double)phi * (double)r.m * (double)r.s;
+#else
         a *= (double)phi * (double)r.m * (double)r.s;
+#endif
         z[0] = r.y[0]; z[1] = r.y[1]; z[2] = r.y[2];
         prim = r.prim;
     }

@@ -21,12 +21,17 @@ CHECKS = {
     5: "W.test_sl_exterior_neumann_and_robin_closed_form(S3, 2)",        # Robin term sign
     6: "N.test_nd_interior_closed_form(S3, 1, N.Z, 1)",                  # no 1/2 on the first line
     7: "N.test_nd_boundary_start_closed_form(S3, 1)",                    # last source not halved
+    8: "F.test_forward_interior_closed_form(S3, 0, 1, F.Z, 1)",          # forward start without 2
+    9: "F.test_forward_interior_closed_form(S3, 0, 2, F.Z, 1)",          # forward step sign
+    10: "F.test_forward_interior_closed_form(S3, 0, 1, F.Z, 1)",         # forward last not halved
+    11: "F.test_forward_interior_closed_form(S3, 1, 1, F.Z, 1)",         # weighted start density
 }
 
 SCRIPT = """
 import sys
 sys.path.insert(0, {root!r}); sys.path.insert(0, {here!r})
 import test_oracle_walks as W, test_oracle_nd as N, test_oracle_geometry as G
+import test_oracle_fwd as F
 from paper_2305_04403_gb300 import inputs as I
 S3 = I.icosphere(3)
 CASE = G._meshes_with_points()[0]
