@@ -90,3 +90,26 @@ def test_exact_density_removes_truncation_bias_and_variance(sphere3):
     assert np.all(np.abs(S.mean(1) - QIN[:, 2]) <= 5 * se + 3e-3)
     assert np.all(np.abs(P.mean(1) - QIN[:, 2]) > 0.05)
     assert S.var(1).mean() < P.var(1).mean()
+
+
+@pytest.mark.parametrize("mistake", ["H sign", "D without 1/2"])
+def test_closed_form_catches_planted_mistakes(sphere3, monkeypatch, mistake):
+    """The closed-form pin has the power to see a wrong weight: with the
+    sign of H^ flipped, or the 1/2 dropped from D^'s first-step weight, the
+    estimate leaves the closed form by far more than 5 standard errors."""
+    v, f = sphere3
+    orig = C._mc_lines
+
+    def planted(verts, tris, x, excl, qi, wi, vtx, K, nu_t, first, phi, seed, problem, tau):
+        acc, flag = orig(verts, tris, x, excl, qi, wi, vtx, K, nu_t, first, phi, seed, problem, tau)
+        if mistake == "H sign" and not first:
+            acc = -acc
+        if mistake == "D without 1/2" and first:
+            acc = 2.0 * acc
+        return acc, flag
+
+    monkeypatch.setattr(C, "_mc_lines", planted)
+    S, _ = C.cv_walks_mc(v, f, QIN, 3000, 2, lambda y: 1.0 * y[:, 2], 2, Z, seed=4)
+    est, se = S.mean(1), S.std(1, ddof=1) / np.sqrt(S.shape[1])
+    pred = _closed(1.0, 1, 2, QIN[:, 2].astype(float))
+    assert np.any(np.abs(est - pred) > 5 * se + 3e-3), (est, pred, se)
