@@ -230,6 +230,34 @@ def test_sl_boundary_queries_torus(wob):
     assert np.all(err <= 1e-5 * at + 1e-12)
 
 
+@pytest.mark.parametrize("kind,phi,alpha,x0,inside", [
+    (1, 1, 0.0, (0.0, 0.0, 5.0), True),      # interior Neumann
+    (2, -1, 2.0, (1.0, 0.0, 0.05), False),   # exterior Robin, alpha 2
+])
+def test_sl_full_size_torus_sampled(wob, kind, phi, alpha, x0, inside):
+    """The single-layer benchmark's mesh and settings, sampled: the
+    200,000-triangle displaced torus, M = 24, 8 boundary + 8 off-boundary
+    queries x 32 walks (area sampling costs the oracle O(log T) per vertex).
+    Per walk |gpu - oracle| <= tol * sum|terms|, tol = max(1e-5, 5e-7 M): the
+    GPU forms 1/r, G and dG/dn in FP32 (relative error below 5e-7 per
+    weight), so a term after k steps carries up to k such errors."""
+    v, f, sh = I.displaced_torus()
+    bp, prim = I.boundary_points(v, f, 8, seed=10)
+    off = I.torus_queries(sh, 8, inside, seed=20)
+    q = np.concatenate([bp, off]).astype(np.float32)
+    pr = np.concatenate([prim, np.full(8, -1, np.int32)])
+    bvh = wob.build_bvh(wob.build_mesh(v, f))
+    prob = wob.Problem(bvh, kind=kind, side=phi, alpha=alpha, data_mode=wob.DATA_POINT, x0=x0,
+                       problem=kind - 1)
+    M, N = 24, 32
+    g = wob.solve_debug(prob, q, N, M, seed=0, query_prim=pr, want_lines=False)
+    pw, at = O.sl_walks(v, f, q, N, M, kind=kind, alpha=alpha, phi=phi, mode=O.DATA_POINT,
+                        x0=x0, seed=0, problem=kind - 1, want_abs=True)
+    err = np.abs(g["per_walk"].cpu().numpy() - pw)
+    tol = max(1e-5, 5e-7 * M)
+    assert np.all(err <= tol * at + 1e-12), (err / np.maximum(tol * at, 1e-300)).max()
+
+
 def test_gauss_invariant_on_gpu(wob):
     v, f, sh = I.star_mesh(5, 0.3, 6, 3, 0.5)
     mesh = wob.build_mesh(v, f)
