@@ -23,6 +23,7 @@
 #include <vector>
 
 #include <sys/stat.h>
+#include <unistd.h>
 
 #include "wob_device.cuh"
 #include "wob_host.h"
@@ -184,7 +185,10 @@ void write_cache(const std::map<std::string, std::string>& m)
 {
     const std::string path = cache_path();
     make_parent_dirs(path);
-    std::ofstream f(path + ".tmp");
+    // a temporary file of this process, renamed over the cache: concurrent
+    // writers never interleave, the last rename wins
+    const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    std::ofstream f(tmp);
     if (!f) return;
     f << "{\n";
     size_t n = 0;
@@ -192,7 +196,7 @@ void write_cache(const std::map<std::string, std::string>& m)
         f << "  \"" << kv.first << "\": \"" << kv.second << "\"" << (++n < m.size() ? "," : "") << "\n";
     f << "}\n";
     f.close();
-    rename((path + ".tmp").c_str(), path.c_str());
+    rename(tmp.c_str(), path.c_str());
 }
 
 int log2_bucket(double x) { return x <= 1 ? 0 : (int)std::floor(std::log2(x)); }

@@ -11,6 +11,7 @@
 //   C (16 x 8, f32):        (row g, n 2t), (row g, n 2t+1), (row g+8, n 2t), (row g+8, n 2t+1)
 // so the C tiles 2j and 2j+1 of one layer are, after the activation, exactly
 // the A fragment of k-block j of the next layer (kept in registers).
+#include <atomic>
 #include <cmath>
 
 #include <cuda_bf16.h>
@@ -497,17 +498,29 @@ __global__ void k_mlp_init(float* __restrict__ params, uint32_t key0, uint32_t k
     }
 }
 
+// The kernels' dynamic shared memory above 48 KB must be allowed once per
+// device (a function attribute of each device's context); one bit per
+// device, set by whichever thread configures it first.
+std::atomic<unsigned long long> g_fwd_configured{0}, g_train_configured{0};
+
+int allow_smem(std::atomic<unsigned long long>& done, const void* kernel, int bytes)
+{
+    int dev = 0;
+    WOB_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return WOB_OK;
+    WOB_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.fetch_or(bit, std::memory_order_release);
+    return WOB_OK;
+}
+
 }  // namespace
 
 int mlp_forward(const float* params, const float* x, int64_t n, float* out, cudaStream_t s,
                 int stride)
 {
     if (n <= 0) return WOB_OK;
-    static bool configured = false;
-    if (!configured) {
-        WOB_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
-        configured = true;
-    }
+    WOB_TRY(allow_smem(g_fwd_configured, (const void*)k_mlp_forward, kFwdSmem));
     const int64_t tiles = (n + 15) / 16;
     const int grid = grid_for((const void*)k_mlp_forward, 128, kFwdSmem, tiles * 32);
     k_mlp_forward<<<grid, 128, kFwdSmem, s>>>(params, x, stride, n, out);
@@ -526,11 +539,7 @@ int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const f
                       cudaStream_t s)
 {
     if (n <= 0) return WOB_OK;
-    static bool configured = false;
-    if (!configured) {
-        WOB_CUDA_TRY(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem));
-        configured = true;
-    }
+    WOB_TRY(allow_smem(g_train_configured, (const void*)k_mlp_train, kTrainSmem));
     const int blocks = (int)((n + kTrainRows - 1) / kTrainRows);
     float* partial = ws;
     float* lp = ws + (int64_t)blocks * kParams;
