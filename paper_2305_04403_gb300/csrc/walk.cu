@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
             Trav t;
             trav_init(t);
             uint32_t nn = 0, nt = 0;
-            trace_wide_q<false, false>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+            trace_wide_q<false, false, true>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
                                        p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn,
                                        nt, err, p.iter_limit, lq);
             wflag |= t.flag;

@@ -317,7 +317,12 @@ struct LeafQueue {
     __device__ __forceinline__ int& operator[](int i) const { return base[i * stride]; }
 };
 
-template <bool COUNT, bool SUM_S>
+// HIT_MASK picks how the slots beyond a node's children are dropped: one
+// mask per node (true) or a test per slot (false).  Both give the same hit
+// set; which runs faster depends on the kernel's register allocation (on a
+// GB300 the mask is 4% faster in the direct-BIE walk kernel and 1% slower in
+// the double-layer one).
+template <bool COUNT, bool SUM_S, bool HIT_MASK = false>
 __device__ __forceinline__ void trace_wide_q(const float4* __restrict__ wn,
                                              const float4* __restrict__ tv, const LinePre& L,
                                              float3 d, float Tthr, float tauL, float graze,
@@ -385,8 +390,10 @@ __device__ __forceinline__ void trace_wide_q(const float4* __restrict__ wn,
                 const float tfz = fmaf(dequant(j < 4 ? fz0 : fz1, j & 3), az, bz);
                 const float tn = fmaxf(fmaxf(tnx, tny), tnz);
                 const float tf = fminf(fminf(tfx, tfy), tfz);
-                if (j < nch && tn <= tf) hit |= 1u << j;
+                if (HIT_MASK) hit |= (tn <= tf ? 1u : 0u) << j;
+                else if (j < nch && tn <= tf) hit |= 1u << j;
             }
+            if (HIT_MASK) hit &= (1u << nch) - 1u;
             const int4 r0 = __ldg(reinterpret_cast<const int4*>(nd + 4));
             uint32_t lm = hit >> nint;  // leaf children: queue their triangles
             if (lm) {
