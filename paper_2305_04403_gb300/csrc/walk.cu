@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
             const int32_t prim = p.query_prim[qi];
             start = (prim >= 0 && prim < p.T) ? p.inv_order[prim] : -1;
         }
-        const double v = dl_walk<COUNT, DEBUG, GRAD>(
+        const double v = dl_walk<COUNT, DEBUG, GRAD, GRAD>(
             G, p.data, (double)p.phi, p.M, key, q, w, x, start, ws, stack, hits, err, wflag,
             DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c, lq);
         p.per_walk[idx] = v;

@@ -320,8 +320,9 @@ struct LeafQueue {
 // HIT_MASK picks how the slots beyond a node's children are dropped: one
 // mask per node (true) or a test per slot (false).  Both give the same hit
 // set; which runs faster depends on the kernel's register allocation (on a
-// GB300 the mask is 4% faster in the direct-BIE walk kernel and 1% slower in
-// the double-layer one).
+// GB300 the mask is 4% faster in the direct-BIE walk kernel, 3% in the
+// batched one, 1% in the gradient walks and 1% slower in the plain
+// double-layer walks).
 template <bool COUNT, bool SUM_S, bool HIT_MASK = false>
 __device__ __forceinline__ void trace_wide_q(const float4* __restrict__ wn,
                                              const float4* __restrict__ tv, const LinePre& L,
@@ -631,8 +632,8 @@ __device__ __forceinline__ double3 grad_factor(const float4* __restrict__ tv, in
 // count of each line, -1 for lines not traced.  start_pos >= 0: x0 lies on
 // that triangle (leaf position) and the walk estimates the density nu(x0)
 // (Eq. indirect_double_boundary_reordered2): x0 is vertex 1 with weight 1
-// and lines 1 .. M-1 follow.
-template <bool COUNT, bool DEBUG, bool GRAD = false>
+// and lines 1 .. M-1 follow.  HIT_MASK: the node-test form of trace_wide_q.
+template <bool COUNT, bool DEBUG, bool GRAD = false, bool HIT_MASK = true>
 __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, double phi, int M,
                                           StreamKey key, uint32_t q, uint32_t w, double3 x0,
                                           int start_pos, const WalkSlot& ws, int* stack,
@@ -672,8 +673,8 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         Trav t;
         trav_init(t);
         uint32_t nn = 0, nt = 0;
-        trace_wide_q<COUNT, false>(G.nodes, G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, G.tauL,
-                                   G.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn, nt,
+        trace_wide_q<COUNT, false, HIT_MASK>(G.nodes, G.tv, L, make_float3(0.f, 0.f, 0.f), Tthr,
+                                             G.tauL, G.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn, nt,
                                    err, G.iter_limit, lq);
         if (COUNT) {
             c.lines++;
