@@ -155,6 +155,15 @@ def _dist():
     return ws, rank, local
 
 
+def _star_config(Q: int, leaf: int, ws: int) -> dict:
+    """The headline workload's `config` (both arms of the benchmark)."""
+    return {"workload": f"star-shaped icosphere L6 (81,920 tris), z=0 slice Q={Q}, "
+                        f"{WALKS} walks, M={MAX_LEN}, Dirichlet double layer, g=1/|x-(3,0,0)|",
+            "queries": Q, "walks": WALKS, "max_len": MAX_LEN, "leaf_size": leaf,
+            "l2": "flushed (512 MB write) between timed steps",
+            "parallelism": f"{ws} independent replica(s)"}
+
+
 def run_ours(args):
     import torch
     from paper_2305_04403_gb300 import build as B
@@ -251,11 +260,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry / f64 accumulation",
         "data": "synthetic (seeded star mesh, slice queries)",
-        "config": {"workload": f"star-shaped icosphere L6 (81,920 tris), z=0 slice Q={Q}, "
-                               f"{WALKS} walks, M={MAX_LEN}, Dirichlet double layer, g=1/|x-(3,0,0)|",
-                   "queries": Q, "walks": WALKS, "max_len": MAX_LEN, "leaf_size": args.leaf,
-                   "l2": "flushed (512 MB write) between timed steps",
-                   "parallelism": f"{ws} independent replica(s)"},
+        "config": _star_config(Q, args.leaf, ws),
         "clocks": clocks,
         "e2e": {"value": lines_all * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": Q * 12, "d2h_bytes_per_step": Q * 16},
@@ -896,14 +901,15 @@ def run_reference(args):
         t_total += time.perf_counter() - t0
         lines_total += int((r["line_m"] >= 0).sum())
     value = lines_total / t_total
-    sample = (f"{len(sel)} queries x {WALKS // 8} walks x up to {MAX_LEN} vertices per step, "
-              f"brute force over 81,920 triangles")
+    sample = (f"{len(sel)} of the {len(q)} queries x {WALKS // 8} walks x up to {MAX_LEN} "
+              f"vertices per step (step i takes walks {WALKS // 8} i and on), brute force over "
+              f"81,920 triangles")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "same mesh, data and walks as the GPU arm; bounded query "
-                                   "sample per step (CPU oracle)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded star mesh, slice queries)",
+            "config": _star_config(len(q), args.leaf, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
