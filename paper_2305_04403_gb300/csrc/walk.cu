@@ -551,8 +551,12 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS)
 // the path is 0, the path adds nothing but still counts in the mean).
 // k_fwd_connect: work items are (block of kFwdThreads x kFwdQ queries, split
 // of the paths); a persistent grid takes them in turn.  Whole paths are
-// staged in shared memory; each thread keeps kFwdQ queries in registers, so
-// one broadcast shared load feeds kFwdQ pairs; distances, G and v_p in FP32.
+// staged in shared memory; each thread keeps kFwdQ queries in registers as
+// pairs, so one broadcast shared load feeds kFwdQ pairs and the distances,
+// squared distances and the sum of w G run as packed FP32x2 operations (two
+// queries per instruction, each lane rounded as the scalar operation would
+// be), which leaves the reciprocal square roots (one MUFU operation per
+// pair) as the bound; distances, G and v_p in FP32.
 // The sums over paths run in FP32 for kFwdFold paths and are then folded into
 // FP64 sums kept in shared memory (FP64 issues at 1/64 of the FP32 rate on
 // this GPU: one FP64 add per path and query would cost as much as the
@@ -610,14 +614,25 @@ __global__ void __launch_bounds__(kFwdThreads)
         const int sp = (int)(item / q_blocks);
         const int64_t pb = (int64_t)sp * per_split;
         const int64_t pe = pb + per_split < n_paths ? pb + per_split : n_paths;
-        float x[kFwdQ], y[kFwdQ], z[kFwdQ], s32[kFwdQ], ss32[kFwdQ];
+        // negated query coordinates, queries 2i and 2i + 1 in pair i: c - x
+        // is computed as c + (-x), which rounds identically
+        float2 nx[kFwdQ / 2], ny[kFwdQ / 2], nz[kFwdQ / 2];
+        float s32[kFwdQ], ss32[kFwdQ];
 #pragma unroll
         for (int k = 0; k < kFwdQ; ++k) {
             const int64_t qi = (qb * kFwdQ + k) * kFwdThreads + t;
             const bool ok = qi < Q;
-            x[k] = ok ? queries[3 * qi] : 0.f;
-            y[k] = ok ? queries[3 * qi + 1] : 0.f;
-            z[k] = ok ? queries[3 * qi + 2] : 0.f;
+            const float qx = ok ? -queries[3 * qi] : 0.f, qy = ok ? -queries[3 * qi + 1] : 0.f,
+                        qz = ok ? -queries[3 * qi + 2] : 0.f;
+            if (k & 1) {
+                nx[k / 2].y = qx;
+                ny[k / 2].y = qy;
+                nz[k / 2].y = qz;
+            } else {
+                nx[k / 2].x = qx;
+                ny[k / 2].x = qy;
+                nz[k / 2].x = qz;
+            }
             s32[k] = ss32[k] = 0.f;
             fsum[k][t] = fsq[k][t] = 0.0;
         }
@@ -630,23 +645,28 @@ __global__ void __launch_bounds__(kFwdThreads)
             __syncthreads();
             for (int pp = 0; pp < np; ++pp) {
                 if (!live[pp]) continue;  // the same path for the whole block
-                float v[kFwdQ];
+                float2 v2[kFwdQ / 2];
 #pragma unroll
-                for (int k = 0; k < kFwdQ; ++k) v[k] = 0.f;
+                for (int k = 0; k < kFwdQ / 2; ++k) v2[k] = make_float2(0.f, 0.f);
                 const float4* rp = rec + pp * M;
 #pragma unroll 2
                 for (int j = 0; j < M; ++j) {
                     const float4 c = rp[j];
+                    const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y),
+                                 cz = make_float2(c.z, c.z), cw = make_float2(c.w, c.w);
 #pragma unroll
-                    for (int k = 0; k < kFwdQ; ++k) {
-                        const float dx = c.x - x[k], dy = c.y - y[k], dz = c.z - z[k];
-                        v[k] = fmaf(c.w, rsqrt_ftz(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), v[k]);
+                    for (int k = 0; k < kFwdQ / 2; ++k) {
+                        const float2 dx = __fadd2_rn(cx, nx[k]), dy = __fadd2_rn(cy, ny[k]),
+                                     dz = __fadd2_rn(cz, nz[k]);
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                        v2[k] = __ffma2_rn(cw, make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y)), v2[k]);
                     }
                 }
 #pragma unroll
                 for (int k = 0; k < kFwdQ; ++k) {
-                    s32[k] += v[k];
-                    ss32[k] = fmaf(v[k], v[k], ss32[k]);
+                    const float v = (k & 1) ? v2[k / 2].y : v2[k / 2].x;
+                    s32[k] += v;
+                    ss32[k] = fmaf(v, v, ss32[k]);
                 }
                 if (++cnt == kFwdFold) {
 #pragma unroll
