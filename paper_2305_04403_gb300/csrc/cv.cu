@@ -203,6 +203,27 @@ __device__ __forceinline__ void node_acc(float4 nd, float omega, float3 x, float
     s0 = fmaf(omega, t, s0);
 }
 
+// node_acc for two nodes at once, stored as (x, x', y, y'), (z, z', w, w'):
+// packed FP32x2 operations, every lane rounded as node_acc rounds it (r =
+// node - x as node + (-x)).
+static_assert(kCoarse % 2 == 1, "coarse nodes: pairs plus one");
+struct NegPoint2 {
+    float2 x, y, z;  // (-x, -x), ...
+};
+
+__device__ __forceinline__ void node_acc2(float4 a, float4 b, float2 omega, const NegPoint2& nx,
+                                          float2& s1, float2& s0)
+{
+    const float2 rx = __fadd2_rn(make_float2(a.x, a.y), nx.x);
+    const float2 ry = __fadd2_rn(make_float2(a.z, a.w), nx.y);
+    const float2 rz = __fadd2_rn(make_float2(b.x, b.y), nx.z);
+    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 t = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+    s1 = __ffma2_rn(make_float2(b.z, b.w), t, s1);
+    s0 = __ffma2_rn(omega, t, s0);
+}
+
 // On the flat triangle j every node has the same r . n_j = d_j - x . n_j, so
 //   sum_q w_q (r . n)/r^3 (f_q - fx) = (d_j - x . n_j) (S1 - fx area_j S0),
 // S1 = sum_q (w_q f_q) / r_q^3, S0 = sum_q omega_q / r_q^3 (w_q = area_j omega_q).
@@ -215,6 +236,8 @@ __device__ __forceinline__ float tri_term(float4 tp, float area, float3 x, float
 
 // Far-field tile: kTileTris triangles (centroid + near radius, plane, area)
 // and their packed coarse nodes, staged in shared memory by the whole block.
+// A triangle's nodes 0..5 are stored as pairs (2q, 2q + 1), each pair as
+// (x, x', y, y') and (z, z', w, w'), node 6 as (x, y, z, w): seven float4.
 constexpr int kQuadThreads = 256;
 constexpr int kTileTris = 64;
 struct FarTile {
@@ -245,6 +268,13 @@ __device__ __forceinline__ float quad_sum(const CvGeom& c, FarTile& sm, float3 x
                                           float fx)
 {
     double tot = 0.0;
+    // the coarse weights of the node pairs and the negated query, in registers
+    float2 om[(kCoarse - 1) / 2];
+#pragma unroll
+    for (int q = 0; q < (kCoarse - 1) / 2; ++q)
+        om[q] = make_float2(c_coarse_w[2 * q], c_coarse_w[2 * q + 1]);
+    const float om_last = c_coarse_w[kCoarse - 1];
+    const NegPoint2 nx{make_float2(-x.x, -x.x), make_float2(-x.y, -x.y), make_float2(-x.z, -x.z)};
     for (int j0 = 0; j0 < c.T; j0 += kTileTris) {
         const int nt = min(kTileTris, c.T - j0);
         __syncthreads();  // the previous tile is no longer read
@@ -253,17 +283,32 @@ __device__ __forceinline__ float quad_sum(const CvGeom& c, FarTile& sm, float3 x
             sm.tp[i] = __ldg(c.tri_p + j0 + i);
             sm.ta[i] = __ldg(c.tri_a + j0 + i);
         }
-        for (int i = threadIdx.x; i < nt * kCoarse; i += blockDim.x)
-            sm.node[i] = __ldg(c.coarse_pk + (int64_t)kCoarse * j0 + i);
+        for (int i = threadIdx.x; i < nt * kCoarse; i += blockDim.x) {
+            const float4 a = __ldg(c.coarse_pk + (int64_t)kCoarse * j0 + i);
+            const int jj = i / kCoarse, q = i - jj * kCoarse;
+            float* d = reinterpret_cast<float*>(sm.node + kCoarse * jj);
+            if (q < kCoarse - 1) {
+                float* e = d + 8 * (q >> 1) + (q & 1);
+                e[0] = a.x;
+                e[2] = a.y;
+                e[4] = a.z;
+                e[6] = a.w;
+            } else {
+                sm.node[kCoarse * jj + kCoarse - 1] = a;
+            }
+        }
         __syncthreads();
         float part = 0.f;
         for (int jj = 0; jj < nt; ++jj) {
             const int j = j0 + jj;
             const bool near_me = is_near(sm.tc[jj], x);
-            float s1 = 0.f, s0 = 0.f;
+            const float4* nb = sm.node + kCoarse * jj;
+            float2 s1p = make_float2(0.f, 0.f), s0p = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int q = 0; q < kCoarse; ++q)
-                node_acc(sm.node[kCoarse * jj + q], c_coarse_w[q], x, s1, s0);
+            for (int q = 0; q < (kCoarse - 1) / 2; ++q)
+                node_acc2(nb[2 * q], nb[2 * q + 1], om[q], nx, s1p, s0p);
+            float s1 = s1p.x + s1p.y, s0 = s0p.x + s0p.y;
+            node_acc(nb[kCoarse - 1], om_last, x, s1, s0);
             const float term = tri_term(sm.tp[jj], sm.ta[jj], x, fx, s1, s0);
             part += (j == own || near_me) ? 0.f : term;
             if (own < 0 && __any_sync(0xFFFFFFFFu, near_me)) {
