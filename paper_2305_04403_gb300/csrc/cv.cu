@@ -151,14 +151,28 @@ __global__ void k_cv_nodes(const float* __restrict__ verts, const int32_t* __res
     }
 }
 
-// Packed nodes for the sums: position and weight x value.
+// Packed nodes for the sums: position and weight x value, `per` nodes per
+// triangle in the paired layout the sums read -- nodes 2i and 2i + 1 as
+// (x, x', y, y'), (z, z', w, w'), an odd last node as (x, y, z, w) -- so
+// that two nodes run as packed FP32x2 operations.
 __global__ void k_cv_pack(const float4* __restrict__ nodes, const float* __restrict__ val,
-                          int64_t n, float4* __restrict__ out)
+                          int64_t n, int per, float4* __restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float4 a = nodes[i];
-        out[i] = make_float4(a.x, a.y, a.z, a.w * val[i]);
+        const float w = a.w * val[i];
+        const int64_t j = i / per;
+        const int q = (int)(i - j * per);
+        if (q < (per & ~1)) {
+            float* e = reinterpret_cast<float*>(out + j * per) + 8 * (q >> 1) + (q & 1);
+            e[0] = a.x;
+            e[2] = a.y;
+            e[4] = a.z;
+            e[6] = w;
+        } else {
+            out[i] = make_float4(a.x, a.y, a.z, w);
+        }
     }
 }
 
@@ -235,9 +249,8 @@ __device__ __forceinline__ float tri_term(float4 tp, float area, float3 x, float
 }
 
 // Far-field tile: kTileTris triangles (centroid + near radius, plane, area)
-// and their packed coarse nodes, staged in shared memory by the whole block.
-// A triangle's nodes 0..5 are stored as pairs (2q, 2q + 1), each pair as
-// (x, x', y, y') and (z, z', w, w'), node 6 as (x, y, z, w): seven float4.
+// and their packed coarse nodes (paired layout, see k_cv_pack), staged in
+// shared memory by the whole block.
 constexpr int kQuadThreads = 256;
 constexpr int kTileTris = 64;
 struct FarTile {
@@ -250,9 +263,15 @@ struct FarTile {
 // Fine-node sum of triangle j (its 4^level sub-triangles).
 __device__ __forceinline__ float fine_tri(const CvGeom& c, int j, float3 x, float fx)
 {
-    float s1 = 0.f, s0 = 0.f;
     const float4* nd = c.fine_pk + (int64_t)c.F * j;
-    for (int q = 0; q < c.F; ++q) node_acc(__ldg(nd + q), c_fine_w[q], x, s1, s0);
+    const NegPoint2 nx{make_float2(-x.x, -x.x), make_float2(-x.y, -x.y), make_float2(-x.z, -x.z)};
+    float2 s1p = make_float2(0.f, 0.f), s0p = make_float2(0.f, 0.f);
+    const int pairs = c.F >> 1;
+    for (int q = 0; q < pairs; ++q)
+        node_acc2(__ldg(nd + 2 * q), __ldg(nd + 2 * q + 1),
+                  make_float2(c_fine_w[2 * q], c_fine_w[2 * q + 1]), nx, s1p, s0p);
+    float s1 = s1p.x + s1p.y, s0 = s0p.x + s0p.y;
+    if (c.F & 1) node_acc(__ldg(nd + c.F - 1), c_fine_w[c.F - 1], x, s1, s0);
     return tri_term(__ldg(c.tri_p + j), __ldg(c.tri_a + j), x, fx, s1, s0);
 }
 
@@ -283,20 +302,8 @@ __device__ __forceinline__ float quad_sum(const CvGeom& c, FarTile& sm, float3 x
             sm.tp[i] = __ldg(c.tri_p + j0 + i);
             sm.ta[i] = __ldg(c.tri_a + j0 + i);
         }
-        for (int i = threadIdx.x; i < nt * kCoarse; i += blockDim.x) {
-            const float4 a = __ldg(c.coarse_pk + (int64_t)kCoarse * j0 + i);
-            const int jj = i / kCoarse, q = i - jj * kCoarse;
-            float* d = reinterpret_cast<float*>(sm.node + kCoarse * jj);
-            if (q < kCoarse - 1) {
-                float* e = d + 8 * (q >> 1) + (q & 1);
-                e[0] = a.x;
-                e[2] = a.y;
-                e[4] = a.z;
-                e[6] = a.w;
-            } else {
-                sm.node[kCoarse * jj + kCoarse - 1] = a;
-            }
-        }
+        for (int i = threadIdx.x; i < nt * kCoarse; i += blockDim.x)
+            sm.node[i] = __ldg(c.coarse_pk + (int64_t)kCoarse * j0 + i);
         __syncthreads();
         float part = 0.f;
         for (int jj = 0; jj < nt; ++jj) {
@@ -680,10 +687,10 @@ void free_cv(wob_cv_s* c)
 int pack_nodes(wob_cv_s* c, cudaStream_t s)
 {
     const int64_t nc = (int64_t)c->T * kCoarse, nf = (int64_t)c->T * c->F;
-    k_cv_pack<<<grid_for((const void*)k_cv_pack, 256, 0, nc), 256, 0, s>>>(c->coarse, c->coarse_val,
-                                                                          nc, c->coarse_pk);
-    k_cv_pack<<<grid_for((const void*)k_cv_pack, 256, 0, nf), 256, 0, s>>>(c->fine, c->fine_val, nf,
-                                                                          c->fine_pk);
+    k_cv_pack<<<grid_for((const void*)k_cv_pack, 256, 0, nc), 256, 0, s>>>(
+        c->coarse, c->coarse_val, nc, kCoarse, c->coarse_pk);
+    k_cv_pack<<<grid_for((const void*)k_cv_pack, 256, 0, nf), 256, 0, s>>>(
+        c->fine, c->fine_val, nf, c->F, c->fine_pk);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
