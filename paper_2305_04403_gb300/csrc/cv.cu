@@ -45,8 +45,8 @@ struct CvGeom {
     const float4* tri_c;         // centroid, near radius (near x longest edge)
     const float4* tri_p;         // unit normal n, plane offset n . y of the triangle
     const float* tri_a;          // area
-    const float4* coarse_pk;     // T x 7: position, weight x node value
-    const float4* fine_pk;       // T x F
+    const float4* coarse_pk;     // T x 7: position, weight x node value (paired, k_cv_pack)
+    const float4* fine_pk;       // T x F, the same layout
     const int* cand_off;         // per triangle: candidate near triangles
     const int* cand;
 };
