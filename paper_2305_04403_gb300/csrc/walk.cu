@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS)
 constexpr int kFwdTile = 1024;     // vertex records per tile (max_len <= kFwdTile)
 constexpr int kFwdThreads = 128;
 constexpr int kFwdQ = 8;           // queries per thread
+static_assert(kFwdQ % 2 == 0, "queries are processed in pairs");
 constexpr int kFwdFold = 32;       // paths summed in FP32 before an FP64 fold
 constexpr float kFwdFar = 1e18f;   // |r|^2 ~ 3e36 stays finite in FP32
 
