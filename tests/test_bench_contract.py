@@ -1,6 +1,6 @@
 """The benchmark's reference arm (the CPU oracle on a bounded sample) prints
 one JSON line with the keys of the GPU arm's line, on the GPU arm's metric,
-unit, direction and workload config."""
+unit, direction and workload config; the clock sampler's parser."""
 import json
 import os
 import subprocess
@@ -29,3 +29,25 @@ def test_reference_arm_json_line():
     assert cb["cores"] >= 1 and "1 of the" in cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_clock_samples_summary():
+    """The nvidia-smi sampler's parser: median SM clock, the maximum, and
+    every throttle reason seen Active in any sample; "[N/A]" or short lines
+    are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    c.out = "\n".join([
+        "0, 2070 MHz, 2070 MHz, 900.10 W, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980 MHz, 2070 MHz, 1390.00 W, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2055 MHz, 2070 MHz, 1200.00 W, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070 MHz, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+        "0, 2070 MHz",
+    ])
+    s = c.summary()
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.out = "0, 2070 MHz, 2070 MHz, 900 W, 0x0, Active, Not Active, Active, Not Active"
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.out = ""
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
