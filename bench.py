@@ -45,10 +45,9 @@ OPS_NODE, OPS_TRI, OPS_HIT, OPS_LINE = 320, 41, 100, 235
 BYTES_NODE, BYTES_TRI = 96, 48
 # DRAM bytes (read + write) of one full-size k_dl_walks launch of this
 # workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
-# dram__bytes_write.sum, or None while the kernel has changed since the
-# last capture (profiles/k_dl_walks_star6_wide.md: 35.49e6 + 228.46e6 bytes
-# with a 16-entry leaf queue; the queue now holds 15).
-TRAFFIC_FULL = None
+# dram__bytes_write.sum (profiles/k_dl_walks_star6_wide.md); None while the
+# kernel has changed since the last capture.
+TRAFFIC_FULL = (29497, 1, 37.86e6 + 228.84e6)
 
 
 def _peaks():
