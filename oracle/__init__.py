@@ -91,8 +91,8 @@ def _load():
                                                P, P, P, P, P, P, P, ctypes.c_int]
             lib.oracle_trace_lines.restype = ctypes.c_int
             lib.oracle_dl_walks.argtypes = [P, I64, P, I64, ctypes.POINTER(_Data), I32, P, P, I64,
-                                            I64, I64, I32, I32, U64, U32, D, D, P, P, P, P, P,
-                                            ctypes.c_int]
+                                            I64, I64, I32, I32, U64, U32, D, D, P, P, P, P, P, P,
+                                            P, ctypes.c_int]
             lib.oracle_dl_walks.restype = ctypes.c_int
             lib.oracle_nd_walks.argtypes = lib.oracle_dl_walks.argtypes[:-2] + [ctypes.c_int]
             lib.oracle_nd_walks.restype = ctypes.c_int
@@ -228,6 +228,16 @@ def _data(mode: int, vertex_data=None, poly=None, x0=None, scale: float = 1.0):
     return d, keep
 
 
+def _line_arrays(Q: int, walks: int, max_len: int, want: bool) -> dict:
+    """Per-line outputs of the walk functions: hit count, picked triangle,
+    near-degenerate flag (None each when not wanted)."""
+    shape = (Q, walks, max_len)
+    if not want:
+        return dict(line_m=None, line_prim=None, line_flag=None)
+    return dict(line_m=np.empty(shape, np.int32), line_prim=np.empty(shape, np.int32),
+                line_flag=np.empty(shape, np.uint8))
+
+
 def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, problem: int = 0,
              phi: int = 1, mode: int = DATA_POLY, vertex_data=None, poly=None, x0=None,
              scale: float = 1.0, q_offset: int = 0, walk_begin: int = 0, tau: float = TAU,
@@ -237,8 +247,10 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     lies on) the walks start on the boundary and estimate the density nu
     there.  Returns per_walk (Q,N), flag (Q,N),
     abs_terms (Q,N: sum over the walk's terms of |term|, the scale of its
-    rounding error), with want_lines line_m (Q,N,M) and with want_grad the
-    per-walk gradient estimates grad (3,Q,N) of the same walks."""
+    rounding error), with want_lines per line the hit count line_m, the
+    picked triangle line_prim and the near-degenerate flag line_flag
+    (Q,N,M), and with want_grad the per-walk gradient estimates grad (3,Q,N)
+    of the same walks."""
     v = _c(verts, np.float32)
     t = _c(tris, np.int32)
     q = _c(queries, np.float32).reshape(-1, 3)
@@ -246,21 +258,21 @@ def dl_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     data, keep = _data(mode, vertex_data, poly, x0, scale)
     per_walk = np.empty((Q, walks), np.float64)
     flag = np.empty((Q, walks), np.uint8)
-    line_m = np.empty((Q, walks, max_len), np.int32) if want_lines else None
+    lines = _line_arrays(Q, walks, max_len, want_lines)
     abs_terms = np.empty((Q, walks), np.float64)
     qp = None if query_prim is None else _c(query_prim, np.int32)
     grad = np.empty((3, Q, walks), np.float64) if want_grad else None
     rc = _load().oracle_dl_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
                                  _p(q), _p(qp), Q, q_offset, walk_begin, walks, max_len, seed,
-                                 problem,
-                                 tau, graze, _p(per_walk), _p(flag), _p(line_m), _p(abs_terms),
-                                 _p(grad), nthreads)
+                                 problem, tau, graze, _p(per_walk), _p(flag),
+                                 *[_p(a) for a in lines.values()], _p(abs_terms), _p(grad),
+                                 nthreads)
     del keep
     if rc != 0:
         raise RuntimeError("oracle_dl_walks failed")
     out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
     if want_lines:
-        out["line_m"] = line_m
+        out.update(lines)
     if want_grad:
         out["grad"] = grad
     return out
@@ -274,7 +286,8 @@ def nd_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     """Neumann walks through the direct boundary integral equation (Sec. 4.2):
     lines for the dG/dn_y term, one area sample per vertex for the G q term,
     q = dh/dn of the field (or the P1 vertex data); with query_prim the walks
-    start on the boundary.  Returns per_walk, flag, abs_terms (and line_m)."""
+    start on the boundary.  Returns per_walk, flag, abs_terms (and, with
+    want_lines, line_m, line_prim and line_flag as dl_walks)."""
     v = _c(verts, np.float32)
     t = _c(tris, np.int32)
     q = _c(queries, np.float32).reshape(-1, 3)
@@ -282,19 +295,19 @@ def nd_walks(verts, tris, queries, walks: int, max_len: int, seed: int = 0, prob
     data, keep = _data(mode, vertex_data, poly, x0, scale)
     per_walk = np.empty((Q, walks), np.float64)
     flag = np.empty((Q, walks), np.uint8)
-    line_m = np.empty((Q, walks, max_len), np.int32) if want_lines else None
+    lines = _line_arrays(Q, walks, max_len, want_lines)
     abs_terms = np.empty((Q, walks), np.float64)
     qp = None if query_prim is None else _c(query_prim, np.int32)
     rc = _load().oracle_nd_walks(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.byref(data), phi,
                                  _p(q), _p(qp), Q, q_offset, walk_begin, walks, max_len, seed,
-                                 problem, tau, graze, _p(per_walk), _p(flag), _p(line_m),
-                                 _p(abs_terms), nthreads)
+                                 problem, tau, graze, _p(per_walk), _p(flag),
+                                 *[_p(a) for a in lines.values()], _p(abs_terms), nthreads)
     del keep
     if rc != 0:
         raise RuntimeError("oracle_nd_walks failed")
     out = dict(per_walk=per_walk, flag=flag, abs_terms=abs_terms)
     if want_lines:
-        out["line_m"] = line_m
+        out.update(lines)
     return out
 
 

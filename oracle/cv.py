@@ -293,7 +293,9 @@ def cv_walks(verts, tris, queries, walks: int, max_len: int, params, nodes: Node
              near: float = 3.0):
     """Residual walks for D rho (per walk values, Q x N) and D nu_t per query.
     Data: the harmonic polynomial `poly` evaluated at the walk's vertices.
-    `params` None means nu_t = 0 (then the walks are plain WoB)."""
+    `params`: the network's parameters, or a callable nu_t on (n, 3) points
+    (node_vals must then hold nu_t at the nodes); None means nu_t = 0 (then
+    the walks are plain WoB)."""
     q = np.asarray(queries, np.float32).reshape(-1, 3)
     Q = q.shape[0]
     nw = Q * walks
@@ -324,7 +326,7 @@ def cv_walks(verts, tris, queries, walks: int, max_len: int, params, nodes: Node
         if params is None:
             src = 2.0 * phi * g
         else:
-            nt, _ = mlp_forward(params, y)
+            nt = params(y) if callable(params) else mlp_forward(params, y)[0]
             hn = np.array([quad_H(nodes, node_vals, y[j], prim[j], nt[j], phi, near)
                            for j in range(len(idx))])
             src = 2.0 * phi * g - nt + hn

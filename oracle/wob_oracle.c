@@ -28,10 +28,13 @@
  *  - The last vertex of a walk of M vertices gets half the source term
  *    (phi * g instead of 2 phi g), Sec. 4.1.2, for every estimator.
  *  - A line is "near-degenerate" (flagged) if, for a triangle whose
- *    tau*L-expanded projection contains the line, the line passes within
- *    tau*L of one of its edges or meets its plane at a grazing angle
- *    (|d . n| < graze), or if a non-self hit lies within |t| < tau*L.
- *    L is the diagonal of the mesh bounding box.
+ *    bounding box padded by tau*L the line meets and whose tau*L-expanded
+ *    projection contains the line, the line passes within tau*L of one of
+ *    its edges or meets its plane at a grazing angle (|d . n| < graze), or
+ *    if a non-self hit lies within |t| < tau*L.  L is the diagonal of the
+ *    mesh bounding box.  (The box condition keeps the flag local: the
+ *    expanded projection of a triangle seen nearly edge-on reaches far
+ *    beyond the triangle along its thin direction.)
  *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key =
  *    (seed_lo ^ problem, seed_hi), counter = (query, walk,
  *    step<<16 | purpose<<12 | attempt, extra).  Line axes by Marsaglia's
@@ -338,6 +341,31 @@ typedef struct {
     double b[3];     /* its barycentrics */
 } line_result;
 
+/* Does the line {o + t d, t real} meet the bounding box of the triangle v,
+ * padded by pad on every side?  Slab test over all t. */
+static int line_meets_box(const double o[3], const double d[3], const double v[3][3], double pad)
+{
+    double tn = -INFINITY, tf = INFINITY;
+    for (int c = 0; c < 3; ++c) {
+        double lo = v[0][c], hi = v[0][c];
+        for (int k = 1; k < 3; ++k) {
+            if (v[k][c] < lo) lo = v[k][c];
+            if (v[k][c] > hi) hi = v[k][c];
+        }
+        lo -= pad;
+        hi += pad;
+        if (d[c] == 0.0) {
+            if (o[c] < lo || o[c] > hi) return 0;
+            continue;
+        }
+        double t0 = (lo - o[c]) / d[c], t1 = (hi - o[c]) / d[c];
+        if (t0 > t1) { double x = t0; t0 = t1; t1 = x; }
+        if (t0 > tn) tn = t0;
+        if (t1 < tf) tf = t1;
+    }
+    return tn <= tf;
+}
+
 static void trace_line(const mesh_t *M, const double o[3], const double d[3], int64_t exclude,
                        uint64_t seed, uint32_t problem, uint32_t q, uint32_t walk,
                        uint32_t step, double tauL, double graze, line_result *r)
@@ -368,7 +396,7 @@ static void trace_line(const mesh_t *M, const double o[3], const double d[3], in
         double nlen = norm3(N);
         int inside_pos = delta[0] > -tauL && delta[1] > -tauL && delta[2] > -tauL;
         int inside_neg = delta[0] < tauL && delta[1] < tauL && delta[2] < tauL;
-        if (inside_pos || inside_neg) {
+        if ((inside_pos || inside_neg) && line_meets_box(o, d, v, tauL)) {
             double mind = fabs(delta[0]);
             if (fabs(delta[1]) < mind) mind = fabs(delta[1]);
             if (fabs(delta[2]) < mind) mind = fabs(delta[2]);
@@ -416,6 +444,22 @@ static void trace_line(const mesh_t *M, const double o[3], const double d[3], in
 /* start_prim >= 0: the walk starts ON the boundary, at x0 on that triangle,
  * and estimates the density nu(x0) (Eq. indirect_double_boundary_reordered2):
  * x0 is vertex 1 (first weight 1), and M - 1 lines follow. */
+/* Per-line records of one walk (each pointer may be NULL): hit count (-1:
+ * line not traced), picked triangle (-1: none) and near-degenerate flag of
+ * line k. */
+typedef struct {
+    int32_t *m;
+    int32_t *prim;
+    uint8_t *flag;
+} line_rec;
+
+static void put_line(const line_rec *L, int32_t k, int32_t m, int32_t prim, int32_t flag)
+{
+    if (L->m) L->m[k] = m;
+    if (L->prim) L->prim[k] = prim;
+    if (L->flag) L->flag[k] = (uint8_t)flag;
+}
+
 /* Gradient weight of the first step (Sec. 4.1.3): the first line's weight
  * -dG/dn_y / p = (m/2) s becomes -grad_x dG/dn_y / p, with
  * grad_x dG/dn_y(x, y) = (n - 3 (w . n) w) / (4 pi r^3), w = (y - x) / r
@@ -438,7 +482,7 @@ static void grad_factor(const mesh_t *M, int64_t prim, const double x[3], const 
 static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const double x0[3],
                       int64_t start_prim, uint32_t q, uint32_t walk, int32_t Mlen,
                       uint64_t seed, uint32_t problem, double tauL, double graze,
-                      uint8_t *flag, int32_t *line_m, double *abs_terms, double grad[3])
+                      uint8_t *flag, const line_rec *lines, double *abs_terms, double grad[3])
 {
     double gf[3] = { 0.0, 0.0, 0.0 };
     double x[3] = { x0[0], x0[1], x0[2] };
@@ -456,14 +500,14 @@ static double dl_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
         A = fabs(c * g);
         exclude = start_prim;
         k0 = 1;
-        if (line_m) line_m[0] = -1;
+        put_line(lines, 0, -1, -1, 0);
     }
     for (int32_t k = k0; k < Mlen; ++k) {
         double d[3];
         line_axis(seed, problem, q, walk, (uint32_t)k, d);
         line_result r;
         trace_line(M, x, d, exclude, seed, problem, q, walk, (uint32_t)k, tauL, graze, &r);
-        if (line_m) line_m[k] = r.m;
+        put_line(lines, k, r.m, r.prim, r.flag);
         if (r.flag) *flag = 1;
         if (r.m == 0) break;
         if (k == 0) {
@@ -675,7 +719,7 @@ static double sl_walk(const mesh_t *M, const oracle_data *D, int kind, double al
 static double nd_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const double x0[3],
                       int64_t start_prim, uint32_t q, uint32_t walk, int32_t Mlen,
                       uint64_t seed, uint32_t problem, double tauL, double graze,
-                      uint8_t *flag, int32_t *line_m, double *abs_terms)
+                      uint8_t *flag, const line_rec *lines, double *abs_terms)
 {
     double x[3] = { x0[0], x0[1], x0[2] };
     int64_t exclude = -1;
@@ -686,7 +730,7 @@ static double nd_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
     if (start_prim >= 0) {
         exclude = start_prim;
         k0 = 1;
-        if (line_m) line_m[0] = -1;
+        put_line(lines, 0, -1, -1, 0);
     }
     for (int32_t k = k0; k <= Mlen; ++k) {
         /* source at vertex k */
@@ -715,7 +759,7 @@ static double nd_walk(const mesh_t *M, const oracle_data *D, int32_t phi, const 
         line_axis(seed, problem, q, walk, (uint32_t)k, d);
         line_result lr;
         trace_line(M, x, d, exclude, seed, problem, q, walk, (uint32_t)k, tauL, graze, &lr);
-        if (line_m) line_m[k] = lr.m;
+        put_line(lines, k, lr.m, lr.prim, lr.flag);
         if (lr.flag) *flag = 1;
         if (lr.m == 0) break;
         const double ms = (double)lr.m * (double)lr.s;
@@ -854,14 +898,16 @@ int oracle_trace_lines(const float *verts, int64_t V, const int32_t *tris, int64
 /* Double-layer Dirichlet walks: per_walk[q*N + w] for walks
  * walk_begin .. walk_begin+N-1 of queries q_offset .. q_offset+Q-1.
  * walk_flag[q*N + w] = 1 if any line of the walk is near-degenerate;
- * line_m[(q*N + w)*M + k] = hit count of line k (-1: not traced). */
+ * line_m[(q*N + w)*M + k] = hit count of line k (-1: not traced),
+ * line_prim[...] its picked triangle (-1: none), line_flag[...] its
+ * near-degenerate flag (each of the three may be NULL). */
 int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t T,
                     const oracle_data *D, int32_t phi, const float *queries,
                     const int32_t *query_prim, int64_t Q,
                     int64_t q_offset, int64_t walk_begin, int32_t N, int32_t Mlen,
                     uint64_t seed, uint32_t problem, double tau, double graze,
-                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, double *abs_terms,
-                    double *per_walk_grad, int nthreads)
+                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, int32_t *line_prim,
+                    uint8_t *line_flag, double *abs_terms, double *per_walk_grad, int nthreads)
 {
     mesh_t M;
     if (mesh_init(&M, verts, V, tris, T, 0)) return -1;
@@ -872,17 +918,15 @@ int oracle_dl_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
     for (int64_t i = 0; i < total; ++i) {
         int64_t qi = i / N, w = i % N;
         double x0[3] = { queries[3 * qi], queries[3 * qi + 1], queries[3 * qi + 2] };
-        int32_t *lm = NULL;
-        if (line_m) {
-            lm = line_m + i * Mlen;
-            for (int32_t k = 0; k < Mlen; ++k) lm[k] = -1;
-        }
+        line_rec lr = { line_m ? line_m + i * Mlen : NULL, line_prim ? line_prim + i * Mlen : NULL,
+                        line_flag ? line_flag + i * Mlen : NULL };
+        for (int32_t k = 0; k < Mlen; ++k) put_line(&lr, k, -1, -1, 0);
         uint8_t f;
         double at;
         double g3[3];
         per_walk[i] = dl_walk(&M, D, phi, x0, query_prim ? query_prim[qi] : -1,
                               (uint32_t)(q_offset + qi),
-                              (uint32_t)(walk_begin + w), Mlen, seed, problem, tauL, graze, &f, lm,
+                              (uint32_t)(walk_begin + w), Mlen, seed, problem, tauL, graze, &f, &lr,
                               &at, per_walk_grad ? g3 : NULL);
         if (per_walk_grad)
             for (int c = 0; c < 3; ++c) per_walk_grad[c * total + i] = g3[c];
@@ -902,8 +946,8 @@ int oracle_nd_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
                     const int32_t *query_prim, int64_t Q,
                     int64_t q_offset, int64_t walk_begin, int32_t N, int32_t Mlen,
                     uint64_t seed, uint32_t problem, double tau, double graze,
-                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, double *abs_terms,
-                    int nthreads)
+                    double *per_walk, uint8_t *walk_flag, int32_t *line_m, int32_t *line_prim,
+                    uint8_t *line_flag, double *abs_terms, int nthreads)
 {
     mesh_t M;
     if (mesh_init(&M, verts, V, tris, T, 1)) return -1;
@@ -914,16 +958,14 @@ int oracle_nd_walks(const float *verts, int64_t V, const int32_t *tris, int64_t 
     for (int64_t i = 0; i < total; ++i) {
         int64_t qi = i / N, w = i % N;
         double x0[3] = { queries[3 * qi], queries[3 * qi + 1], queries[3 * qi + 2] };
-        int32_t *lm = NULL;
-        if (line_m) {
-            lm = line_m + i * Mlen;
-            for (int32_t k = 0; k < Mlen; ++k) lm[k] = -1;
-        }
+        line_rec lr = { line_m ? line_m + i * Mlen : NULL, line_prim ? line_prim + i * Mlen : NULL,
+                        line_flag ? line_flag + i * Mlen : NULL };
+        for (int32_t k = 0; k < Mlen; ++k) put_line(&lr, k, -1, -1, 0);
         uint8_t f;
         double at;
         per_walk[i] = nd_walk(&M, D, phi, x0, query_prim ? query_prim[qi] : -1,
                               (uint32_t)(q_offset + qi), (uint32_t)(walk_begin + w), Mlen, seed,
-                              problem, tauL, graze, &f, lm, &at);
+                              problem, tauL, graze, &f, &lr, &at);
         if (walk_flag) walk_flag[i] = f;
         if (abs_terms) abs_terms[i] = at;
     }
