@@ -47,7 +47,11 @@ BYTES_NODE, BYTES_TRI = 96, 48
 # workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
 # dram__bytes_write.sum (profiles/k_dl_walks_star6_wide.md); None while the
 # kernel has changed since the last capture.
-TRAFFIC_FULL = (29497, 1, 37.86e6 + 228.84e6)
+TRAFFIC_FULL = None
+# The walk kernel's issue-slot use from the same profile: fraction of cycles
+# with an instruction issued, and active threads per warp instruction; None
+# while the kernel has changed since the last capture.
+ISSUE_PROFILE = None
 
 
 def _peaks():
@@ -58,9 +62,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _workload():
+def _workload(kind: str = "star"):
+    """The headline star (coefficients N(0,1)/(l+1)^2, seed 0: a near-convex
+    shape, 1.06 hits per line) or, for `--workload spiky`, the same generator
+    with coefficients N(0,1)/(l+1)^0.5 and seed 3, a genuinely non-convex
+    star whose lines meet the surface up to 7 times (the pick-one-of-m of
+    Sec. 4.4.1 with m > 2); queries on its z = 0 slice."""
     from paper_2305_04403_gb300 import inputs as I
-    v, f, shape = I.star_mesh(6)
+    if kind == "spiky":
+        v, f, shape = I.star_mesh(6, 0.3, 6, 3, 0.5)
+    else:
+        v, f, shape = I.star_mesh(6)
     q = I.star_slice_queries(shape, 256)
     return v, f, q
 
@@ -156,9 +168,11 @@ def _dist():
     return ws, rank, local
 
 
-def _star_config(Q: int, leaf: int, ws: int) -> dict:
+def _star_config(Q: int, leaf: int, ws: int, kind: str = "star") -> dict:
     """The headline workload's `config` (both arms of the benchmark)."""
-    return {"workload": f"star-shaped icosphere L6 (81,920 tris), z=0 slice Q={Q}, "
+    shape = ("spiky star-shaped icosphere L6 (81,920 tris; SH coefficients N(0,1)/(l+1)^0.5, "
+             "seed 3)" if kind == "spiky" else "star-shaped icosphere L6 (81,920 tris)")
+    return {"workload": f"{shape}, z=0 slice Q={Q}, "
                         f"{WALKS} walks, M={MAX_LEN}, Dirichlet double layer, g=1/|x-(3,0,0)|",
             "queries": Q, "walks": WALKS, "max_len": MAX_LEN, "leaf_size": leaf,
             "l2": "flushed (512 MB write) between timed steps",
@@ -177,7 +191,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    v, f, q = _workload()
+    v, f, q = _workload(args.workload)
     if args.queries:
         q = q[:: max(1, len(q) // args.queries)][:args.queries].copy()
     Q = q.shape[0]
@@ -254,41 +268,74 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
     achieved_ops = ops / per_launch_s / 1e12
+    # algorithmic bytes of the traversal: every 8-wide node and leaf triangle
+    # the lines fetch (served from L1/L2: the BVH is L2-resident)
     bytes_step = st["node_visits"] * BYTES_NODE + st["tri_tests"] * BYTES_TRI
+    achieved_gbs = bytes_step / per_launch_s / 1e9
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
     value = lines_all * args.steps / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry / f64 accumulation",
         "data": "synthetic (seeded star mesh, slice queries)",
-        "config": _star_config(Q, args.leaf, ws),
+        "config": _star_config(Q, args.leaf, ws, args.workload),
         "clocks": clocks,
         "e2e": {"value": lines_all * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": Q * 12, "d2h_bytes_per_step": Q * 16},
         "gpu_launches": 2 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak,
-                     "unit": "T lane-ops/s", "frac": achieved_ops / alu_peak,
+        "roofline": {"bound": "l1l2-bytes", "achieved": achieved_gbs, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved_gbs / hbm,
                      "traffic": (TRAFFIC_FULL[2] if TRAFFIC_FULL and
                                  (Q, args.leaf) == TRAFFIC_FULL[:2] else None),
                      "kernel": "k_dl_walks",
-                     "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
-                                    f"({which} sm_max_mhz)"},
-        "memory": {"l1_l2_bytes_per_step": bytes_step,
-                   "achieved_gbs": bytes_step / per_launch_s / 1e9,
-                   "l2_probe_gbs": l2_gbs,
-                   "frac_of_l2_probe": bytes_step / per_launch_s / 1e9 / l2_gbs,
-                   "l2_probe": "wob_probe_l2_read: 20 streaming reads (16-byte loads, L1 "
-                               "bypassed) of a 96 MB buffer, L2-resident after a warm-up "
-                               "call; median of 5 calls",
-                   "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                   "per_line": {"nodes": st["node_visits"] / lines, "tris": st["tri_tests"] / lines,
-                                "hits": st["hits"] / lines, "flagged": st["flagged"] / lines}},
+                     "algorithmic_bytes_per_launch": bytes_step,
+                     "bytes_per_unit": {"wide_node": BYTES_NODE, "triangle": BYTES_TRI},
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({which})",
+                     "l2_probe_gbs": l2_gbs, "frac_of_l2_probe": achieved_gbs / l2_gbs,
+                     "l2_probe": "wob_probe_l2_read: 20 streaming reads (16-byte loads, L1 "
+                                 "bypassed) of a 96 MB buffer, L2-resident after a warm-up "
+                                 "call; median of 5 calls",
+                     "issue_active": ISSUE_PROFILE[0] if ISSUE_PROFILE else None,
+                     "lanes_per_inst": ISSUE_PROFILE[1] if ISSUE_PROFILE else None,
+                     "alu": {"achieved": achieved_ops, "peak": alu_peak, "unit": "T lane-ops/s",
+                             "frac": achieved_ops / alu_peak,
+                             "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
+                                            f"({which} sm_max_mhz)"}},
+        "per_line": {"nodes": st["node_visits"] / lines, "tris": st["tri_tests"] / lines,
+                     "hits": st["hits"] / lines, "flagged": st["flagged"] / lines},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(v, f, q, args.cpu_queries)
     if dist:
         dist.destroy_process_group()
+    if ws == 1 and not args.no_rmse and args.workload == "star":
+        line["time_to_rmse"] = _time_to_rmse_summary(args)
     return line
+
+
+def _time_to_rmse_summary(args) -> dict:
+    """The second half of the metric, measured in the default run: the
+    learned control variate's time to RMSE 1e-3 on the fifth configuration
+    (icosphere L3, g = x^2 - y^2 + 0.5 z, 65,536 queries), beside plain WoB
+    at its best path length (projected from measured seconds per walk,
+    per-walk variance and truncation bias, with a bounded direct run to
+    check the model).  The full record is `--workload cv`."""
+    import copy
+    a = copy.copy(args)
+    a.warmup, a.plain_cap, a.cv_mc = 1, args.rmse_plain_cap, 0
+    r = run_cv(a)
+    return {"metric": r["metric"], "unit": "s", "higher_is_better": False,
+            "workload": r["config"]["workload"],
+            "cv": {"time_to_rmse_s": r["cv"]["solve_s"], "measured": True,
+                   "train_s": r["cv"]["train_s"], "walks": r["cv"]["walks"],
+                   "rmse": r["cv"]["rmse"], "residual_len": r["config"]["cv_len"]},
+            "plain_best": {"M": r["best_plain"]["M"],
+                           "time_to_rmse_s": r["best_plain"]["time_to_rmse_s"],
+                           "projected": True, "direct_check": r["best_plain"]["direct_check"]},
+            "speedup_solve": r["speedup_solve"],
+            "speedup_incl_training": r["speedup_incl_training"],
+            "clocks": r["clocks"], "gpu_launches": r["gpu_launches"]}
 
 
 def run_batched(args):
@@ -929,7 +976,7 @@ def main():
     ap.add_argument("--queries", type=int, default=0,
                     help="evenly subsample this many queries (profiling runs; 0 = all)")
     ap.add_argument("--workload", default="star",
-                    choices=["star", "batched", "cv", "sl", "nd", "grad", "mixed", "fwd"])
+                    choices=["star", "spiky", "batched", "cv", "sl", "nd", "grad", "mixed", "fwd"])
     ap.add_argument("--sl-ris", type=int, default=0,
                     help="sl workload: resampling candidates (0 = area sampling)")
     ap.add_argument("--sl-queries", type=int, default=131072)
@@ -946,6 +993,10 @@ def main():
     ap.add_argument("--cv-max-walks", type=int, default=1 << 16)
     ap.add_argument("--bias-walks", type=int, default=1 << 22)
     ap.add_argument("--plain-cap", type=float, default=20.0)
+    ap.add_argument("--no-rmse", action="store_true",
+                    help="default workload: skip the control variate's time to RMSE 1e-3")
+    ap.add_argument("--rmse-plain-cap", type=float, default=8.0,
+                    help="default workload: seconds of the direct plain-WoB check run")
     ap.add_argument("--problems", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":

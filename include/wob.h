@@ -151,11 +151,15 @@ typedef struct {
     int32_t iter_limit;
 } wob_problem;
 
-/* Per-walk outputs for parity checks (each pointer device, may be NULL). */
+/* Per-walk and per-line outputs for parity checks (each pointer device, may
+ * be NULL).  Line k of walk w of query q is entry (q * N + w) * M + k. */
 typedef struct {
-    double *per_walk;   /* Q x N walk values */
-    uint8_t *walk_flag; /* Q x N: 1 if any line of the walk was near-degenerate */
-    int32_t *line_m;    /* Q x N x M hit counts, -1 for lines not traced */
+    double *per_walk;    /* Q x N walk values */
+    uint8_t *walk_flag;  /* Q x N: 1 if any line of the walk was near-degenerate */
+    int32_t *line_m;     /* Q x N x M hit counts, -1 for lines not traced */
+    int32_t *line_prim;  /* Q x N x M picked triangle (original id), -1 for no hit
+                            or a line not traced */
+    uint8_t *line_flag;  /* Q x N x M: 1 if the line was near-degenerate */
 } wob_debug_out;
 
 /* Counters of the most recent wob_solve_counted() call. */
@@ -218,7 +222,10 @@ void wob_destroy_bvh(wob_bvh b);
  * dh/dn of the field (POLY, POINT) or the P1 vertex data.  Interior Neumann
  * solutions are defined up to a constant: the walks do not fix it.
  * est, var: device, Q doubles.  walks >= 2, 1 <= max_len <= 4096.
- * Allocates scratch of Q * walks doubles on `stream` (stream-ordered).
+ * Allocates Q * ceil(walks / 32) * 16 bytes of scratch on `stream`
+ * (stream-ordered): per query and block of 32 walks the sum and the sum of
+ * squares of the walk values, added in a fixed order (results do not depend
+ * on scheduling); var = (sum of squares - sum * mean) / (walks - 1).
  */
 int wob_solve(const wob_problem *prob, const float *queries, const int32_t *query_prim,
               int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
@@ -297,10 +304,16 @@ int wob_solve_forward(const wob_problem *prob, const float *queries, int64_t Q, 
                       double *est, double *var, double *zpos, double *zw, uint8_t *path_flag,
                       void *stream);
 
-/* As wob_solve, counting traversal work into *stats (synchronises). */
+/* As wob_solve, counting traversal work into *stats (synchronises).  The
+ * counters are also kept for wob_get_stats. */
 int wob_solve_counted(const wob_problem *prob, const float *queries, const int32_t *query_prim,
                       int64_t Q, int32_t walks, int32_t max_len, uint64_t seed, double *est,
                       double *var, wob_stats *stats, void *stream);
+
+/* Counters (line queries, node visits, triangle tests, hits, near-degenerate
+ * lines) of the most recent successful wob_solve_counted call of the calling
+ * thread; all zero before the first.  Errors: WOB_ERR_INVALID_ARG (NULL). */
+int wob_get_stats(wob_stats *out);
 
 /*
  * wob_solve with HOST queries / query_prim / est / var: copies the inputs to
@@ -330,8 +343,9 @@ int wob_solve_host(const wob_problem *prob, const float *queries_host,
  *                  schedules once on this batch (walk counts scaled down)
  *                  and caches the choice in $WOB_TUNE_CACHE (default
  *                  ~/.cache/wob_autotune.json), keyed by GPU and batch shape
- * The batch allocates Q_total * walks doubles of scratch at creation and
- * keeps it until wob_batch_destroy.  The BVHs must outlive the batch.
+ * The batch allocates Q_total * ceil(walks / 32) * 16 bytes of scratch (sum
+ * and sum of squares per query and block of 32 walks) at creation and keeps
+ * it until wob_batch_destroy.  The BVHs must outlive the batch.
  */
 typedef struct wob_batch_s *wob_batch;
 
@@ -353,6 +367,19 @@ typedef struct {
     int64_t tiles;
     double tune_ms[8];     /* measured candidates (tile_rounds x order), 0 if not run */
 } wob_batch_info;
+
+/*
+ * One-shot batched solve: P double-layer problems (Sec. 4.1) in one
+ * persistent launch, with the arguments of wob_batch_create and the seed of
+ * wob_batch_run (schedule from the autotune cache, timed on first use).
+ * Equivalent to wob_batch_create + wob_batch_run + wob_batch_destroy;
+ * synchronises on `stream`.  est / var receive, per problem p, rows
+ * query_offsets[p] .. query_offsets[p+1] - 1.  Results equal P separate
+ * wob_solve calls with the same seed and the problems' own `problem` indices.
+ */
+int wob_solve_batched(const wob_problem *problems, int32_t P, const int64_t *query_offsets,
+                      const float *queries, const int32_t *walks, const int32_t *max_len,
+                      uint64_t seed, double *est, double *var, void *stream);
 
 int wob_batch_create(const wob_problem *problems, int32_t P, const int64_t *query_offsets,
                      const int32_t *walks, const int32_t *max_len, const float *queries,
@@ -499,13 +526,17 @@ int wob_cv_train(const wob_problem *prob, wob_cv c, const wob_cv_train_params *t
  * calls this instead.  The per-walk values live in a fixed array inside the
  * library (2^20 doubles = 8 MiB, held on every GPU that loads the library's
  * device code until exit), so:
- *   - Q * walks must be <= 2^20 (else WOB_ERR_INVALID_ARG, nothing launched);
+ *   - Q * ceil(walks / 32) must be <= 2^19 (the array holds a sum and a sum
+ *     of squares per query and block of 32 walks; else WOB_ERR_INVALID_ARG,
+ *     nothing launched);
  *   - no cudaMalloc, cudaFree or other allocating routine is called;
  *   - all calls share that array: calls that overlap on the GPU (other
  *     streams or host threads) race; serialise them;
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after a cudaDeviceReset (or any other end of the device's
+ *     primary context) it is stale, so do not call this entry point again.
  * Arguments, outputs and results are those of wob_solve (bit-identical).
  */
 int wob_solve_noalloc(const wob_problem *prob, const float *queries, const int32_t *query_prim,

@@ -23,6 +23,7 @@ __all__ = [
     "BC_NEUMANN", "BC_ROBIN", "DATA_VERTEX_P1", "DATA_POLY", "DATA_POINT",
     "WobError", "Mesh", "BVH", "Problem", "Batch", "build_mesh", "build_bvh", "solve", "solve_range",
     "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "solve_density",
+    "solve_batched", "get_stats",
     "mlp_num_params", "mlp_forward", "mlp_train_step", "ControlVariate", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
@@ -81,7 +82,8 @@ class _BatchInfo(ctypes.Structure):
 
 class _DebugOut(ctypes.Structure):
     _fields_ = [("per_walk", ctypes.c_void_p), ("walk_flag", ctypes.c_void_p),
-                ("line_m", ctypes.c_void_p)]
+                ("line_m", ctypes.c_void_p), ("line_prim", ctypes.c_void_p),
+                ("line_flag", ctypes.c_void_p)]
 
 
 class _CvTrainParams(ctypes.Structure):
@@ -171,6 +173,8 @@ def load_library() -> ctypes.CDLL:
             "wob_batch_create": ([P, I32, P, P, P, P, P, P, ctypes.POINTER(_BatchParams), P,
                                   ctypes.POINTER(P)], ctypes.c_int),
             "wob_batch_run": ([P, U64, P], ctypes.c_int),
+            "wob_solve_batched": ([P, I32, P, P, P, P, U64, P, P, P], ctypes.c_int),
+            "wob_get_stats": ([ctypes.POINTER(_Stats)], ctypes.c_int),
             "wob_batch_get_info": ([P, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
             "wob_batch_destroy": ([P], None),
             "wob_line_axes": ([U64, U32, P, I64, P, P], ctypes.c_int),
@@ -380,6 +384,37 @@ class Batch:
         if h and _lib is not None:
             _lib.wob_batch_destroy(h)
             self._h = None
+
+
+def solve_batched(problems, queries, walks, max_len, seed: int = 0, stream=None):
+    """wob_solve_batched: one-shot batched solve of double-layer problems;
+    `queries` a list of per-problem (Q_p, 3) arrays, walks / max_len ints or
+    per-problem lists.  Returns (est, var) per problem as numpy arrays."""
+    import torch
+    P = len(problems)
+    qs = [np.asarray(q, np.float32).reshape(-1, 3) for q in queries]
+    off = np.zeros(P + 1, np.int64)
+    off[1:] = np.cumsum([len(q) for q in qs])
+    qd = _dev(np.concatenate(qs, 0) if P else np.zeros((0, 3), np.float32), torch.float32)
+    est = torch.empty(int(off[-1]), dtype=torch.float64, device="cuda")
+    var = torch.empty_like(est)
+    probs = (_Problem * P)(*[p._c() for p in problems])
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(walks, np.int32), (P,)))
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(max_len, np.int32), (P,)))
+    _check(load_library().wob_solve_batched(probs, P, off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(qd), w.ctypes.data_as(ctypes.c_void_p),
+                                            m.ctypes.data_as(ctypes.c_void_p), seed, _ptr(est),
+                                            _ptr(var), _stream(stream)))
+    e, v = est.cpu().numpy(), var.cpu().numpy()
+    return [(e[off[i]:off[i + 1]], v[off[i]:off[i + 1]]) for i in range(P)]
+
+
+def get_stats() -> dict:
+    """wob_get_stats: counters of this thread's last wob_solve_counted call."""
+    st = _Stats()
+    _check(load_library().wob_get_stats(ctypes.byref(st)))
+    return dict(lines=st.lines, node_visits=st.node_visits, tri_tests=st.tri_tests, hits=st.hits,
+                flagged=st.flagged)
 
 
 def solve(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
@@ -639,7 +674,9 @@ def solve_range(problem: Problem, queries, walk_begin: int, walks: int, max_len:
 
 def solve_debug(problem: Problem, queries, walks: int, max_len: int, seed: int = 0,
                 query_prim=None, want_lines: bool = True, stream=None) -> dict:
-    """wob_solve_debug: est, var and per-walk values, flags and hit counts."""
+    """wob_solve_debug: est, var and per-walk values and flags; with
+    want_lines also per line the hit count line_m, the picked triangle
+    line_prim and the near-degenerate flag line_flag (Q, walks, max_len)."""
     import torch
     q = _dev(queries, torch.float32).reshape(-1, 3)
     qp = None if query_prim is None else _dev(query_prim, torch.int32)
@@ -649,9 +686,13 @@ def solve_debug(problem: Problem, queries, walks: int, max_len: int, seed: int =
                per_walk=torch.empty((Q, walks), dtype=torch.float64, device="cuda"),
                flag=torch.zeros((Q, walks), dtype=torch.uint8, device="cuda"))
     if want_lines:
-        out["line_m"] = torch.empty((Q, walks, max_len), dtype=torch.int32, device="cuda")
+        shape = (Q, walks, max_len)
+        out["line_m"] = torch.empty(shape, dtype=torch.int32, device="cuda")
+        out["line_prim"] = torch.empty(shape, dtype=torch.int32, device="cuda")
+        out["line_flag"] = torch.zeros(shape, dtype=torch.uint8, device="cuda")
     dbg = _DebugOut(out["per_walk"].data_ptr(), out["flag"].data_ptr(),
-                    out["line_m"].data_ptr() if want_lines else None)
+                    *((out["line_m"].data_ptr(), out["line_prim"].data_ptr(),
+                       out["line_flag"].data_ptr()) if want_lines else (None, None, None)))
     pc = problem._c()
     _check(load_library().wob_solve_debug(ctypes.byref(pc), _ptr(q), _ptr(qp), Q, walks, max_len,
                                           seed, _ptr(out["est"]), _ptr(out["var"]),

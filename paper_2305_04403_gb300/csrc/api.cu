@@ -16,6 +16,7 @@ namespace wob {
 
 namespace {
 thread_local std::string g_error;
+thread_local wob_stats g_last_stats = {0, 0, 0, 0, 0};  // of the last counted solve
 }
 
 void set_error(const char* fmt, ...)
@@ -145,17 +146,18 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     p.Q = Q;
     p.N = walks;
     p.M = max_len;
+    p.tpq = (walks + 31) / 32;
     p.walk_begin = walk_begin;
     p.q_base = 0;
     const float tau = prob->tau > 0.0f ? prob->tau : kDefaultTau;
     p.tauL = (float)(tau * m.L);
-    p.edge_thr_L = (float)(tau * m.L * m.max_edge);
+    p.edge_thr_L = (float)((double)kRareMargin * kFlagMargin * tau * m.L * m.max_edge);
     p.graze = kGraze;
 }
 
 namespace {
 
-// Run the walks of one problem into per_walk (device, Q x walks).
+// Run the walks of one problem into the partials p.part (and p.per_walk, if set).
 int run_walks(WalkParams& p, const wob_debug_out* dbg, bool counted, cudaStream_t s,
               int* err_dev)
 {
@@ -163,6 +165,8 @@ int run_walks(WalkParams& p, const wob_debug_out* dbg, bool counted, cudaStream_
     if (dbg) {
         p.walk_flag = dbg->walk_flag;
         p.line_m = dbg->line_m;
+        p.line_prim = dbg->line_prim;
+        p.line_flag = dbg->line_flag;
     }
     if (p.kind == WOB_DIRICHLET_DL) return launch_dl_walks(p, counted, dbg != nullptr, s);
     if (p.kind == WOB_NEUMANN_DIRECT) return launch_nd_walks(p, dbg != nullptr, s);
@@ -177,7 +181,7 @@ struct Control {
 };
 
 struct Scratch {
-    double* per_walk = nullptr;
+    double* per_walk = nullptr;  // per-walk values or (sum, sum of squares) partials
     Control* err = nullptr;
     unsigned long long* counters = nullptr;
     cudaStream_t s = nullptr;
@@ -215,11 +219,12 @@ int solve_common(const wob_problem* prob, const float* queries, const int32_t* q
     fill_params(p, prob, queries, query_prim, Q, walk_begin, walks, max_len, seed);
     Scratch sc;
     sc.s = s;
-    double* per_walk = dbg && dbg->per_walk ? dbg->per_walk : nullptr;
-    if (!per_walk) {
-        WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.per_walk, Q * walks * sizeof(double), s));
-        per_walk = sc.per_walk;
-    }
+    // (sum, sum of squares) per query and block of 32 walks
+    const size_t part_bytes = (size_t)Q * p.tpq * 2 * sizeof(double);
+    WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.per_walk, part_bytes, s));
+    WOB_CUDA_TRY(cudaMemsetAsync(sc.per_walk, 0, part_bytes, s));
+    p.part = sc.per_walk;
+    p.per_walk = dbg ? dbg->per_walk : nullptr;
     WOB_CUDA_TRY(cudaMallocAsync((void**)&sc.err, sizeof(Control), s));
     WOB_CUDA_TRY(cudaMemsetAsync(sc.err, 0, sizeof(Control), s));
     p.tile_counter = &sc.err->next_tile;
@@ -228,10 +233,8 @@ int solve_common(const wob_problem* prob, const float* queries, const int32_t* q
         WOB_CUDA_TRY(cudaMemsetAsync(sc.counters, 0, 5 * sizeof(unsigned long long), s));
         p.counters = sc.counters;
     }
-    p.per_walk = per_walk;
     WOB_TRY(run_walks(p, dbg, stats != nullptr, s, &sc.err->err));
-    if (est) WOB_TRY(launch_reduce(per_walk, Q, walks, est, var, s, &sc.err->err));
-    if (sum) WOB_TRY(launch_reduce_accum(per_walk, Q, walks, sum, sumsq, s, &sc.err->err));
+    WOB_TRY(launch_reduce_part(p.part, Q, walks, p.tpq, est, var, sum, sumsq, s, &sc.err->err));
     if (stats) {
         unsigned long long h[5];
         int herr = 0;
@@ -522,8 +525,21 @@ int wob_solve_counted(const wob_problem* prob, const float* queries, const int32
         return WOB_ERR_INVALID_ARG;
     }
     memset(stats, 0, sizeof(*stats));
-    return solve_common(prob, queries, query_prim, Q, 0, walks, max_len, seed, est, var,
-                        nullptr, nullptr, nullptr, stats, (cudaStream_t)stream);
+    const int rc = solve_common(prob, queries, query_prim, Q, 0, walks, max_len, seed, est, var,
+                                nullptr, nullptr, nullptr, stats, (cudaStream_t)stream);
+    if (rc == WOB_OK) wob::g_last_stats = *stats;
+    return rc;
+}
+
+int wob_get_stats(wob_stats* out)
+{
+    clear_error();
+    if (!out) {
+        set_error("wob_get_stats: out is NULL");
+        return WOB_ERR_INVALID_ARG;
+    }
+    *out = wob::g_last_stats;
+    return WOB_OK;
 }
 
 int wob_solve_host(const wob_problem* prob, const float* queries_host,
@@ -592,8 +608,8 @@ int wob_trace_lines(wob_bvh b, const double* origins, const double* dirs,
     WOB_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     int rc = launch_trace_lines(b->d, origins, dirs, exclude, keys, n, (uint32_t)seed ^ problem,
                                 (uint32_t)(seed >> 32), (float)(tu * md.L),
-                                (float)(tu * md.L * md.max_edge), m, sum_s, prim, s, t, y, flag,
-                                err, st);
+                                (float)((double)kRareMargin * kFlagMargin * tu * md.L * md.max_edge),
+                                m, sum_s, prim, s, t, y, flag, err, st);
     int herr = 0;
     cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(err, st);

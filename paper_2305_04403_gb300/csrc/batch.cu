@@ -47,7 +47,7 @@ struct BatchProblem {
     float edge_thr_L;
     float graze;
     int64_t query_base;  // first row of this problem in queries / est / var
-    int64_t walk_base;   // first entry in the per-walk buffer
+    int64_t part_base;   // first (query, 32-walk block) slot of this problem's partials
     int64_t n_walks;     // Q_p * N_p
 };
 
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128, 8)
     k_dl_batched(const BatchProblem* __restrict__ probs, const Tile* __restrict__ tiles,
                  int64_t n_tiles, const float* __restrict__ queries,
                  const uint64_t* __restrict__ seed_dev, unsigned long long* counter,
-                 double* __restrict__ per_walk, int* err_word)
+                 double* __restrict__ part, int* err_word)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t seed = *seed_dev;
@@ -86,26 +86,29 @@ __global__ void __launch_bounds__(128, 8)
 #pragma unroll 1
         for (int r = 0; r < ROUNDS; ++r) {
             const int64_t local = tile.first + r * 32 + lane;
-            if (local < P.n_walks) {
-                const int64_t qi = local / P.N;
-                const uint32_t w = (uint32_t)(local - qi * P.N);
+            const bool live = local < P.n_walks;
+            const int64_t qi = live ? local / P.N : 0;
+            const int64_t w = local - qi * P.N;
+            double v = 0.0;
+            if (live) {
                 const float* qp = queries + 3 * (P.query_base + qi);
                 const double3 x = make_double3(qp[0], qp[1], qp[2]);
                 int wflag = 0;
-                per_walk[P.walk_base + local] =
-                    dl_walk<false, false>(G, P.data, (double)P.phi, P.M, key, (uint32_t)qi, w, x,
-                                          -1, ws, stack, hits, err, wflag, nullptr, c, lq);
+                v = dl_walk<false, false>(G, P.data, (double)P.phi, P.M, key, (uint32_t)qi,
+                                          (uint32_t)w, x, -1, ws, stack, hits, err, wflag,
+                                          LineOut{nullptr, nullptr, nullptr}, c, lq);
             }
+            add_tile_partials(v, live, qi, w, (P.N + 31) / 32, part + 2 * P.part_base);
         }
     }
     if (err) atomicOr(err_word, err);
 }
 
-// One warp per query: find the query's problem, then mean and variance of
-// its walks in a fixed order (as k_reduce).
-__global__ void k_reduce_batched(const double* __restrict__ per_walk,
+// One warp per query: find the query's problem, then mean and variance from
+// the partials of its 32-walk blocks in a fixed order.
+__global__ void k_reduce_batched(const double* __restrict__ part,
                                  const int64_t* __restrict__ qoff,
-                                 const int64_t* __restrict__ walk_base,
+                                 const int64_t* __restrict__ part_base,
                                  const int32_t* __restrict__ walks, int32_t P, int64_t Qt,
                                  double* __restrict__ est, double* __restrict__ var,
                                  const int* __restrict__ err)
@@ -121,21 +124,24 @@ __global__ void k_reduce_batched(const double* __restrict__ per_walk,
             if (qoff[mid] <= gq) lo = mid; else hi = mid - 1;
         }
         const int N = walks[lo];
-        const double* v = per_walk + walk_base[lo] + (gq - qoff[lo]) * N;
-        double s = 0.0;
-        for (int i = lane; i < N; i += 32) s += v[i];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        const double mean = s / N;
-        double ss = 0.0;
-        for (int i = lane; i < N; i += 32) {
-            const double e = v[i] - mean;
-            ss = fma(e, e, ss);
+        const int tpq = (N + 31) / 32;
+        const double2* v =
+            reinterpret_cast<const double2*>(part) + part_base[lo] + (gq - qoff[lo]) * tpq;
+        double s = 0.0, ss = 0.0;
+        for (int i = lane; i < tpq; i += 32) {
+            const double2 x = v[i];
+            s += x.x;
+            ss += x.y;
         }
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(kFull, s, o);
+            ss += __shfl_xor_sync(kFull, ss, o);
+        }
         if (lane == 0) {
+            const double mean = s / N;
             est[gq] = bad ? __longlong_as_double(0x7FF8000000000000ll) : mean;
             var[gq] = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                          : (N > 1 ? ss / (N - 1) : 0.0);
+                          : (N > 1 ? fmax(ss - s * mean, 0.0) / (N - 1) : 0.0);
         }
     }
 }
@@ -209,16 +215,17 @@ using namespace wob;
 struct wob_batch_s {
     int32_t P = 0;
     int64_t Qt = 0, W = 0, max_lines = 0;
+    int64_t n_slots = 0;  // (query, 32-walk block) slots of all problems
     std::vector<BatchProblem> host_probs;
     std::vector<int32_t> walks;
-    std::vector<int64_t> qoff, walk_base;
+    std::vector<int64_t> qoff, part_base;
     BatchProblem* probs = nullptr;
     Tile* tiles = nullptr;
     int64_t n_tiles = 0;
     int64_t* qoff_dev = nullptr;
-    int64_t* walk_base_dev = nullptr;
+    int64_t* part_base_dev = nullptr;
     int32_t* walks_dev = nullptr;
-    double* per_walk = nullptr;
+    double* part = nullptr;  // (sum, sum of squares) per slot
     unsigned long long* counter = nullptr;
     uint64_t* seed_dev = nullptr;
     int* err = nullptr;
@@ -259,17 +266,19 @@ int batch_grid(int rounds, int64_t n_tiles)
 
 // Counter reset + walk kernel (no API call here may break stream capture).
 int launch_batch_kernels(wob_batch_s& b, const BatchProblem* probs, const Tile* tiles,
-                         int64_t n_tiles, int rounds, int grid, double* per_walk, cudaStream_t s)
+                         int64_t n_tiles, int rounds, int grid, double* part, int64_t n_slots,
+                         cudaStream_t s)
 {
     WOB_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(unsigned long long), s));
     WOB_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int), s));  // this run's checks
+    WOB_CUDA_TRY(cudaMemsetAsync(part, 0, n_slots * 2 * sizeof(double), s));  // added into
     const int threads = 128;
     if (rounds == 4)
-        k_dl_batched<4><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, per_walk, b.err);
+        k_dl_batched<4><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, part, b.err);
     else if (rounds == 2)
-        k_dl_batched<2><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, per_walk, b.err);
+        k_dl_batched<2><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, part, b.err);
     else
-        k_dl_batched<1><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, per_walk, b.err);
+        k_dl_batched<1><<<grid, threads, 0, s>>>(probs, tiles, n_tiles, b.queries, b.seed_dev, b.counter, part, b.err);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
@@ -279,8 +288,8 @@ void free_batch(wob_batch_s* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    for (void* p : {(void*)b->probs, (void*)b->tiles, (void*)b->qoff_dev, (void*)b->walk_base_dev,
-                    (void*)b->walks_dev, (void*)b->per_walk, (void*)b->counter,
+    for (void* p : {(void*)b->probs, (void*)b->tiles, (void*)b->qoff_dev, (void*)b->part_base_dev,
+                    (void*)b->walks_dev, (void*)b->part, (void*)b->counter,
                     (void*)b->seed_dev, (void*)b->err})
         if (p) cudaFree(p);
 }
@@ -296,8 +305,8 @@ int autotune(wob_batch_s& b, const std::vector<double>& cost, cudaStream_t s)
         const int Ns = std::max(32, b.walks[p] / 8);
         small[p].N = std::min(Ns, b.walks[p]);
         small[p].n_walks = (b.qoff[p + 1] - b.qoff[p]) * (int64_t)small[p].N;
-        small[p].walk_base = base;
-        base += small[p].n_walks;
+        small[p].part_base = base;  // fewer walks: at most the full batch's slots
+        base += (b.qoff[p + 1] - b.qoff[p]) * (int64_t)((small[p].N + 31) / 32);
         n_small[p] = small[p].n_walks;
     }
     BatchProblem* dprobs = nullptr;
@@ -322,7 +331,8 @@ int autotune(wob_batch_s& b, const std::vector<double>& cost, cudaStream_t s)
             for (int rep = 0; rep < 2 && rc == WOB_OK; ++rep) {  // first run warms caches
                 cudaEventRecord(e0, s);
                 rc = launch_batch_kernels(b, dprobs, dt, (int64_t)t.size(), rounds_c[ri],
-                                          batch_grid(rounds_c[ri], (int64_t)t.size()), b.per_walk, s);
+                                          batch_grid(rounds_c[ri], (int64_t)t.size()), b.part,
+                                          base, s);
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -369,7 +379,7 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
     b->var = var;
     b->walks.assign(walks, walks + P);
     b->qoff.assign(query_offsets, query_offsets + P + 1);
-    b->walk_base.resize(P + 1);
+    b->part_base.resize(P + 1);
     b->host_probs.resize(P);
     std::vector<double> cost(P);
     std::vector<int64_t> n_walks(P);
@@ -405,17 +415,18 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
         bp.edge_thr_L = wp.edge_thr_L;
         bp.graze = wp.graze;
         bp.query_base = query_offsets[p];
-        bp.walk_base = b->W;
+        bp.part_base = b->n_slots;
         bp.n_walks = Qp * walks[p];
         n_walks[p] = bp.n_walks;
-        b->walk_base[p] = b->W;
+        b->part_base[p] = b->n_slots;
+        b->n_slots += Qp * (int64_t)((walks[p] + 31) / 32);
         b->W += bp.n_walks;
         b->max_lines += bp.n_walks * max_len[p];
         const double T = (double)pr->bvh->d.mesh->T;
         tris += T;
         cost[p] = max_len[p] * std::log2(T + 1.0);
     }
-    b->walk_base[P] = b->W;
+    b->part_base[P] = b->n_slots;
     b->Qt = query_offsets[P];
     if (rc == WOB_OK && b->Qt > 0 && (!queries || !est || !var)) {
         set_error("queries/est/var is NULL");
@@ -430,9 +441,9 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
     if (rc != WOB_OK) return fail(rc);
     if (cudaMalloc((void**)&b->probs, P * sizeof(BatchProblem)) != cudaSuccess ||
         cudaMalloc((void**)&b->qoff_dev, (P + 1) * sizeof(int64_t)) != cudaSuccess ||
-        cudaMalloc((void**)&b->walk_base_dev, (P + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc((void**)&b->part_base_dev, (P + 1) * sizeof(int64_t)) != cudaSuccess ||
         cudaMalloc((void**)&b->walks_dev, P * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc((void**)&b->per_walk, std::max<int64_t>(b->W, 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&b->part, std::max<int64_t>(b->n_slots, 1) * 2 * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&b->counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void**)&b->seed_dev, sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc((void**)&b->err, sizeof(int)) != cudaSuccess) {
@@ -441,7 +452,7 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
     }
     cudaMemcpy(b->probs, b->host_probs.data(), P * sizeof(BatchProblem), cudaMemcpyHostToDevice);
     cudaMemcpy(b->qoff_dev, b->qoff.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(b->walk_base_dev, b->walk_base.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->part_base_dev, b->part_base.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     cudaMemcpy(b->walks_dev, b->walks.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
     cudaMemset(b->err, 0, sizeof(int));
     cudaMemset(b->seed_dev, 0, sizeof(uint64_t));
@@ -495,11 +506,11 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
     const int g_walk = batch_grid(b->rounds, b->n_tiles);
     const int g_red = grid_for((const void*)k_reduce_batched, 256, 0, b->Qt * 32);
     cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
-    rc = launch_batch_kernels(*b, b->probs, b->tiles, b->n_tiles, b->rounds, g_walk, b->per_walk,
-                              b->cap_stream);
+    rc = launch_batch_kernels(*b, b->probs, b->tiles, b->n_tiles, b->rounds, g_walk, b->part,
+                              b->n_slots, b->cap_stream);
     if (rc == WOB_OK && b->Qt > 0)
-        k_reduce_batched<<<g_red, 256, 0, b->cap_stream>>>(b->per_walk, b->qoff_dev,
-                                                           b->walk_base_dev, b->walks_dev, P,
+        k_reduce_batched<<<g_red, 256, 0, b->cap_stream>>>(b->part, b->qoff_dev,
+                                                           b->part_base_dev, b->walks_dev, P,
                                                            b->Qt, est, var, b->err);
     const cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &b->graph);
     if (rc != WOB_OK || ce != cudaSuccess ||
@@ -513,6 +524,24 @@ int wob_batch_create(const wob_problem* problems, int32_t P, const int64_t* quer
     }
     *out = b;
     return WOB_OK;
+}
+
+int wob_solve_batched(const wob_problem* problems, int32_t P, const int64_t* query_offsets,
+                      const float* queries, const int32_t* walks, const int32_t* max_len,
+                      uint64_t seed, double* est, double* var, void* stream)
+{
+    wob_batch b = nullptr;
+    int rc = wob_batch_create(problems, P, query_offsets, walks, max_len, queries, est, var,
+                              nullptr, stream, &b);
+    if (rc != WOB_OK) return rc;
+    rc = wob_batch_run(b, seed, stream);
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    wob_batch_destroy(b);
+    if (rc == WOB_OK && e != cudaSuccess) {
+        set_error("wob_solve_batched: %s", cudaGetErrorString(e));
+        rc = WOB_ERR_CUDA;
+    }
+    return rc;
 }
 
 int wob_batch_run(wob_batch b, uint64_t seed, void* stream)

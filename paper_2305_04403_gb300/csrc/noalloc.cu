@@ -1,15 +1,16 @@
 // noalloc.cu -- wob_solve_noalloc: the same solve as wob_solve, for callers
 // that cannot allocate device memory.
 //
-// wob_solve keeps one FP64 value per walk in scratch memory that it
+// wob_solve keeps per-query partial sums of the walk values (a sum and a sum
+// of squares per block of 32 walks of a query) in scratch memory that it
 // allocates on the stream for every call.  Some callers cannot let a library
 // do that: an application or framework that has already reserved the GPU's
 // memory for its own allocator (a library cudaMalloc would fail, or eat into
 // memory the caller has promised elsewhere), or a latency-critical loop in
 // which a cudaMalloc / cudaFree and the synchronisation it may imply are not
-// acceptable.  This entry point keeps the per-walk values in a fixed-size
-// array compiled into the library instead (kNoAllocMaxWalkValues doubles,
-// 8 MiB); it calls no cudaMalloc, cudaFree or other allocating routine.
+// acceptable.  This entry point keeps the partial sums in a fixed-size array
+// compiled into the library instead (kNoAllocScratch doubles, 8 MiB); it
+// calls no cudaMalloc, cudaFree or other allocating routine.
 //
 // Costs and rules of that choice:
 //  * every GPU on which the library's device code is loaded holds the 8 MiB
@@ -17,11 +18,15 @@
 //  * all calls share the one array per device, so calls whose work overlaps
 //    on the GPU (different streams, or different host threads) race: order
 //    them on one stream or synchronise between them;
-//  * Q * walks must not exceed kNoAllocMaxWalkValues (checked, rejected with
+//  * Q * ceil(walks / 32) must not exceed kNoAllocScratch / 2 = 2^19 (two
+//    doubles per query and block of 32 walks; checked, rejected with
 //    WOB_ERR_INVALID_ARG before any GPU work);
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (a host-side name of a __device__ variable is not
 //    a device pointer); make that first call before any stream capture.
+//    The address is cached per device for the life of the process: a
+//    cudaDeviceReset (or any other end of the device's primary context)
+//    invalidates it, so do not call this entry point after one.
 #include <mutex>
 
 #include "wob_host.h"
@@ -30,11 +35,11 @@ namespace wob {
 
 namespace {
 
-constexpr int64_t kNoAllocMaxWalkValues = int64_t(1) << 20;  // 8 MiB of doubles
+constexpr int64_t kNoAllocScratch = int64_t(1) << 20;  // 8 MiB of doubles
 constexpr int kMaxDevices = 64;
 
-// Per-walk values of the most recent call; check word and walk-tile counter.
-static __device__ __align__(256) double g_walk_values[kNoAllocMaxWalkValues];
+// Walk-value partial sums of the most recent call; check word and walk-tile counter.
+static __device__ __align__(256) double g_walk_values[kNoAllocScratch];
 static __device__ __align__(256) int g_check_word[64];
 
 std::mutex g_setup_mutex;
@@ -80,10 +85,11 @@ extern "C" int wob_solve_noalloc(const wob_problem* prob, const float* queries,
         set_error("queries/est/var is NULL");
         return WOB_ERR_INVALID_ARG;
     }
-    if (Q * (int64_t)walks > kNoAllocMaxWalkValues) {
-        set_error("wob_solve_noalloc: Q * walks = %lld exceeds the fixed scratch of %lld walk "
-                  "values; split the queries or use wob_solve",
-                  (long long)(Q * (int64_t)walks), (long long)kNoAllocMaxWalkValues);
+    const int64_t blocks = Q * (int64_t)((walks + 31) / 32);
+    if (2 * blocks > kNoAllocScratch) {
+        set_error("wob_solve_noalloc: Q * ceil(walks / 32) = %lld exceeds the fixed scratch of "
+                  "%lld blocks of 32 walks; split the queries or use wob_solve",
+                  (long long)blocks, (long long)(kNoAllocScratch / 2));
         return WOB_ERR_INVALID_ARG;
     }
     if (prob->kind == WOB_DIRICHLET_DL && query_prim) {
@@ -102,15 +108,16 @@ extern "C" int wob_solve_noalloc(const wob_problem* prob, const float* queries,
     cudaStream_t s = (cudaStream_t)stream;
     WalkParams p;
     fill_params(p, prob, queries, query_prim, Q, 0, walks, max_len, seed);
-    p.per_walk = values;  // every entry is written by the walk kernel
+    p.part = values;  // the walk kernels add into it: cleared below
     p.error_word = check;                                                   // check[0]
     p.tile_counter = reinterpret_cast<unsigned long long*>(check + 2);      // check[2..3]
     WOB_CUDA_TRY(cudaMemsetAsync(check, 0, 4 * sizeof(int), s));  // both must start at zero
+    WOB_CUDA_TRY(cudaMemsetAsync(values, 0, 2 * blocks * sizeof(double), s));
     if (p.kind == WOB_DIRICHLET_DL)
         WOB_TRY(launch_dl_walks(p, false, false, s));
     else if (p.kind == WOB_NEUMANN_DIRECT)
         WOB_TRY(launch_nd_walks(p, false, s));
     else
         WOB_TRY(launch_sl_walks(p, false, s));
-    return launch_reduce(values, Q, walks, est, var, s, check);
+    return launch_reduce_part(values, Q, walks, p.tpq, est, var, nullptr, nullptr, s, check);
 }

@@ -7,9 +7,11 @@
 // plus the debug kernels behind wob_trace_lines / wob_line_axes /
 // wob_philox4x32_10.
 //
-// One thread owns one walk from start to end; a walk's value is written to
-// per_walk[q * N + w] and reduced per query in a fixed order, so results do
-// not depend on scheduling.
+// One thread owns one walk from start to end; the walk values of a warp's 32
+// walks are summed per query in a fixed order into (sum, sum of squares)
+// partials (add_tile_partials), which k_reduce_part combines per query in a
+// fixed order, so results do not depend on scheduling.  Debug solves also
+// write every walk's value.
 #include <cmath>
 #include <cstdlib>
 
@@ -59,27 +61,36 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_dl_walks(WalkParams 
         tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
         if ((int64_t)tile * 32 >= total) break;
         const int64_t idx = (int64_t)tile * 32 + lane;
-        if (idx >= total) continue;
-        const int64_t qi = idx / p.N;
-        const uint32_t q = p.q_base + (uint32_t)qi;
-        const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
-        const double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
-        int wflag = 0;
-        int start = -1;
-        if (p.query_prim) {  // density walks from boundary points
-            const int32_t prim = p.query_prim[qi];
-            start = (prim >= 0 && prim < p.T) ? p.inv_order[prim] : -1;
+        const bool live = idx < total;
+        const int64_t qi = live ? idx / p.N : 0;
+        const int64_t wi = idx - qi * p.N;
+        double v = 0.0;
+        if (live) {
+            const uint32_t q = p.q_base + (uint32_t)qi;
+            const uint32_t w = (uint32_t)(p.walk_begin + wi);
+            const double3 x =
+                make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+            int wflag = 0;
+            int start = -1;
+            if (p.query_prim) {  // density walks from boundary points
+                const int32_t prim = p.query_prim[qi];
+                start = (prim >= 0 && prim < p.T) ? p.inv_order[prim] : -1;
+            }
+            const int64_t lk = idx * p.M;
+            const LineOut lo{DEBUG && p.line_m ? p.line_m + lk : nullptr,
+                             DEBUG && p.line_prim ? p.line_prim + lk : nullptr,
+                             DEBUG && p.line_flag ? p.line_flag + lk : nullptr};
+            v = dl_walk<COUNT, DEBUG, GRAD, GRAD>(G, p.data, (double)p.phi, p.M, key, q, w, x,
+                                                  start, ws, stack, hits, err, wflag, lo, c, lq);
+            if (p.per_walk) p.per_walk[idx] = v;
+            if (GRAD) {  // gradient of the same walk: first-step factor x walk value
+                p.per_walk_grad[idx] = ws.get(8) * v;
+                p.per_walk_grad[total + idx] = ws.get(9) * v;
+                p.per_walk_grad[2 * total + idx] = ws.get(10) * v;
+            }
+            if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
         }
-        const double v = dl_walk<COUNT, DEBUG, GRAD, GRAD>(
-            G, p.data, (double)p.phi, p.M, key, q, w, x, start, ws, stack, hits, err, wflag,
-            DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr, c, lq);
-        p.per_walk[idx] = v;
-        if (GRAD) {  // gradient of the same walk: first-step factor x walk value
-            p.per_walk_grad[idx] = ws.get(8) * v;
-            p.per_walk_grad[total + idx] = ws.get(9) * v;
-            p.per_walk_grad[2 * total + idx] = ws.get(10) * v;
-        }
-        if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
+        if (p.part) add_tile_partials(v, live, qi, wi, p.tpq, p.part);
     }
     if (err) atomicOr(p.error_word, err);
     if (COUNT) {
@@ -254,73 +265,82 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
     const double rmin = 1e-12 * p.L;
     const int uniform_bc = p.kind == WOB_ROBIN_SL ? WOB_BC_ROBIN : WOB_BC_NEUMANN;
     double wc[kMaxRis];
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = idx / p.N;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform loop over groups of 32 consecutive walks
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = base + lane;
+        const bool live = idx < total;
+        const int64_t qi = live ? idx / p.N : 0;
         const int64_t wi = idx - qi * p.N;
-        const uint32_t q = p.q_base + (uint32_t)qi;
-        const uint32_t w = (uint32_t)(p.walk_begin + wi);
-        double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
-        double3 nx = make_double3(0.0, 0.0, 0.0);
-        int bx = -1;
-        int64_t jx = -1;
-        double S = 0.0, P = 1.0, W0 = 0.0;
-        for (int k = 0; k < p.M; ++k) {
-            bool stay = false;
-            if (bx == WOB_BC_DIRICHLET) {
-                const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeBranch, 0u, 0u);
-                stay = u24(u.x) >= (double)p.pk;
-            }
-            AreaPoint a;
-            double wfac;
-            if (stay) {
-                a.j = jx;
-                a.y = x;
-                a.n = nx;
-                a.b0 = a.b1 = a.b2 = 0.0;  // mixed problems take analytic data
-                wfac = 1.0 / (1.0 - (double)p.pk);
-            } else if (p.ris <= 1) {
-                a = area_point(p, key, q, w, (uint32_t)k);
-                const double3 r = make_double3(a.y.x - x.x, a.y.y - x.y, a.y.z - x.z);
-                const double r2 = r.x * r.x + r.y * r.y + r.z * r.z;
-                if (r2 < rmin * rmin) break;  // empty sample
-                wfac = area * sl_kernel32(p, bx, r, r2, nx);
-            } else {
-                double sumw = 0.0;
-                for (int c = 0; c < p.ris; ++c) {
-                    const AreaPoint ac = area_point(p, key, q, w, (uint32_t)k, (uint32_t)c);
-                    wc[c] = fabs(sl_kernel(p, bx, x, nx, ac.y, rmin));
-                    sumw += wc[c];
+        double value = 0.0;
+        if (live) {
+            const uint32_t q = p.q_base + (uint32_t)qi;
+            const uint32_t w = (uint32_t)(p.walk_begin + wi);
+            double3 x = make_double3(p.queries[3 * qi], p.queries[3 * qi + 1], p.queries[3 * qi + 2]);
+            double3 nx = make_double3(0.0, 0.0, 0.0);
+            int bx = -1;
+            int64_t jx = -1;
+            double S = 0.0, P = 1.0, W0 = 0.0;
+            for (int k = 0; k < p.M; ++k) {
+                bool stay = false;
+                if (bx == WOB_BC_DIRICHLET) {
+                    const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeBranch, 0u, 0u);
+                    stay = u24(u.x) >= (double)p.pk;
                 }
-                if (!(sumw > 0.0)) break;  // every candidate has a zero kernel
-                const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeRis, 0u, 0u);
-                const double target = u53(u.x, u.y) * sumw;
-                double acc = 0.0;
-                int pick = p.ris - 1;
-                for (int c = 0; c < p.ris; ++c) {
-                    acc += wc[c];
-                    if (acc > target) {
-                        pick = c;
-                        break;
+                AreaPoint a;
+                double wfac;
+                if (stay) {
+                    a.j = jx;
+                    a.y = x;
+                    a.n = nx;
+                    a.b0 = a.b1 = a.b2 = 0.0;  // mixed problems take analytic data
+                    wfac = 1.0 / (1.0 - (double)p.pk);
+                } else if (p.ris <= 1) {
+                    a = area_point(p, key, q, w, (uint32_t)k);
+                    const double3 r = make_double3(a.y.x - x.x, a.y.y - x.y, a.y.z - x.z);
+                    const double r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                    if (r2 < rmin * rmin) break;  // empty sample
+                    wfac = area * sl_kernel32(p, bx, r, r2, nx);
+                } else {
+                    double sumw = 0.0;
+                    for (int c = 0; c < p.ris; ++c) {
+                        const AreaPoint ac = area_point(p, key, q, w, (uint32_t)k, (uint32_t)c);
+                        wc[c] = fabs(sl_kernel(p, bx, x, nx, ac.y, rmin));
+                        sumw += wc[c];
                     }
+                    if (!(sumw > 0.0)) break;  // every candidate has a zero kernel
+                    const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeRis, 0u, 0u);
+                    const double target = u53(u.x, u.y) * sumw;
+                    double acc = 0.0;
+                    int pick = p.ris - 1;
+                    for (int c = 0; c < p.ris; ++c) {
+                        acc += wc[c];
+                        if (acc > target) {
+                            pick = c;
+                            break;
+                        }
+                    }
+                    a = area_point(p, key, q, w, (uint32_t)k, (uint32_t)pick);
+                    const double K = sl_kernel(p, bx, x, nx, a.y, rmin);
+                    wfac = (K > 0.0 ? 1.0 : -1.0) * area * sumw / (double)p.ris;
                 }
-                a = area_point(p, key, q, w, (uint32_t)k, (uint32_t)pick);
-                const double K = sl_kernel(p, bx, x, nx, a.y, rmin);
-                wfac = (K > 0.0 ? 1.0 : -1.0) * area * sumw / (double)p.ris;
+                if (k == 0) W0 = wfac; else P *= wfac;
+                const int by = p.bc_type ? (int)__ldg(p.bc_type + a.j) : uniform_bc;
+                const double dat = sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by);
+                double src = by == WOB_BC_DIRICHLET ? (double)p.kmix * dat : 2.0 * phi * dat;
+                if (k == p.M - 1) src *= 0.5;
+                S = fma(P, src, S);
+                x = a.y;
+                nx = a.n;
+                bx = by;
+                jx = a.j;
             }
-            if (k == 0) W0 = wfac; else P *= wfac;
-            const int by = p.bc_type ? (int)__ldg(p.bc_type + a.j) : uniform_bc;
-            const double dat = sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, by);
-            double src = by == WOB_BC_DIRICHLET ? (double)p.kmix * dat : 2.0 * phi * dat;
-            if (k == p.M - 1) src *= 0.5;
-            S = fma(P, src, S);
-            x = a.y;
-            nx = a.n;
-            bx = by;
-            jx = a.j;
+            value = W0 * S;
+            if (p.per_walk) p.per_walk[idx] = value;
+            if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
         }
-        p.per_walk[idx] = W0 * S;
-        if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
+        if (p.part) add_tile_partials(value, live, qi, wi, p.tpq, p.part);
     }
 }
 
@@ -349,77 +369,92 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
     int err = 0;
     int stack[kStackSize];
     int hits[kMaxHits];
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = idx / p.N;
-        const uint32_t q = p.q_base + (uint32_t)qi;
-        const uint32_t w = (uint32_t)(p.walk_begin + (idx - qi * p.N));
-        ws.set(X0, p.queries[3 * qi]);
-        ws.set(X1, p.queries[3 * qi + 1]);
-        ws.set(X2, p.queries[3 * qi + 2]);
-        ws.set(SS, 0.0);
-        ws.set(PP, 1.0);
-        int32_t* lm = DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr;
-        if (DEBUG && lm)
-            for (int k = 0; k < p.M; ++k) lm[k] = -1;
-        int self = -1, k0 = 0, wflag = 0;
-        if (p.query_prim) {
-            const int32_t prim = p.query_prim[qi];
-            if (prim >= 0 && prim < p.T) {
-                self = p.inv_order[prim];
-                k0 = 1;
-            }
-        }
-        for (int k = k0; k <= p.M; ++k) {
-            // source at vertex k
-            {
-                const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
-                const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
-                const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
-                const double r2 = rx * rx + ry * ry + rz * rz;
-                if (r2 >= rmin * rmin) {
-                    const double f =
-                        sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
-                    double c = (k == 0) ? phi : 2.0 * phi;
-                    if (k == p.M) c *= 0.5;
-                    const double G = (double)(0.0795774715459476678f * rsqrtf((float)r2));
-                    ws.set(SS, fma(ws.get(PP) * c * p.area * G, f, ws.get(SS)));
+    const int lane = threadIdx.x & 31;
+    // warp-uniform loop over groups of 32 consecutive walks
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = base + lane;
+        const bool live = idx < total;
+        const int64_t qi = live ? idx / p.N : 0;
+        const int64_t wi = idx - qi * p.N;
+        double value = 0.0;
+        if (live) {
+            const uint32_t q = p.q_base + (uint32_t)qi;
+            const uint32_t w = (uint32_t)(p.walk_begin + wi);
+            ws.set(X0, p.queries[3 * qi]);
+            ws.set(X1, p.queries[3 * qi + 1]);
+            ws.set(X2, p.queries[3 * qi + 2]);
+            ws.set(SS, 0.0);
+            ws.set(PP, 1.0);
+            const LineOut lo{DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr,
+                             DEBUG && p.line_prim ? p.line_prim + idx * p.M : nullptr,
+                             DEBUG && p.line_flag ? p.line_flag + idx * p.M : nullptr};
+            if (DEBUG)
+                for (int k = 0; k < p.M; ++k) lo.put(k, -1, -1, 0);
+            int self = -1, k0 = 0, wflag = 0;
+            if (p.query_prim) {
+                const int32_t prim = p.query_prim[qi];
+                if (prim >= 0 && prim < p.T) {
+                    self = p.inv_order[prim];
+                    k0 = 1;
                 }
             }
-            if (k == p.M) break;
-            // line from vertex k to vertex k + 1
-            LinePre L;
-            {
-                const double3 d = line_axis(key, q, w, (uint32_t)k);
-                ws.set(D0, d.x);
-                ws.set(D1, d.y);
-                ws.set(D2, d.z);
-                L = line_pre(make_float3((float)ws.get(X0), (float)ws.get(X1), (float)ws.get(X2)),
-                             make_float3((float)d.x, (float)d.y, (float)d.z));
+            for (int k = k0; k <= p.M; ++k) {
+                // source at vertex k
+                {
+                    const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
+                    const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
+                    const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
+                    const double r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 >= rmin * rmin) {
+                        const double f =
+                            sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
+                        double c = (k == 0) ? phi : 2.0 * phi;
+                        if (k == p.M) c *= 0.5;
+                        const double G = (double)(0.0795774715459476678f * rsqrtf((float)r2));
+                        ws.set(SS, fma(ws.get(PP) * c * p.area * G, f, ws.get(SS)));
+                    }
+                }
+                if (k == p.M) break;
+                // line from vertex k to vertex k + 1
+                LinePre L;
+                {
+                    const double3 d = line_axis(key, q, w, (uint32_t)k);
+                    ws.set(D0, d.x);
+                    ws.set(D1, d.y);
+                    ws.set(D2, d.z);
+                    L = line_pre(make_float3((float)ws.get(X0), (float)ws.get(X1), (float)ws.get(X2)),
+                                 make_float3((float)d.x, (float)d.y, (float)d.z));
+                }
+                const float Tthr = p.edge_thr_L * fabsf(L.Sz);
+                Trav t;
+                trav_init(t);
+                uint32_t nn = 0, nt = 0;
+                trace_wide_q<false, false, true>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
+                                           p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn,
+                                           nt, err, p.iter_limit, lq);
+                wflag |= t.flag;
+                if (t.m == 0) {
+                    if (DEBUG) lo.put(k, 0, -1, t.flag);
+                    break;
+                }
+                const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
+                if (DEBUG) lo.put(k, t.m, (int)prim_of(p.tv, pos), t.flag);
+                const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
+                const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
+                const Refined r = refine_hit(p.tv, pos, x, d);
+                const double ms = (double)t.m * (double)r.s;
+                ws.set(PP, ws.get(PP) * ((k == 0) ? 0.5 * phi * ms : phi * ms));
+                ws.set(X0, r.y.x);
+                ws.set(X1, r.y.y);
+                ws.set(X2, r.y.z);
+                self = pos;
             }
-            const float Tthr = p.edge_thr_L * fabsf(L.Sz);
-            Trav t;
-            trav_init(t);
-            uint32_t nn = 0, nt = 0;
-            trace_wide_q<false, false, true>(p.nodes, p.tv, L, make_float3(0.f, 0.f, 0.f), Tthr, p.tauL,
-                                       p.graze, self, t, hits, stack, key, q, w, (uint32_t)k, nn,
-                                       nt, err, p.iter_limit, lq);
-            wflag |= t.flag;
-            if (DEBUG && lm) lm[k] = t.m;
-            if (t.m == 0) break;
-            const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
-            const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
-            const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
-            const Refined r = refine_hit(p.tv, pos, x, d);
-            const double ms = (double)t.m * (double)r.s;
-            ws.set(PP, ws.get(PP) * ((k == 0) ? 0.5 * phi * ms : phi * ms));
-            ws.set(X0, r.y.x);
-            ws.set(X1, r.y.y);
-            ws.set(X2, r.y.z);
-            self = pos;
+            value = ws.get(SS);
+            if (p.per_walk) p.per_walk[idx] = value;
+            if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
         }
-        p.per_walk[idx] = ws.get(SS);
-        if (DEBUG && p.walk_flag) p.walk_flag[idx] = (uint8_t)wflag;
+        if (p.part) add_tile_partials(value, live, qi, wi, p.tpq, p.part);
     }
     if (err) atomicOr(p.error_word, err);
 }
@@ -792,6 +827,45 @@ __global__ void k_reduce_accum(const double* __restrict__ per_walk, int64_t Q, i
     }
 }
 
+// One warp per query from the (sum, sum of squares) partials of its tpq
+// 32-walk blocks: mean and unbiased variance, blocks combined in a fixed
+// order (lane i takes blocks i, i + 32, ..., then a fixed shuffle tree).
+__global__ void k_reduce_part(const double* __restrict__ part, int64_t Q, int32_t N, int32_t tpq,
+                              double* __restrict__ est, double* __restrict__ var,
+                              double* __restrict__ sum, double* __restrict__ sumsq,
+                              const int* __restrict__ err)
+{
+    const bool bad = solve_failed(err);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < Q;
+         q += warps) {
+        const double2* pq = reinterpret_cast<const double2*>(part) + q * tpq;
+        double s = 0.0, ss = 0.0;
+        for (int i = lane; i < tpq; i += 32) {
+            const double2 v = pq[i];
+            s += v.x;
+            ss += v.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+            ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+        }
+        if (lane == 0) {
+            const double nan = __longlong_as_double(0x7FF8000000000000ll);
+            if (est) {
+                const double mean = s / N;
+                est[q] = bad ? nan : mean;
+                var[q] = bad ? nan : (N > 1 ? fmax(ss - s * mean, 0.0) / (N - 1) : 0.0);
+            }
+            if (sum) {
+                sum[q] += bad ? nan : s;
+                sumsq[q] += bad ? nan : ss;
+            }
+        }
+    }
+}
+
 __global__ void k_trace_lines(const float4* __restrict__ nodes, const float4* __restrict__ tv,
                               const int32_t* __restrict__ inv_order, int64_t n_tris,
                               int iter_limit, const double* __restrict__ o,
@@ -979,6 +1053,16 @@ int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, dou
     const int threads = 256;
     k_reduce<<<grid_for((const void*)k_reduce, threads, 0, Q * 32), threads, 0, s>>>(
         per_walk, Q, N, est, var, err);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int launch_reduce_part(const double* part, int64_t Q, int32_t N, int32_t tpq, double* est,
+                       double* var, double* sum, double* sumsq, cudaStream_t s, const int* err)
+{
+    const int threads = 256;
+    k_reduce_part<<<grid_for((const void*)k_reduce_part, threads, 0, Q * 32), threads, 0, s>>>(
+        part, Q, N, tpq, est, var, sum, sumsq, err);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }

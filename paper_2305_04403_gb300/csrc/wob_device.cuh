@@ -204,38 +204,119 @@ __device__ __forceinline__ void keep_min(uint64_t k, uint32_t prim, int pos, uin
     }
 }
 
-// Line-triangle test (Woop, Benthin, Wald, "Watertight ray/triangle
-// intersection", JCGT 2013, applied to a line: no parameter range) of the
-// triangle (a4, b4, c4) in leaf layout: true on a hit (tl = its line
-// parameter); flag = 1 on a near-degenerate configuration.
+// Line-triangle test of the triangle (a4, b4, c4) in leaf layout, applied
+// to a line (no parameter range): true on a hit (tl = its line parameter);
+// flag = 1 on a near-degenerate configuration.
+//
+// The test works in the sheared frame of Woop, Benthin and Wald
+// ("Watertight ray/triangle intersection", JCGT 2013), where the line is the
+// kz axis and each directed edge P -> Q has the edge function
+// f = cross2(Q', P') (twice the signed area of the origin and the projected
+// edge).  A hit is f > 0 on all three edges or f < 0 on all three.
+//
+// Main path: the edge functions are formed from the sheared vertex A' and
+// the sheared WORLD differences b - a and c - a (nearby vertices, so these
+// differences are nearly exact): W = f(A->B) = cross2(eb', A'),
+// V = f(C->A) = cross2(A', ec'), det = U + V + W = cross2(ec', eb') and
+// U = det - V - W.  Their rounding error is of order 2^-24 |A'| |e'| -- a
+// distance of order 2^-24 |A'| from the edge, not 2^-24 |A'|^2 / |e'| as
+// when the edge functions are products of two sheared vertices.
+//
+// Near an edge (some |f| < Trare, a bound above both that rounding error and
+// the flag distance) the three edge functions are recomputed by near_edges
+// in a canonical form, so that two triangles sharing an edge obtain exactly
+// opposite values for it (watertight), and the near-degenerate flag is
+// decided from the true distances of the line to the edges.
+// Sheared coordinates (kx, ky) of a point p relative to the line origin.
+__device__ __forceinline__ float2 shear_rel(const float4& p, const LinePre& L)
+{
+    const float3 r = make_float3(p.x - L.ox, p.y - L.oy, p.z - L.oz);
+    const float rz = comp(r, L.kz);
+    return make_float2(fmaf(-L.Sx, rz, comp(r, L.kx)), fmaf(-L.Sy, rz, comp(r, L.ky)));
+}
+
+// Edge function of the directed edge P -> Q in the canonical form: the world
+// difference e = Q - P sheared to e', then cross2(e', X') at the anchor X,
+// the endpoint whose sheared (x, y) is lexicographically smaller.  Reversing
+// the edge negates e' exactly and keeps the anchor, so the value is exactly
+// negated: the two triangles of an edge agree on the side the line passes.
+// len2 receives |d x e|^2 / d_kz^2, so that f^2 / len2 is the squared
+// distance of the line to the edge's supporting line.
+__device__ __forceinline__ float edge_fn(const float4& P, float2 Pp, const float4& Q, float2 Qp,
+                                         const LinePre& L, float& len2)
+{
+    const float3 e = make_float3(Q.x - P.x, Q.y - P.y, Q.z - P.z);
+    const float ez = comp(e, L.kz);
+    const float ex = fmaf(-L.Sx, ez, comp(e, L.kx)), ey = fmaf(-L.Sy, ez, comp(e, L.ky));
+    const bool anchor_p = Pp.x < Qp.x || (Pp.x == Qp.x && Pp.y < Qp.y);
+    const float2 X = anchor_p ? Pp : Qp;
+    const float c = fmaf(L.Sx, ey, -L.Sy * ex);
+    len2 = fmaf(ex, ex, fmaf(ey, ey, c * c));
+    return __fmaf_rn(ex, X.y, -__fmul_rn(ey, X.x));
+}
+
+// Canonical edge functions and the near-degenerate flag of a line that
+// passes close to an edge of the triangle: (U, V, W, flag).  The flag
+// follows the oracle's definition with the distance kFlagMargin tau L: the
+// line lies within that distance of the triangle (the expanded projection
+// contains it) and within it of an edge.  Not inlined: it runs on a small
+// fraction of the triangle tests, and kept out of line it adds no register
+// pressure to the traversal loop.
+struct EdgeFns {
+    float U, V, W;
+    int flag;
+};
+
+static __device__ __noinline__ EdgeFns near_edges(float4 a4, float4 b4, float4 c4, LinePre L, float tauL)
+{
+    const float2 A = shear_rel(a4, L), B = shear_rel(b4, L), C = shear_rel(c4, L);
+    float lu, lv, lw;
+    EdgeFns r;
+    r.W = edge_fn(a4, A, b4, B, L, lw);
+    r.U = edge_fn(b4, B, c4, C, L, lu);
+    r.V = edge_fn(c4, C, a4, A, L, lv);
+    const float t = kFlagMargin * tauL;
+    const float du = t * sqrtf(lu), dv = t * sqrtf(lv), dw = t * sqrtf(lw);
+    const bool inside = (r.U > -du && r.V > -dv && r.W > -dw) || (r.U < du && r.V < dv && r.W < dw);
+    r.flag = inside && (fabsf(r.U) < du || fabsf(r.V) < dv || fabsf(r.W) < dw);
+    return r;
+}
+
 __device__ __forceinline__ bool line_tri(const float4& a4, const float4& b4, const float4& c4,
-                                         const LinePre& L, float Tthr, float tauL, float graze,
+                                         const LinePre& L, float Trare, float tauL, float graze,
                                          int& flag, float& tl)
 {
     const float3 A = make_float3(a4.x - L.ox, a4.y - L.oy, a4.z - L.oz);
-    const float3 B = make_float3(b4.x - L.ox, b4.y - L.oy, b4.z - L.oz);
-    const float3 C = make_float3(c4.x - L.ox, c4.y - L.oy, c4.z - L.oz);
-    const float Akz = comp(A, L.kz), Bkz = comp(B, L.kz), Ckz = comp(C, L.kz);
+    const float3 eb = make_float3(b4.x - a4.x, b4.y - a4.y, b4.z - a4.z);
+    const float3 ec = make_float3(c4.x - a4.x, c4.y - a4.y, c4.z - a4.z);
+    const float Akz = comp(A, L.kz), bkz = comp(eb, L.kz), ckz = comp(ec, L.kz);
     const float Ax = fmaf(-L.Sx, Akz, comp(A, L.kx));
     const float Ay = fmaf(-L.Sy, Akz, comp(A, L.ky));
-    const float Bx = fmaf(-L.Sx, Bkz, comp(B, L.kx));
-    const float By = fmaf(-L.Sy, Bkz, comp(B, L.ky));
-    const float Cx = fmaf(-L.Sx, Ckz, comp(C, L.kx));
-    const float Cy = fmaf(-L.Sy, Ckz, comp(C, L.ky));
-    const float U = Cx * By - Cy * Bx;
-    const float V = Ax * Cy - Ay * Cx;
-    const float W = Bx * Ay - By * Ax;
-    const bool pos_side = (U > -Tthr) && (V > -Tthr) && (W > -Tthr);
-    const bool neg_side = (U < Tthr) && (V < Tthr) && (W < Tthr);
+    const float bx = fmaf(-L.Sx, bkz, comp(eb, L.kx));
+    const float by = fmaf(-L.Sy, bkz, comp(eb, L.ky));
+    const float cx = fmaf(-L.Sx, ckz, comp(ec, L.kx));
+    const float cy = fmaf(-L.Sy, ckz, comp(ec, L.ky));
+    float W = bx * Ay - by * Ax;  // edge A -> B
+    float V = Ax * cy - Ay * cx;  // edge C -> A
+    float det = cx * by - cy * bx;
+    float U = det - V - W;        // edge B -> C
+    const bool pos_side = (U > -Trare) && (V > -Trare) && (W > -Trare);
+    const bool neg_side = (U < Trare) && (V < Trare) && (W < Trare);
     if (!(pos_side || neg_side)) return false;
-    const float det = U + V + W;
-    const float mn = fminf(fminf(fabsf(U), fabsf(V)), fabsf(W));
-    if (mn < Tthr || fabsf(det) < graze * b4.w * fabsf(L.Sz)) flag = 1;
+    if (fminf(fminf(fabsf(U), fabsf(V)), fabsf(W)) < Trare) {
+        const EdgeFns e = near_edges(a4, b4, c4, L, tauL);
+        U = e.U;
+        V = e.V;
+        W = e.W;
+        flag |= e.flag;
+        det = U + V + W;
+    }
+    if (fabsf(det) < graze * b4.w * fabsf(L.Sz)) flag = 1;
     const bool hit = (U > 0.f && V > 0.f && W > 0.f) || (U < 0.f && V < 0.f && W < 0.f);
     if (!hit) return false;
-    const float T = fmaf(U, L.Sz * Akz, fmaf(V, L.Sz * Bkz, W * (L.Sz * Ckz)));
-    tl = T / det;
-    if (fabsf(tl) < tauL) flag = 1;
+    // kz of the hit relative to the origin: barycentric mix of A, B, C
+    tl = L.Sz * (Akz + fmaf(V, bkz, W * ckz) / det);
+    if (fabsf(tl) < kFlagMargin * tauL) flag = 1;
     return true;
 }
 
@@ -629,11 +710,26 @@ __device__ __forceinline__ double3 grad_factor(const float4* __restrict__ tv, in
                         k * (nz - 3.0 * wn * wz));
 }
 
+// Per-line debug outputs of one walk (each pointer may be NULL): hit count
+// (-1: line not traced), picked triangle (original id, -1: none) and the
+// near-degenerate flag of every line k = 0 .. M-1.
+struct LineOut {
+    int32_t* m;
+    int32_t* prim;
+    uint8_t* flag;
+    __device__ __forceinline__ void put(int k, int mk, int pk, int fk) const
+    {
+        if (m) m[k] = mk;
+        if (prim) prim[k] = pk;
+        if (flag) flag[k] = (uint8_t)fk;
+    }
+};
+
 // One double-layer walk from x (Sec. 4.1.1-4.1.2, ray sampling of Sec.
 // 4.4.1): per line, draw the axis, traverse (descend to a leaf, test it,
 // repeat), pick the hit (keys only when m > 1), refine it in FP64 and
-// accumulate.  Returns the walk value; `line_m` (optional) receives the hit
-// count of each line, -1 for lines not traced.  start_pos >= 0: x0 lies on
+// accumulate.  Returns the walk value; `lo` (DEBUG only) receives the
+// per-line outputs.  start_pos >= 0: x0 lies on
 // that triangle (leaf position) and the walk estimates the density nu(x0)
 // (Eq. indirect_double_boundary_reordered2): x0 is vertex 1 with weight 1
 // and lines 1 .. M-1 follow.  HIT_MASK: the node-test form of trace_wide_q.
@@ -641,7 +737,7 @@ template <bool COUNT, bool DEBUG, bool GRAD = false, bool HIT_MASK = true>
 __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, double phi, int M,
                                           StreamKey key, uint32_t q, uint32_t w, double3 x0,
                                           int start_pos, const WalkSlot& ws, int* stack,
-                                          int* hits, int& err, int& wflag, int32_t* line_m,
+                                          int* hits, int& err, int& wflag, const LineOut& lo,
                                           WalkCount& c, LeafQueue lq)
 {
     enum { X0 = 0, X1, X2, D0, D1, D2, SS, PP, GX, GY, GZ };  // GX..GZ: GRAD only
@@ -661,7 +757,7 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         ws.set(SS, ((M == 1) ? phi : 2.0 * phi) * g);
         self = start_pos;
         k = 1;
-        if (DEBUG && line_m) line_m[0] = -1;
+        if (DEBUG) lo.put(0, -1, -1, 0);
     }
     for (; k < M; ++k) {
         LinePre L;
@@ -688,12 +784,13 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
             c.flag += t.flag;
         }
         wflag |= t.flag;
-        if (DEBUG && line_m) line_m[k] = t.m;
         if (t.m == 0) {
+            if (DEBUG) lo.put(k, 0, -1, t.flag);
             ++k;
             break;
         }
         const int pos = select_hit(G.tv, t, hits, key, q, w, (uint32_t)k);
+        if (DEBUG) lo.put(k, t.m, (int)prim_of(G.tv, pos), t.flag);
         double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
         const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
         double S = ws.get(SS), P = ws.get(PP);
@@ -712,9 +809,41 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         ws.set(PP, P);
         self = pos;
     }
-    if (DEBUG && line_m)
-        for (int k2 = k; k2 < M; ++k2) line_m[k2] = -1;
+    if (DEBUG)
+        for (int k2 = k; k2 < M; ++k2) lo.put(k2, -1, -1, 0);
     return ws.get(SS);
+}
+
+// Per-query partial sums of the walk values.  Slot (query qi, block b of 32
+// walks of the call) holds (sum, sum of squares) at part[2 s], part[2 s + 1],
+// s = qi * tpq + b.  The 32 lanes of a warp hold 32 consecutive walks of the
+// call (walk index qi * N + w, the group aligned to 32); the lanes of one
+// slot sum their values in a fixed tree order (segmented scan) and the
+// slot's last lane adds the result with an atomic.  A slot's walks span at
+// most two aligned groups of 32, so it receives at most two adds onto zero,
+// and two adds commute exactly: the sums do not depend on scheduling.  All
+// 32 lanes call this together (live = false for lanes without a walk).
+__device__ __forceinline__ void add_tile_partials(double v, bool live, int64_t qi, int64_t w,
+                                                  int tpq, double* __restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    const long long slot = live ? qi * tpq + (w >> 5) : -1ll;
+    double s = live ? v : 0.0, ss = live ? v * v : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double s2 = __shfl_up_sync(0xFFFFFFFFu, s, o);
+        const double ss2 = __shfl_up_sync(0xFFFFFFFFu, ss, o);
+        const long long sl2 = __shfl_up_sync(0xFFFFFFFFu, slot, o);
+        if (lane >= o && sl2 == slot) {
+            s += s2;
+            ss += ss2;
+        }
+    }
+    const long long next = __shfl_down_sync(0xFFFFFFFFu, slot, 1);
+    if (live && (lane == 31 || next != slot)) {
+        atomicAdd(part + 2 * slot, s);
+        atomicAdd(part + 2 * slot + 1, ss);
+    }
 }
 
 }  // namespace wob

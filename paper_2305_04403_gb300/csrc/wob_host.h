@@ -63,6 +63,10 @@ int launch_forward(const WalkParams& p, int64_t n_paths, int start_mode, double 
 // err: the solve's device check word (NULL: none); when set, the outputs are NaN
 int launch_reduce(const double* per_walk, int64_t Q, int32_t N, double* est, double* var,
                   cudaStream_t s, const int* err);
+// From the (sum, sum of squares) partials of the walk kernels (Q x tpq x 2):
+// est / var (may be NULL) and, accumulated, sum / sumsq (may be NULL).
+int launch_reduce_part(const double* part, int64_t Q, int32_t N, int32_t tpq, double* est,
+                       double* var, double* sum, double* sumsq, cudaStream_t s, const int* err);
 int launch_reduce_accum(const double* per_walk, int64_t Q, int32_t N, double* sum,
                         double* sumsq, cudaStream_t s, const int* err);
 int launch_trace_lines(const BvhDev& b, const double* o, const double* d, const int32_t* exclude,

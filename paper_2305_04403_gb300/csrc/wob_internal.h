@@ -21,6 +21,15 @@ constexpr int kNoRef = INT32_MIN;     // empty traversal stack marker
 constexpr int64_t kMaxTriangles = (int64_t(1) << 28) - 2;
 constexpr float kDefaultTau = 2e-6f;
 constexpr float kGraze = 1e-4f;
+// The line-triangle test flags a line within kFlagMargin tau L of an edge,
+// or with a hit at |t| < kFlagMargin tau L (the oracle flags within tau L;
+// the margin covers the FP32 rounding of the line's origin and axis, so that
+// every line the oracle flags is flagged),
+// and recomputes the edge functions of a triangle in their canonical form
+// when one is below kRareMargin times that distance (scaled by the longest
+// edge): a bound above the main path's rounding error.
+constexpr float kFlagMargin = 1.25f;
+constexpr float kRareMargin = 1.5f;
 constexpr int kMaxLen = 4096;
 // Box padding in units of the mesh diagonal L: above the slab test's
 // rounding (at most 1.53e-5 of a node's extent, see dequant).
@@ -102,13 +111,17 @@ struct WalkParams {
     uint32_t q_base;
     // near-degenerate thresholds
     float tauL;
-    float edge_thr_L;  // tau * L * max_edge
+    float edge_thr_L;  // kRareMargin * kFlagMargin * tau * L * max_edge
     float graze;
     // outputs
-    double* per_walk;    // Q x N
+    double* part;        // (sum, sum of squares) per (query, 32-walk block): Q x tpq x 2
+    int32_t tpq;         // 32-walk blocks per query, ceil(N / 32)
+    double* per_walk;    // Q x N (optional: debug and gradient solves)
     double* per_walk_grad;  // 3 x Q x N gradient estimates (gradient kernels only)
     uint8_t* walk_flag;  // Q x N (optional)
     int32_t* line_m;     // Q x N x M (optional)
+    int32_t* line_prim;  // Q x N x M picked triangle (original id, -1: none) (optional)
+    uint8_t* line_flag;  // Q x N x M near-degenerate line (optional)
     unsigned long long* counters;  // [lines, nodes, tris, hits, flagged] (optional)
     int* error_word;
     unsigned long long* tile_counter;  // next walk tile (zero before the launch)

@@ -1,10 +1,12 @@
-"""Batched solves (one graph-captured launch over many problems) against
-separate single-problem solves, which the parity tests tie to the oracle."""
+"""Batched solves (one graph-captured launch over many problems) against the
+oracle's walks of each problem (problem index p), against separate
+single-problem solves and against the exact solution."""
 import os
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2305_04403_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -43,6 +45,38 @@ def small_batch(wob, tmp_path_factory):
     return items, probs, walks, keep
 
 
+def test_batched_matches_oracle(wob, small_batch):
+    """The batched kernel's estimates against the oracle's walks of every
+    problem (the double-layer recursion of Sec. 4.1 with the 1/2 rule of
+    Sec. 4.1.2, problem index p in the generator key): per query within
+    1e-4 * max|g|.  A query may miss the bar only if the oracle flagged a
+    line of its walks (the two sides can trace a line differently only
+    within the FP32 rounding distance of an edge, far inside the flag
+    distance); at least 99% of the queries must meet it."""
+    items, probs, walks, _ = small_batch
+    M = [it.max_len for it in items]
+    b = wob.Batch(probs, [it.queries for it in items], walks, M)
+    b.run(seed=5)
+    torch.cuda.synchronize()
+    n_ok = n_all = n_flag = 0
+    for p, ((est, var), it, w, m) in enumerate(zip(b.split(), items, walks, M)):
+        if len(it.queries) == 0:
+            continue
+        r = O.dl_walks(it.verts, it.tris, it.queries, w, m, seed=5, problem=p,
+                       mode=O.DATA_POINT, x0=(3.0, 0.0, 0.0))
+        e_r, v_r = O.reduce(r["per_walk"])
+        scale = 1.0 / max(3.0 - float(np.abs(it.verts).max()), 0.5)
+        flagged = r["flag"].sum(1) > 0
+        ok = (np.abs(est - e_r) <= 1e-4 * scale) & np.isclose(var, v_r, rtol=1e-6, atol=1e-12)
+        assert np.all(ok | flagged)
+        n_ok += int(ok.sum())
+        n_all += len(ok)
+        n_flag += int(flagged.sum())
+    print(f"batched vs oracle: {n_ok} of {n_all} queries within the bar "
+          f"({n_flag} with an oracle-flagged line)")
+    assert n_ok >= 0.99 * n_all
+
+
 def test_batched_equals_separate_solves(wob, small_batch):
     items, probs, walks, _ = small_batch
     M = [it.max_len for it in items]
@@ -60,6 +94,19 @@ def test_batched_equals_separate_solves(wob, small_batch):
         e1, v1 = e1.cpu().numpy(), v1.cpu().numpy()
         assert np.allclose(est, e1, rtol=1e-12, atol=1e-13)
         assert np.allclose(var, v1, rtol=1e-10, atol=1e-13)
+
+
+def test_solve_batched_one_shot_equals_batch(wob, small_batch):
+    """wob_solve_batched (create + run + destroy in one call, through the C
+    ABI) gives the persistent batch's estimates."""
+    items, probs, walks, _ = small_batch
+    M = [it.max_len for it in items]
+    b = wob.Batch(probs, [it.queries for it in items], walks, M)
+    b.run(seed=7)
+    ref = b.split()
+    got = wob.solve_batched(probs, [it.queries for it in items], walks, M, seed=7)
+    for (e, v), (er, vr) in zip(got, ref):
+        assert np.array_equal(e, er) and np.array_equal(v, vr)
 
 
 def test_batched_schedules_agree_and_seed_matters(wob, small_batch):

@@ -1,7 +1,8 @@
 """Edge cases of the newer entry points: empty query sets are no-ops
 (nothing launched, accumulators untouched), the largest accepted path
 length runs and one beyond is refused, and every problem kind accepts a
-walk count that is not a multiple of the 32-walk warp tile."""
+walk count that is not a multiple of the 32-walk warp tile; wob_get_stats
+returns the last counted solve's counters."""
 import numpy as np
 import pytest
 
@@ -72,3 +73,21 @@ def test_ragged_walk_counts(wob, sphere, kind):
     a = wob.solve_debug(prob, q, 33, 3, seed=7, want_lines=False)["per_walk"]
     b = wob.solve_debug(prob, q, 64, 3, seed=7, want_lines=False)["per_walk"]
     assert torch.equal(a, b[:, :33])
+
+
+def test_get_stats_returns_the_last_counted_solve(wob, sphere):
+    """wob_get_stats (through the C ABI) returns the counters of the calling
+    thread's last wob_solve_counted call; another thread has its own."""
+    import threading
+    prob = wob.Problem(sphere, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    q = I.ball_queries(40, 0.8, 2)
+    _, _, st = wob.solve_counted(prob, q, 64, 4, seed=3)
+    assert st["lines"] > 0 and st["node_visits"] > 0 and st["hits"] >= st["lines"]
+    assert wob.get_stats() == st
+    wob.solve(prob, q, 64, 4, seed=4)  # an uncounted solve leaves them alone
+    assert wob.get_stats() == st
+    other = {}
+    t = threading.Thread(target=lambda: other.update(wob.get_stats()))
+    t.start()
+    t.join()
+    assert other == dict(lines=0, node_visits=0, tri_tests=0, hits=0, flagged=0)

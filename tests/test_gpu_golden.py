@@ -1,6 +1,9 @@
 """The CUDA path on the first workload against the stored oracle values
-(tests/golden/config1_oracle.csv): per query within 1e-4 * max|g| wherever
-neither side flagged a walk of that query as near-degenerate."""
+(tests/golden/config1_oracle.csv): per query within 1e-4 * max|g|.  A query
+may miss the bar only if the oracle flagged a line of its walks as
+near-degenerate (the two sides can trace a line differently only within
+the FP32 rounding distance of a triangle edge, far inside the flag distance
+tau L); at least 99% of the queries must meet it."""
 import numpy as np
 import pytest
 
@@ -24,10 +27,10 @@ def test_config1_matches_stored_oracle_values():
     prob = wob.Problem(bvh, data_mode=wob.DATA_VERTEX_P1, vertex_data=torch.from_numpy(vd).cuda())
     q = g["q"].astype(np.float32)
     d = {k: t.cpu().numpy() for k, t in wob.solve_debug(prob, q, 64, 4, seed=0, want_lines=False).items()}
-    ok = (g["flagged"] == 0) & (d["flag"].sum(axis=1) == 0)
-    assert ok.mean() > 0.3   # 256 lines per query; either side's flag drops the query
     tol = 1e-4 * np.abs(vd).max()
-    assert np.all(np.abs(d["est"][ok] - g["est"][ok]) <= tol)
+    ok = np.abs(d["est"] - g["est"]) <= tol
+    assert np.all(ok | (g["flagged"] > 0))
+    assert ok.mean() >= 0.99, ok.mean()
     # the production entry point gives the debug kernel's numbers
     est, var = wob.solve(prob, q, 64, 4, seed=0)
     assert np.array_equal(est.cpu().numpy(), d["est"])

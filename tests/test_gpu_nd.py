@@ -1,16 +1,19 @@
 """GPU parity of the Neumann walks through the direct boundary integral
 equation (Sec. 4.2; kind WOB_NEUMANN_DIRECT) against the oracle's nd_walks.
 
-Bars as for the double-layer walks: hit counts of every line exact on walks
-neither side flags; per walk |gpu - oracle| <= 1e-5 * sum_k |term_k| (the
-GPU evaluates the source's data in FP64 from FP32 vertices, G in FP64);
-per query the mean over unflagged walks within 1e-4 * the data scale.
+Bars as for the double-layer walks (tests/_parity.py): every walk is
+followed line by line and compared whole where its lines agree, flagged or
+not -- |gpu - oracle| <= 1e-5 * sum_k |term_k| (the GPU evaluates the
+source's data in FP64 from FP32 vertices, G in FP32 from an FP64 distance);
+a line where the two sides first differ must be flagged; per query the
+mean over the walks compared whole within 1e-4 * the data scale.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2305_04403_gb300 import inputs as I
+from _parity import compare_walks
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,17 +48,10 @@ def _run(wob, v, f, q, N, M, phi=1, mode=O.DATA_POLY, poly=None, x0=None, vd=Non
 
 
 def _bars(g, r, scale, min_ok):
-    ok = (g["flag"] == 0) & (r["flag"] == 0)
-    assert ok.mean() >= min_ok
-    err = np.abs(g["per_walk"] - r["per_walk"])
-    tol = 1e-5 * r["abs_terms"] + 1e-12 * scale
-    assert np.all(err[ok] <= tol[ok]), (err[ok] / np.maximum(tol[ok], 1e-300)).max()
-    assert np.array_equal(g["line_m"][ok], r["line_m"][ok])
-    n = np.maximum(ok.sum(1), 1)
-    mg = np.where(ok, g["per_walk"], 0.0).sum(1) / n
-    mr = np.where(ok, r["per_walk"], 0.0).sum(1) / n
-    assert np.all(np.abs(mg - mr) <= 1e-4 * scale)
-    return ok
+    same, st = compare_walks(g, r, scale)
+    print("direct BIE:", st)
+    assert st["walks_compared"] >= min_ok
+    return same
 
 
 def test_nd_interior_sphere_parity(wob):
@@ -63,7 +59,7 @@ def test_nd_interior_sphere_parity(wob):
     q = I.ball_queries(48, 0.85, 2)
     poly = (0.0, 0.3, -0.2, 0.5, 1.0, -1.0, 0.0, 0.4, 0.0, 0.0)
     g, r = _run(wob, v, f, q, 64, 5, poly=poly, seed=3, problem=1)
-    ok = _bars(g, r, 2.0, 0.95)
+    ok = _bars(g, r, 2.0, 0.999)
     assert np.all(g["line_m"][ok][:, 0] == 2) and np.all(g["line_m"][ok][:, 1:] == 1)
 
 
@@ -77,7 +73,7 @@ def test_nd_nonconvex_parity(wob, phi):
     q = (d * (sh.radius(d) * fac)[:, None]).astype(np.float32)
     x0 = (0.05, -0.1, 0.1) if phi == -1 else (3.0, 0.5, -1.0)
     g, r = _run(wob, v, f, q, 64, 8, phi=phi, mode=O.DATA_POINT, x0=x0, seed=7, problem=2)
-    _bars(g, r, 1.0 / 0.5, 0.8)
+    _bars(g, r, 1.0 / 0.5, 0.99)
     assert (r["line_m"] >= 3).any()
 
 
@@ -86,7 +82,7 @@ def test_nd_vertex_data_and_boundary_start(wob):
     p, prim = I.boundary_points(v, f, 32, 9)
     vd = (0.3 * v[:, 0] - 0.2 * v[:, 2] + 0.1).astype(np.float32)  # any P1 flux
     g, r = _run(wob, v, f, p, 64, 6, mode=O.DATA_VERTEX_P1, vd=vd, prim=prim, seed=1)
-    _bars(g, r, float(np.abs(vd).max()), 0.9)
+    _bars(g, r, float(np.abs(vd).max()), 0.99)
     assert np.all(g["line_m"][..., 0] == -1)
 
 

@@ -3,7 +3,10 @@ device memory (a process whose GPU memory belongs to its own allocator, or a
 path that cannot take an allocation and its synchronisation).  It must give
 the same estimates as wob_solve, whose scratch is allocated per call, on two
 calls in a row (the second reuses the library's fixed array, which still
-holds the first call's values), and reject sizes beyond its fixed array.
+holds the first call's values), accept the largest size its fixed array
+holds, reject larger ones, and allocate nothing: the device's memory pool
+(where the library's stream-ordered allocations come from) keeps its
+high-water mark across the call.
 
 Kept in a file pytest collects last so that a run stopping at the first
 failure has already run every other test; it also passes on its own.
@@ -18,7 +21,7 @@ from paper_2305_04403_gb300 import inputs as I
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MAX_WALK_VALUES = 1 << 20
+MAX_BLOCKS = 1 << 19  # (query, 32-walk block) partial sums the fixed array holds
 
 
 @pytest.fixture(scope="module")
@@ -31,12 +34,13 @@ def wob():
     return w
 
 
-def _noalloc(wob, prob, q, walks, max_len, seed):
+def _noalloc(wob, prob, q, walks, max_len, seed, est=None, var=None):
     """Call wob_solve_noalloc through the C ABI with caller-owned outputs."""
     lib = wob.load_library()
     Q = q.shape[0]
-    est = torch.full((Q,), np.nan, dtype=torch.float64, device="cuda")
-    var = torch.full((Q,), np.nan, dtype=torch.float64, device="cuda")
+    if est is None:
+        est = torch.full((Q,), np.nan, dtype=torch.float64, device="cuda")
+        var = torch.full((Q,), np.nan, dtype=torch.float64, device="cuda")
     pc = prob._c()
     stream = torch.cuda.current_stream()
     rc = lib.wob_solve_noalloc(ctypes.byref(pc), ctypes.c_void_p(q.data_ptr()), None, Q, walks,
@@ -96,14 +100,74 @@ def test_noalloc_single_layer_matches(wob):
     assert torch.allclose(est, est_ref, rtol=0, atol=1e-12 * est_ref.abs().max().item())
 
 
-def test_noalloc_rejects_oversized_work(wob):
+def test_noalloc_largest_size_and_oversized_work(wob):
     v, f = I.icosphere(1)
     mesh = wob.build_mesh(v, f)
     bvh = wob.build_bvh(mesh)
     prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
-    q = torch.from_numpy(I.ball_queries(1025, 0.5, 1)).cuda()
-    rc, est, var = _noalloc(wob, prob, q, 1024, 4, 0)  # 1025 * 1024 > 2^20
+    # the largest size: Q * ceil(1024 / 32) = 2^19 blocks
+    q = torch.from_numpy(I.ball_queries(MAX_BLOCKS // 32, 0.5, 1)).cuda()
+    est_ref, _ = wob.solve(prob, q, 1024, 4, seed=3)
+    rc, est, var = _noalloc(wob, prob, q, 1024, 4, 3)
+    torch.cuda.synchronize()
+    assert rc == 0, wob.load_library().wob_last_error()
+    assert torch.allclose(est, est_ref, rtol=0, atol=1e-12)
+    # one query more does not fit
+    q = torch.from_numpy(I.ball_queries(MAX_BLOCKS // 32 + 1, 0.5, 1)).cuda()
+    rc, est, var = _noalloc(wob, prob, q, 1024, 4, 0)
     assert rc == -1
     assert b"exceeds" in wob.load_library().wob_last_error()
     torch.cuda.synchronize()
     assert torch.isnan(est).all()  # nothing was launched
+
+
+class _Pool:
+    """High-water mark of the current device's memory pool (the pool that
+    stream-ordered allocations draw from), read through the driver API."""
+
+    USED_MEM_HIGH = 8  # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def reset(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+    def high(self) -> int:
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(v)) == 0
+        return v.value
+
+
+def test_noalloc_allocates_nothing(wob):
+    v, f = I.icosphere(3)
+    mesh = wob.build_mesh(v, f)
+    bvh = wob.build_bvh(mesh)
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    q = torch.from_numpy(I.ball_queries(512, 0.9, 2)).cuda()
+    rc, _, _ = _noalloc(wob, prob, q, 64, 4, 0)  # first call on the device: set-up
+    torch.cuda.synchronize()
+    assert rc == 0
+    pool = _Pool()
+    # the detector sees the stream-ordered scratch that wob_solve allocates
+    torch.cuda.synchronize()
+    pool.reset()
+    base = pool.high()
+    wob.solve(prob, q, 64, 4, seed=1)
+    torch.cuda.synchronize()
+    assert pool.high() > base
+    # ... and wob_solve_noalloc leaves the high-water mark where it was
+    est = torch.empty(512, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(est)
+    torch.cuda.synchronize()
+    pool.reset()
+    base = pool.high()
+    rc, est, var = _noalloc(wob, prob, q, 64, 4, 1, est, var)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert pool.high() == base
