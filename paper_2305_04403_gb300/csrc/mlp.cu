@@ -1,21 +1,16 @@
-// mlp.cu -- the control variate's network on the tensor cores:
-// Fourier features (16 frequencies 2^(k/3), sin and cos of 2 pi f y_d:
-// 96 inputs) -> 4 x (64, SiLU) -> 1.  BF16 operands, FP32 accumulation,
-// mma.sync.m16n8k16; FP32 master weights (out x in layout, biases after
-// each matrix) and Adam state in device memory.
-//
-// Layouts (m16n8k16, g = lane / 4, t = lane % 4):
-//   A (16 x 16, row-major): regs (row g, k 2t..2t+1), (row g+8, k 2t..),
-//                           (row g, k 8+2t..), (row g+8, k 8+2t..)
-//   B (16 x 8, "col"):      regs (k 2t.., n g), (k 8+2t.., n g)
-//   C (16 x 8, f32):        (row g, n 2t), (row g, n 2t+1), (row g+8, n 2t), (row g+8, n 2t+1)
-// so the C tiles 2j and 2j+1 of one layer are, after the activation, exactly
-// the A fragment of k-block j of the next layer (kept in registers).
+// mlp.cu -- the control variate's network on the 5th-generation tensor
+// cores (tcgen05.mma, accumulators in tensor memory): Fourier features (16
+// frequencies 2^(k/3), sin and cos of 2 pi f y_d: 96 inputs) ->
+// 4 x (64, SiLU) -> 1.  BF16 operands, FP32 accumulation; FP32 master weights
+// (out x in layout, biases after each matrix) and Adam state in device
+// memory.  Operands live in shared memory in the canonical K-major layout
+// of tcgen05.cuh; every product is issued by one thread with M = 128 rows.
 #include <atomic>
 #include <cmath>
 
 #include <cuda_bf16.h>
 
+#include "tcgen05.cuh"
 #include "wob_device.cuh"
 #include "wob_host.h"
 
@@ -34,31 +29,10 @@ __host__ __device__ constexpr int b_off(int l) { return w_off(l) + (l == 0 ? 96 
 constexpr int kW5 = 96 * 64 + 64 + 3 * (64 * 64 + 64);
 constexpr int kB5 = kW5 + 64;
 
-constexpr int kLd1 = kFeat + 8;   // smem row stride (bf16) of a 96-wide matrix
-constexpr int kLd = kWidth + 8;   // of a 64-wide matrix
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t (&r)[4], const void* p)
-{
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
 }
 
 __device__ __forceinline__ float silu(float a) { return a / (1.0f + __expf(-a)); }
@@ -78,162 +52,6 @@ __device__ __forceinline__ float feature(const float y[3], int c)
     return (j & 1) ? cv : sv;
 }
 
-// Weights into shared memory as BF16: Wt[l] = [out][in] (forward B operand)
-// and optionally, for layers 1..3, W[l] = [in][out] (the B operand of the
-// backward product da . W; layer 0's input gradient is never needed).
-struct SmemNet {
-    __nv_bfloat16* wt[4];
-    __nv_bfloat16* w[4];
-    float* bias;  // 4 x 64
-    float* w5;    // 64
-    float b5;
-};
-
-// One layer's matrix (64 x IN, row-major FP32) into shared memory as BF16.
-// 128 threads; every thread issues all of its float4 loads before any
-// store, so the loads are in flight together.
-template <int IN>
-__device__ __forceinline__ void load_layer(const float* __restrict__ W, __nv_bfloat16* wt,
-                                           __nv_bfloat16* w, bool vec)
-{
-    constexpr int kLdIn = IN == kFeat ? kLd1 : kLd;
-    constexpr int kPer = 64 * IN / 4 / 128;  // float4 per thread
-    static_assert(64 * IN % (4 * 128) == 0, "layer size");
-    float4 r[kPer];
-    if (vec) {
-        const float4* W4 = reinterpret_cast<const float4*>(W);
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) r[u] = __ldg(W4 + threadIdx.x + 128 * u);
-    } else {
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const float* p = W + 4 * (threadIdx.x + 128 * u);
-            r[u] = make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int i = 4 * (threadIdx.x + 128 * u);
-        const int o = i / IN, k = i - o * IN;  // 4 consecutive k of row o
-        const __nv_bfloat16 b[4] = {__float2bfloat16_rn(r[u].x), __float2bfloat16_rn(r[u].y),
-                                    __float2bfloat16_rn(r[u].z), __float2bfloat16_rn(r[u].w)};
-        __nv_bfloat16* d = wt + o * kLdIn + k;
-        *reinterpret_cast<uint2*>(d) =
-            make_uint2((uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16),
-                       (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16));
-        if (w)
-            for (int c = 0; c < 4; ++c) w[(k + c) * kLd + o] = b[c];
-    }
-}
-
-// The network into shared memory (launched with 128 threads).
-__device__ void load_net(const float* __restrict__ params, SmemNet& n, bool with_transposed)
-{
-    const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
-    load_layer<kFeat>(params + w_off(0), n.wt[0], nullptr, vec);
-    for (int l = 1; l < 4; ++l)
-        load_layer<kWidth>(params + w_off(l), n.wt[l], with_transposed ? n.w[l] : nullptr, vec);
-    for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x)
-        n.bias[i] = params[b_off(i >> 6) + (i & 63)];
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) n.w5[i] = params[kW5 + i];
-    n.b5 = params[kB5];
-    __syncthreads();
-}
-
-// Forward of one 16-row tile held by a warp.  Features at rows r0 = g and
-// r1 = g + 8 of the tile (ya, yb); returns the outputs of those rows.
-// Optionally stores pre-activations (FP32) and activations (BF16) of every
-// layer for the backward pass (row stride kLd / kLd1 per layer buffer).
-template <bool STORE>
-__device__ __forceinline__ void forward_tile(const SmemNet& n, const float ya[3], const float yb[3],
-                                             float& out_a, float& out_b, float* const* pre,
-                                             __nv_bfloat16* const* act, int row0)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    uint32_t A[6][4];
-    for (int kb = 0; kb < 6; ++kb) {
-        const int c = 16 * kb + 2 * t;
-        A[kb][0] = pack_bf16(feature(ya, c), feature(ya, c + 1));
-        A[kb][1] = pack_bf16(feature(yb, c), feature(yb, c + 1));
-        A[kb][2] = pack_bf16(feature(ya, c + 8), feature(ya, c + 9));
-        A[kb][3] = pack_bf16(feature(yb, c + 8), feature(yb, c + 9));
-        if (STORE) {
-            __nv_bfloat16* h0 = act[0];
-            *reinterpret_cast<uint32_t*>(h0 + (row0 + g) * kLd1 + c) = A[kb][0];
-            *reinterpret_cast<uint32_t*>(h0 + (row0 + g + 8) * kLd1 + c) = A[kb][1];
-            *reinterpret_cast<uint32_t*>(h0 + (row0 + g) * kLd1 + c + 8) = A[kb][2];
-            *reinterpret_cast<uint32_t*>(h0 + (row0 + g + 8) * kLd1 + c + 8) = A[kb][3];
-        }
-    }
-    float H[8][4];
-    int kblocks = 6;
-    for (int l = 0; l < 4; ++l) {
-        const int ld_in = l == 0 ? kLd1 : kLd;
-        const __nv_bfloat16* wt = n.wt[l];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            const __nv_bfloat16* brow = wt + (nt * 8 + g) * ld_in + 2 * t;
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(brow + 16 * kb);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(brow + 16 * kb + 8);
-                mma_bf16(c, A[kb], b0, b1);
-            }
-            const float bias0 = n.bias[l * 64 + nt * 8 + 2 * t];
-            const float bias1 = n.bias[l * 64 + nt * 8 + 2 * t + 1];
-            H[nt][0] = c[0] + bias0;
-            H[nt][1] = c[1] + bias1;
-            H[nt][2] = c[2] + bias0;
-            H[nt][3] = c[3] + bias1;
-            if (STORE) {
-                float* p = pre[l];
-                const int col = nt * 8 + 2 * t;
-                p[(row0 + g) * kLd + col] = H[nt][0];
-                p[(row0 + g) * kLd + col + 1] = H[nt][1];
-                p[(row0 + g + 8) * kLd + col] = H[nt][2];
-                p[(row0 + g + 8) * kLd + col + 1] = H[nt][3];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) H[nt][i] = silu(H[nt][i]);
-        }
-        // activations -> A fragments of the next layer
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            A[kb][0] = pack_bf16(H[2 * kb][0], H[2 * kb][1]);
-            A[kb][1] = pack_bf16(H[2 * kb][2], H[2 * kb][3]);
-            A[kb][2] = pack_bf16(H[2 * kb + 1][0], H[2 * kb + 1][1]);
-            A[kb][3] = pack_bf16(H[2 * kb + 1][2], H[2 * kb + 1][3]);
-            if (STORE) {
-                __nv_bfloat16* h = act[l + 1];
-                const int c = 16 * kb + 2 * t;
-                *reinterpret_cast<uint32_t*>(h + (row0 + g) * kLd + c) = A[kb][0];
-                *reinterpret_cast<uint32_t*>(h + (row0 + g + 8) * kLd + c) = A[kb][1];
-                *reinterpret_cast<uint32_t*>(h + (row0 + g) * kLd + c + 8) = A[kb][2];
-                *reinterpret_cast<uint32_t*>(h + (row0 + g + 8) * kLd + c + 8) = A[kb][3];
-            }
-        }
-        kblocks = 4;
-    }
-    // output layer (64 -> 1) in FP32 on the last activations (rounded as
-    // the next layer would see them), reduced over the 4 lanes of a row
-    float sa = 0.f, sb = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int col = nt * 8 + 2 * t;
-        const float w0 = n.w5[col], w1 = n.w5[col + 1];
-        sa += __bfloat162float(__float2bfloat16_rn(H[nt][0])) * w0 +
-              __bfloat162float(__float2bfloat16_rn(H[nt][1])) * w1;
-        sb += __bfloat162float(__float2bfloat16_rn(H[nt][2])) * w0 +
-              __bfloat162float(__float2bfloat16_rn(H[nt][3])) * w1;
-    }
-    sa += __shfl_xor_sync(kFull, sa, 1);
-    sa += __shfl_xor_sync(kFull, sa, 2);
-    sb += __shfl_xor_sync(kFull, sb, 1);
-    sb += __shfl_xor_sync(kFull, sb, 2);
-    out_a = sa + n.b5;
-    out_b = sb + n.b5;
-}
-
 __device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t n, int64_t r,
                                            float y[3], int stride = 3)
 {
@@ -246,204 +64,430 @@ __device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t 
     }
 }
 
-constexpr int kFwdSmem = 64 * kLd1 * 2 + 3 * 64 * kLd * 2 + 4 * 64 * 4 + 64 * 4;
+// ---------------------------------------------------------------------------
+// Forward on the 5th-generation tensor cores (tcgen05): a CTA of 128 threads
+// takes tiles of 128 points; thread t owns row t of the tile.  Per tile the
+// features (BF16) go to shared memory in the canonical K-major layout (the
+// A operand), one thread issues the layer's tcgen05.mma (M 128, N 64, K 16
+// per instruction) into a 64-column FP32 accumulator in tensor memory, the
+// commit arrives on an mbarrier, every thread loads its row of the
+// accumulator (tcgen05.ld), adds the bias, applies SiLU and writes the BF16
+// activations back as the next layer's A operand.  The weights (B operand,
+// W as stored: out x in = N x K, K-major) stay in shared memory for the
+// whole launch.  The 64 -> 1 output layer runs in FP32 per thread on the
+// BF16-rounded activations, as the tensor cores would see them.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr int kTcCols = 64;                          // tensor-memory columns per CTA
+constexpr int kTcOffW0 = 0;                          // 64 x 96 BF16, canonical K-major
+constexpr int kTcOffW1 = kTcOffW0 + 64 * kFeat * 2;  // W1..W3: 64 x 64 each
+constexpr int kTcOffA = kTcOffW1 + 3 * 64 * kWidth * 2;  // 128 x 96 BF16 (layers 1-3: 128 x 64)
+constexpr int kTcOffBias = kTcOffA + kTcRows * kFeat * 2;  // 4 x 64 FP32
+constexpr int kTcOffW5 = kTcOffBias + 4 * 64 * 4;          // 64 FP32, then b5
+constexpr int kTcOffMisc = kTcOffW5 + 64 * 4 + 16;         // mbarrier (8 B), TMEM address (4 B)
+constexpr int kTcFwdSmem = kTcOffMisc + 16;
+constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before giving up (seconds)
+static_assert(kTcOffA % 1024 == 0 && kTcOffW1 % 1024 == 0, "operand alignment");
 
-__global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ params,
-                                                     const float* __restrict__ x, int stride,
-                                                     int64_t n, float* __restrict__ out)
+// One layer's matrix (64 x IN, row-major FP32 in params) into shared memory
+// as BF16 in the canonical K-major layout (rows = outputs, K = inputs).
+template <int IN>
+__device__ __forceinline__ void load_layer_kmajor(const float* __restrict__ W, unsigned char* dst,
+                                                  bool vec)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    SmemNet net;
-    unsigned char* p = smem;
-    net.wt[0] = (__nv_bfloat16*)p;
-    p += 64 * kLd1 * 2;
-    for (int l = 1; l < 4; ++l) {
-        net.wt[l] = (__nv_bfloat16*)p;
-        p += 64 * kLd * 2;
-    }
-    net.bias = (float*)p;
-    p += 4 * 64 * 4;
-    net.w5 = (float*)p;
-    load_net(params, net, false);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2;
-    const int64_t tiles = (n + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
-        const int64_t ra = tile * 16 + g, rb = ra + 8;
-        float ya[3], yb[3];
-        load_point(x, n, ra, ya, stride);
-        load_point(x, n, rb, yb, stride);
-        float oa, ob;
-        forward_tile<false>(net, ya, yb, oa, ob, nullptr, nullptr, 0);
-        if ((lane & 3) == 0) {
-            if (ra < n) out[ra] = oa;
-            if (rb < n) out[rb] = ob;
+    constexpr int kChunks = 64 * IN / 8;  // 8 consecutive inputs of one output
+    for (int c = threadIdx.x; c < kChunks; c += blockDim.x) {
+        const int o = c / (IN / 8), k0 = (c % (IN / 8)) * 8;
+        const float* src = W + o * IN + k0;
+        float4 lo, hi;
+        if (vec) {
+            lo = __ldg(reinterpret_cast<const float4*>(src));
+            hi = __ldg(reinterpret_cast<const float4*>(src) + 1);
+        } else {
+            lo = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+            hi = make_float4(__ldg(src + 4), __ldg(src + 5), __ldg(src + 6), __ldg(src + 7));
         }
+        const uint4 v = make_uint4(pack_bf16(lo.x, lo.y), pack_bf16(lo.z, lo.w),
+                                   pack_bf16(hi.x, hi.y), pack_bf16(hi.z, hi.w));
+        *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(o, k0, IN)) = v;
     }
 }
 
-// ---------------------------------------------------------------------------
-// training step: forward + backward of 64 rows per block, per-block partial
-// gradients (reduced in a fixed order by k_mlp_adam)
-// ---------------------------------------------------------------------------
-constexpr int kTrainRows = 64;
-// shared-memory layout of the training kernel (byte offsets); the size the
-// kernel is launched with is the end of the last region
-constexpr int kOffWt = 0;                                   // Wt[0..3]
-constexpr int kOffW = kOffWt + 64 * kLd1 * 2 + 3 * 64 * kLd * 2;  // W[1..3], [64][kLd]
-constexpr int kOffBias = kOffW + 3 * 64 * kLd * 2;          // bias 4 x 64, w5 64
-constexpr int kOffAct = kOffBias + 4 * 64 * 4 + 64 * 4;     // h0 [rows][kLd1], h1..h4 [rows][kLd]
-constexpr int kOffPre = kOffAct + kTrainRows * kLd1 * 2 + 4 * kTrainRows * kLd * 2;  // a1..a4 FP32
-constexpr int kOffDa = kOffPre + 4 * kTrainRows * kLd * 4;  // da (BF16, current layer)
-constexpr int kOffDout = kOffDa + kTrainRows * kLd * 2;     // dL/dout per row
-constexpr int kTrainSmem = kOffDout + kTrainRows * 4;
-static_assert(kTrainSmem <= 227 * 1024, "training tile exceeds shared memory");
-static_assert(kOffW % 16 == 0 && kOffAct % 16 == 0 && kOffPre % 16 == 0 && kOffDa % 16 == 0,
-              "ldmatrix rows need 16-byte alignment");
-
-__global__ void __launch_bounds__(128) k_mlp_train(const float* __restrict__ params,
-                                                   const float* __restrict__ x,
-                                                   const float* __restrict__ target, int64_t n,
-                                                   float* __restrict__ partial,
-                                                   float* __restrict__ loss_partial)
+__global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restrict__ params,
+                                                           const float* __restrict__ x,
+                                                           int stride, int64_t n,
+                                                           float* __restrict__ out)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    SmemNet net;
-    net.wt[0] = (__nv_bfloat16*)(smem + kOffWt);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float* bias = reinterpret_cast<float*>(smem + kTcOffBias);
+    float* w5 = reinterpret_cast<float*>(smem + kTcOffW5);
+    const uint32_t mbar = tc::smem_addr(smem + kTcOffMisc);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcOffMisc + 8);
+
+    // the network into shared memory, the accumulator into tensor memory
+    const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
+    load_layer_kmajor<kFeat>(params + w_off(0), smem + kTcOffW0, vec);
     for (int l = 1; l < 4; ++l)
-        net.wt[l] = (__nv_bfloat16*)(smem + kOffWt + 64 * kLd1 * 2 + (l - 1) * 64 * kLd * 2);
-    net.w[0] = nullptr;
-    for (int l = 1; l < 4; ++l) net.w[l] = (__nv_bfloat16*)(smem + kOffW + (l - 1) * 64 * kLd * 2);
-    net.bias = (float*)(smem + kOffBias);
-    net.w5 = net.bias + 4 * 64;
-    __nv_bfloat16* act[5];
-    act[0] = (__nv_bfloat16*)(smem + kOffAct);
-    for (int l = 1; l < 5; ++l)
-        act[l] = (__nv_bfloat16*)(smem + kOffAct + kTrainRows * kLd1 * 2 + (l - 1) * kTrainRows * kLd * 2);
-    float* pre[4];
-    for (int l = 0; l < 4; ++l) pre[l] = (float*)(smem + kOffPre + l * kTrainRows * kLd * 4);
-    __nv_bfloat16* da = (__nv_bfloat16*)(smem + kOffDa);
-    float* dout = (float*)(smem + kOffDout);
+        load_layer_kmajor<kWidth>(params + w_off(l), smem + kTcOffW1 + (l - 1) * 64 * kWidth * 2,
+                                  vec);
+    for (int i = tid; i < 4 * 64; i += blockDim.x) bias[i] = params[b_off(i >> 6) + (i & 63)];
+    for (int i = tid; i < 64; i += blockDim.x) w5[i] = params[kW5 + i];
+    if (tid == 0) {
+        w5[64] = params[kB5];
+        tc::mbar_init(mbar, 1);
+    }
+    __syncwarp();
+    if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTcCols);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's lanes
+    constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTcRows, 64);
+    const uint32_t a_base = tc::smem_addr(smem + kTcOffA);
+    uint32_t phase = 0;
+    bool failed = false;
 
-    load_net(params, net, true);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int64_t row_base = (int64_t)blockIdx.x * kTrainRows;
-    const int row0 = warp * 16;
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+        const int64_t r = tile * kTcRows + tid;
+        float y[3];
+        load_point(x, n, r, y, stride);
+        // features of row tid: 12 chunks of 8 columns, one 16-byte store each
+#pragma unroll 1
+        for (int c = 0; c < kFeat / 8; ++c) {
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) f[j] = feature(y, 8 * c + j);
+            *reinterpret_cast<uint4*>(smem + kTcOffA + tc::kmajor_offset(tid, 8 * c, kFeat)) =
+                make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                           pack_bf16(f[6], f[7]));
+        }
+        float o = 0.f;
+        for (int l = 0; l < 4; ++l) {
+            const int K = l == 0 ? kFeat : kWidth;
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t b_base =
+                    tc::smem_addr(smem + (l == 0 ? kTcOffW0 : kTcOffW1 + (l - 1) * 64 * kWidth * 2));
+                for (int kb = 0; kb < K / 16; ++kb)
+                    tc::mma_bf16(tmem, tc::smem_desc(a_base + 256 * kb, 128, K * 16),
+                                 tc::smem_desc(b_base + 256 * kb, 128, K * 16), kIdesc, kb > 0);
+                tc::commit(mbar);
+            }
+            const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+            if (__syncthreads_or(!ok)) {  // block-uniform: every thread stops together
+                failed = true;
+                if (ok) break;
+                tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the product in flight, bounded
+                break;
+            }
+            phase ^= 1u;
+            tc::fence_after_sync();
+            float h[64];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tc::tmem_ld16(trow + 16 * q, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) h[16 * q + j] = v[j];
+            }
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; ++j) h[j] = silu(h[j] + bias[64 * l + j]);
+            if (l < 3) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    *reinterpret_cast<uint4*>(smem + kTcOffA + tc::kmajor_offset(tid, 8 * c, kWidth)) =
+                        make_uint4(pack_bf16(h[8 * c], h[8 * c + 1]), pack_bf16(h[8 * c + 2], h[8 * c + 3]),
+                                   pack_bf16(h[8 * c + 4], h[8 * c + 5]),
+                                   pack_bf16(h[8 * c + 6], h[8 * c + 7]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j)
+                    o = fmaf(__bfloat162float(__float2bfloat16_rn(h[j])), w5[j], o);
+                o += w5[64];
+            }
+        }
+        if (r < n) out[r] = failed ? __int_as_float(0x7FC00000) : o;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, kTcCols);
+}
 
-    // forward, storing activations
-    {
-        const int64_t ra = row_base + row0 + g, rb = ra + 8;
-        float ya[3], yb[3];
-        load_point(x, n, ra, ya);
-        load_point(x, n, rb, yb);
-        float oa, ob;
-        forward_tile<true>(net, ya, yb, oa, ob, pre, act, row0);
-        // dL/dout of the mean squared error over the n samples
-        if (t == 0) {
-            const float ea = ra < n ? oa - target[ra] : 0.f;
-            const float eb = rb < n ? ob - target[rb] : 0.f;
-            dout[row0 + g] = 2.f * ea / (float)n;
-            dout[row0 + g + 8] = 2.f * eb / (float)n;
-            atomicAdd(loss_partial + blockIdx.x, ea * ea + eb * eb);
+// ---------------------------------------------------------------------------
+// Training step on the tensor cores: forward and backward of 128 rows per
+// CTA (thread t owns row t), per-CTA partial gradients (summed in a fixed
+// order by k_mlp_adam).  Every product is a tcgen05.mma of M 128 with the
+// accumulator in tensor memory:
+//   forward    a_l = h_l W_l^T          (A = h_l [rows x in], B = W_l)
+//   weights    dW_l^T = h_l^T da_l      (A = h_l^T [in x rows], B = da_l^T)
+//   inputs     dh_l = da_l W_l          (A = da_l [rows x 64], B = W_l^T)
+// The pre-activations of the four hidden layers stay in tensor memory
+// (columns 64 l .. 64 l + 63) until the backward pass reads them; h_l^T
+// carries a row of ones after its K_l inputs, so row K_l of dW_l^T is the
+// bias gradient.  Operands are BF16 in the canonical K-major layout, the
+// transposes written by the threads that own the rows.
+// ---------------------------------------------------------------------------
+constexpr int kTrainRows = 128;
+constexpr int kTrOffW0 = 0;                               // W0: 64 x 96
+constexpr int kTrOffW1 = kTrOffW0 + 64 * kFeat * 2;       // W1..W3: 64 x 64
+constexpr int kTrOffWT1 = kTrOffW1 + 3 * 64 * kWidth * 2;  // W1^T..W3^T: 64 (in) x 64 (out)
+constexpr int kTrOffA = kTrOffWT1 + 3 * 64 * kWidth * 2;   // forward A: 128 x 96
+constexpr int kHt0Rows = 104;                             // 96 inputs, the ones row, padding
+constexpr int kHtRows = 72;                               // 64 inputs, the ones row, padding
+constexpr int kTrOffHT0 = kTrOffA + kTrainRows * kFeat * 2;  // h0^T: 104 x 128
+constexpr int kTrOffHT1 = kTrOffHT0 + kHt0Rows * kTrainRows * 2;  // h1^T..h3^T: 72 x 128
+constexpr int kTrOffDA = kTrOffHT1 + 3 * kHtRows * kTrainRows * 2;  // da: 128 x 64
+constexpr int kTrOffDAT = kTrOffDA + kTrainRows * kWidth * 2;        // da^T: 64 x 128
+constexpr int kTrOffBias = kTrOffDAT + kWidth * kTrainRows * 2;      // 4 x 64 FP32
+constexpr int kTrOffW5 = kTrOffBias + 4 * 64 * 4;                    // 64 FP32 + b5
+constexpr int kTrOffRed = kTrOffW5 + 64 * 4 + 16;                    // 4 warps x 66 FP32
+constexpr int kTrOffMisc = kTrOffRed + 4 * 66 * 4;                   // mbarrier, TMEM address
+constexpr int kTrainSmem = kTrOffMisc + 16;
+static_assert(kTrainSmem <= 227 * 1024, "training tile exceeds shared memory");
+static_assert(kTrOffA % 1024 == 0 && kTrOffHT0 % 1024 == 0 && kTrOffDA % 1024 == 0 &&
+                  kTrOffDAT % 1024 == 0,
+              "operand alignment");
+// The weight-gradient product reads 128 rows of h_l^T: rows past the
+// buffer's own (padding rows of h0^T, of h3^T) lie inside shared memory.
+static_assert(kTrOffHT1 + 2 * kHtRows * kTrainRows * 2 + kTrainRows * kTrainRows * 2 <= kTrainSmem,
+              "weight-gradient operand stays inside shared memory");
+constexpr int kTrCols = 512;  // 4 x 64 pre-activations, 64 dh, 64 dW^T (+ unused)
+constexpr uint32_t kColDX = 256, kColDW = 320;
+
+// W_l^T (rows = inputs, K = outputs) of a 64 x 64 layer, canonical K-major.
+__device__ __forceinline__ void load_layer_transposed(const float* __restrict__ W,
+                                                      unsigned char* dst)
+{
+    for (int c = threadIdx.x; c < 64 * 64 / 8; c += blockDim.x) {
+        const int i = c / 8, o0 = (c % 8) * 8;  // 8 outputs of input i
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(W + (o0 + j) * 64 + i);
+        *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(i, o0, 64)) =
+            make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                       pack_bf16(v[6], v[7]));
+    }
+}
+
+__device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float v)
+{
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// 64 FP32 columns [col, col + 64) of the calling thread's tensor-memory row.
+__device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&h)[64])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float v[16];
+        tc::tmem_ld16(taddr + 16 * q, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[16 * q + j] = v[j];
+    }
+    tc::tmem_wait_ld();
+}
+
+__global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train_tc(const float* __restrict__ params,
+                                                               const float* __restrict__ x,
+                                                               const float* __restrict__ target,
+                                                               int64_t n,
+                                                               float* __restrict__ partial,
+                                                               float* __restrict__ loss_partial)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* bias = reinterpret_cast<float*>(smem + kTrOffBias);
+    float* w5 = reinterpret_cast<float*>(smem + kTrOffW5);
+    float* red = reinterpret_cast<float*>(smem + kTrOffRed);
+    const uint32_t mbar = tc::smem_addr(smem + kTrOffMisc);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTrOffMisc + 8);
+    unsigned char* A = smem + kTrOffA;
+    unsigned char* DA = smem + kTrOffDA;
+    unsigned char* DAT = smem + kTrOffDAT;
+    auto ht = [&](int l) { return smem + (l == 0 ? kTrOffHT0 : kTrOffHT1 + (l - 1) * kHtRows * kTrainRows * 2); };
+    auto wsm = [&](int l) { return smem + (l == 0 ? kTrOffW0 : kTrOffW1 + (l - 1) * 64 * kWidth * 2); };
+
+    const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
+    load_layer_kmajor<kFeat>(params + w_off(0), smem + kTrOffW0, vec);
+    for (int l = 1; l < 4; ++l) {
+        load_layer_kmajor<kWidth>(params + w_off(l), wsm(l), vec);
+        load_layer_transposed(params + w_off(l), smem + kTrOffWT1 + (l - 1) * 64 * kWidth * 2);
+    }
+    for (int i = tid; i < 4 * 64; i += blockDim.x) bias[i] = params[b_off(i >> 6) + (i & 63)];
+    for (int i = tid; i < 64; i += blockDim.x) w5[i] = params[kW5 + i];
+    // the ones rows (bias gradients) and the padding rows of the transposes
+    for (int i = tid; i < (kHt0Rows - kFeat) * kTrainRows; i += blockDim.x) {
+        const int row = kFeat + i / kTrainRows, r = i % kTrainRows;
+        store_bf16(ht(0), tc::kmajor_offset(row, r, kTrainRows), row == kFeat ? 1.f : 0.f);
+    }
+    for (int l = 1; l < 4; ++l)
+        for (int i = tid; i < (kHtRows - kWidth) * kTrainRows; i += blockDim.x) {
+            const int row = kWidth + i / kTrainRows, r = i % kTrainRows;
+            store_bf16(ht(l), tc::kmajor_offset(row, r, kTrainRows), row == kWidth ? 1.f : 0.f);
+        }
+    if (tid == 0) {
+        w5[64] = params[kB5];
+        tc::mbar_init(mbar, 1);
+    }
+    __syncwarp();
+    if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTrCols);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTrainRows, 64);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    // issue the products of one stage (thread 0), then every thread waits
+    auto run = [&](auto issue) -> bool {
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue();
+            tc::commit(mbar);
+        }
+        const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+        if (__syncthreads_or(!ok)) {
+            if (!ok) tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the products in flight, bounded
+            return false;
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        return true;
+    };
+    auto gemm = [&](uint32_t dcol, const unsigned char* a, int a_k, const unsigned char* b, int b_k,
+                    int K) {
+        const uint32_t ab = tc::smem_addr(a), bb = tc::smem_addr(b);
+        for (int kb = 0; kb < K / 16; ++kb)
+            tc::mma_bf16(tmem + dcol, tc::smem_desc(ab + 256 * kb, 128, a_k * 16),
+                         tc::smem_desc(bb + 256 * kb, 128, b_k * 16), kIdesc, kb > 0);
+    };
+
+    const int64_t row = (int64_t)blockIdx.x * kTrainRows + tid;
+    float y[3];
+    load_point(x, n, row, y);
+    // ---- forward: features -> A and h0^T
+#pragma unroll 1
+    for (int c = 0; c < kFeat / 8; ++c) {
+        float f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = feature(y, 8 * c + j);
+        *reinterpret_cast<uint4*>(A + tc::kmajor_offset(tid, 8 * c, kFeat)) =
+            make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                       pack_bf16(f[6], f[7]));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) store_bf16(ht(0), tc::kmajor_offset(8 * c + j, tid, kTrainRows), f[j]);
+    }
+    float out = 0.f;
+    float h[64];
+    for (int l = 0; l < 4 && !failed; ++l) {
+        const int K = l == 0 ? kFeat : kWidth;
+        if (!run([&] { gemm(64u * l, A, K, wsm(l), K, K); })) {
+            failed = true;
+            break;
+        }
+        tmem_row64(trow + 64u * l, h);
+#pragma unroll
+        for (int j = 0; j < 64; ++j) h[j] = silu(h[j] + bias[64 * l + j]);
+        if (l < 3) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<uint4*>(A + tc::kmajor_offset(tid, 8 * c, kWidth)) =
+                    make_uint4(pack_bf16(h[8 * c], h[8 * c + 1]), pack_bf16(h[8 * c + 2], h[8 * c + 3]),
+                               pack_bf16(h[8 * c + 4], h[8 * c + 5]), pack_bf16(h[8 * c + 6], h[8 * c + 7]));
+#pragma unroll
+            for (int j = 0; j < 64; ++j) store_bf16(ht(l + 1), tc::kmajor_offset(j, tid, kTrainRows), h[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                h[j] = __bfloat162float(__float2bfloat16_rn(h[j]));  // h4 as the layers see it
+                out = fmaf(h[j], w5[j], out);
+            }
+            out += w5[64];
         }
     }
-    __syncthreads();
     float* gpart = partial + (int64_t)blockIdx.x * kParams;
-
-    // output layer: dw5[j] = sum_r dout[r] h4[r][j]; db5 = sum_r dout[r];
-    // da4[r][j] = dout[r] w5[j] silu'(a4[r][j])
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-        float s = 0.f;
-        for (int r = 0; r < kTrainRows; ++r) s += dout[r] * __bfloat162float(act[4][r * kLd + j]);
-        gpart[kW5 + j] = s;
+    if (!failed) {
+        // ---- output layer: dout, dw5, db5, da3
+        const float e = row < n ? out - target[row] : 0.f;
+        const float dout = 2.f * e / (float)n;
+        float le = e * e;
+        for (int o = 16; o > 0; o >>= 1) le += __shfl_xor_sync(kFull, le, o);
+        for (int j = 0; j < 64; ++j) {
+            float v = dout * h[j];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            if (lane == 0) red[warp * 66 + j] = v;
+        }
+        float dsum = dout;
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+        if (lane == 0) {
+            red[warp * 66 + 64] = dsum;
+            red[warp * 66 + 65] = le;
+        }
+        float a[64];
+        tmem_row64(trow + 192u, a);
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            const float d = dout * w5[j] * silu_grad(a[j] + bias[192 + j]);
+            store_bf16(DA, tc::kmajor_offset(tid, j, kWidth), d);
+            store_bf16(DAT, tc::kmajor_offset(j, tid, kTrainRows), d);
+        }
+        __syncthreads();
+        if (tid < 65) {
+            const float v = red[tid] + red[66 + tid] + red[132 + tid] + red[198 + tid];
+            gpart[tid < 64 ? kW5 + tid : kB5] = v;
+        }
+        if (tid == 0) loss_partial[blockIdx.x] = red[65] + red[131] + red[197] + red[263];
+        // ---- layers 3 .. 0: weight gradients, then the previous layer's da
+        for (int l = 3; l >= 0; --l) {
+            const int K = l == 0 ? kFeat : kWidth;
+            if (!run([&] {
+                    gemm(kColDW, ht(l), kTrainRows, DAT, kTrainRows, kTrainRows);
+                    if (l > 0)
+                        gemm(kColDX, DA, kWidth, smem + kTrOffWT1 + (l - 1) * 64 * kWidth * 2, kWidth, kWidth);
+                })) {
+                failed = true;
+                break;
+            }
+            float g[64];
+            tmem_row64(trow + kColDW, g);  // row tid of dW_l^T: input tid, 64 outputs
+            if (tid < K) {
+                for (int o = 0; o < 64; ++o) gpart[w_off(l) + o * K + tid] = g[o];
+            } else if (tid == K) {
+                for (int o = 0; o < 64; ++o) gpart[b_off(l) + o] = g[o];
+            }
+            if (l == 0) break;
+            float dh[64];
+            tmem_row64(trow + kColDX, dh);
+            tmem_row64(trow + 64u * (l - 1), a);
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const float d = dh[j] * silu_grad(a[j] + bias[64 * (l - 1) + j]);
+                store_bf16(DA, tc::kmajor_offset(tid, j, kWidth), d);
+                store_bf16(DAT, tc::kmajor_offset(j, tid, kTrainRows), d);
+            }
+        }
     }
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int r = 0; r < kTrainRows; ++r) s += dout[r];
-        gpart[kB5] = s;
+    if (failed) {  // a wait gave up: this block's gradients and loss are NaN
+        for (int i = tid; i < kParams; i += blockDim.x) gpart[i] = __int_as_float(0x7FC00000);
+        if (tid == 0) loss_partial[blockIdx.x] = __int_as_float(0x7FC00000);
     }
-    for (int i = threadIdx.x; i < kTrainRows * 64; i += blockDim.x) {
-        const int r = i >> 6, j = i & 63;
-        const float v = dout[r] * net.w5[j] * silu_grad(pre[3][r * kLd + j]);
-        da[r * kLd + j] = __float2bfloat16_rn(v);
-    }
+    tc::fence_before_sync();
     __syncthreads();
-
-    for (int l = 3; l >= 0; --l) {
-        const int in = l == 0 ? kFeat : kWidth;
-        const int ld_in = l == 0 ? kLd1 : kLd;
-        const __nv_bfloat16* h_in = act[l];
-        // bias gradient: column sums of da
-        for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-            float s = 0.f;
-            for (int r = 0; r < kTrainRows; ++r) s += __bfloat162float(da[r * kLd + j]);
-            gpart[b_off(l) + j] = s;
-        }
-        // dW[o][i] = sum_r da[r][o] h[r][i]: warp w owns outputs 16w..16w+15
-        {
-            const int m0 = warp * 16;
-            const int n_tiles = in / 8;
-            float C[12][4];
-            for (int nt = 0; nt < n_tiles; ++nt)
-                for (int i = 0; i < 4; ++i) C[nt][i] = 0.f;
-            for (int kb = 0; kb < kTrainRows / 16; ++kb) {
-                uint32_t A[4];
-                {
-                    const int mat = lane >> 3, j = lane & 7;
-                    const int k = kb * 16 + (mat >> 1) * 8 + j;
-                    const int m = m0 + (mat & 1) * 8;
-                    ldmatrix_x4_trans(A, da + k * kLd + m);
-                }
-                for (int nt = 0; nt < n_tiles; nt += 2) {
-                    uint32_t B[4];
-                    const int mat = lane >> 3, j = lane & 7;
-                    const int k = kb * 16 + (mat & 1) * 8 + j;
-                    const int ncol = (nt + (mat >> 1)) * 8;
-                    ldmatrix_x4_trans(B, h_in + k * ld_in + ncol);
-                    mma_bf16(C[nt], A, B[0], B[1]);
-                    mma_bf16(C[nt + 1], A, B[2], B[3]);
-                }
-            }
-            for (int nt = 0; nt < n_tiles; ++nt) {
-                const int col = nt * 8 + 2 * t;
-                gpart[w_off(l) + (m0 + g) * in + col] = C[nt][0];
-                gpart[w_off(l) + (m0 + g) * in + col + 1] = C[nt][1];
-                gpart[w_off(l) + (m0 + g + 8) * in + col] = C[nt][2];
-                gpart[w_off(l) + (m0 + g + 8) * in + col + 1] = C[nt][3];
-            }
-        }
-        if (l == 0) break;
-        __syncthreads();
-        // dh_{l-1}[r][i] = sum_o da[r][o] W[o][i]; da_{l-1} = dh * silu'(a_{l-1})
-        {
-            float C[8][4];
-            for (int nt = 0; nt < 8; ++nt)
-                for (int i = 0; i < 4; ++i) C[nt][i] = 0.f;
-            for (int kb = 0; kb < 4; ++kb) {
-                uint32_t A[4];
-                const int c = 16 * kb + 2 * t;
-                A[0] = *reinterpret_cast<const uint32_t*>(da + (row0 + g) * kLd + c);
-                A[1] = *reinterpret_cast<const uint32_t*>(da + (row0 + g + 8) * kLd + c);
-                A[2] = *reinterpret_cast<const uint32_t*>(da + (row0 + g) * kLd + c + 8);
-                A[3] = *reinterpret_cast<const uint32_t*>(da + (row0 + g + 8) * kLd + c + 8);
-                for (int nt = 0; nt < 8; ++nt) {
-                    // B[k = o][n = i] = W[o][i]: stored transposed as w[i][o]
-                    const __nv_bfloat16* brow = net.w[l] + (nt * 8 + g) * kLd + 16 * kb + 2 * t;
-                    mma_bf16(C[nt], A, *reinterpret_cast<const uint32_t*>(brow),
-                             *reinterpret_cast<const uint32_t*>(brow + 8));
-                }
-            }
-            __syncthreads();  // every warp has read da
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = nt * 8 + 2 * t;
-                const float* a = pre[l - 1];
-                da[(row0 + g) * kLd + col] = __float2bfloat16_rn(C[nt][0] * silu_grad(a[(row0 + g) * kLd + col]));
-                da[(row0 + g) * kLd + col + 1] = __float2bfloat16_rn(C[nt][1] * silu_grad(a[(row0 + g) * kLd + col + 1]));
-                da[(row0 + g + 8) * kLd + col] = __float2bfloat16_rn(C[nt][2] * silu_grad(a[(row0 + g + 8) * kLd + col]));
-                da[(row0 + g + 8) * kLd + col + 1] = __float2bfloat16_rn(C[nt][3] * silu_grad(a[(row0 + g + 8) * kLd + col + 1]));
-            }
-        }
-        __syncthreads();
-    }
+    if (warp == 0) tc::tmem_free(tmem, kTrCols);
 }
 
 // Sum the per-block partial gradients in block order, then one Adam step
@@ -520,10 +564,10 @@ int mlp_forward(const float* params, const float* x, int64_t n, float* out, cuda
                 int stride)
 {
     if (n <= 0) return WOB_OK;
-    WOB_TRY(allow_smem(g_fwd_configured, (const void*)k_mlp_forward, kFwdSmem));
-    const int64_t tiles = (n + 15) / 16;
-    const int grid = grid_for((const void*)k_mlp_forward, 128, kFwdSmem, tiles * 32);
-    k_mlp_forward<<<grid, 128, kFwdSmem, s>>>(params, x, stride, n, out);
+    WOB_TRY(allow_smem(g_fwd_configured, (const void*)k_mlp_forward_tc, kTcFwdSmem));
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    const int grid = grid_for((const void*)k_mlp_forward_tc, kTcRows, kTcFwdSmem, tiles * kTcRows);
+    k_mlp_forward_tc<<<grid, kTcRows, kTcFwdSmem, s>>>(params, x, stride, n, out);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
@@ -539,12 +583,11 @@ int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const f
                       cudaStream_t s)
 {
     if (n <= 0) return WOB_OK;
-    WOB_TRY(allow_smem(g_train_configured, (const void*)k_mlp_train, kTrainSmem));
+    WOB_TRY(allow_smem(g_train_configured, (const void*)k_mlp_train_tc, kTrainSmem));
     const int blocks = (int)((n + kTrainRows - 1) / kTrainRows);
     float* partial = ws;
     float* lp = ws + (int64_t)blocks * kParams;
-    WOB_CUDA_TRY(cudaMemsetAsync(lp, 0, blocks * sizeof(float), s));
-    k_mlp_train<<<blocks, 128, kTrainSmem, s>>>(params, x, target, n, partial, lp);
+    k_mlp_train_tc<<<blocks, kTrainRows, kTrainSmem, s>>>(params, x, target, n, partial, lp);
     WOB_CUDA_TRY(cudaGetLastError());
     k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out, lr,
                                                      0.9f, 0.999f, 1e-8f, step);

@@ -48,10 +48,16 @@ def test_mlp_forward_matches_oracle(wob):
     got = wob.mlp_forward(flat, y).cpu().numpy()
     ref, _ = C.mlp_forward(params, y.astype(np.float64))
     assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), np.abs(got - ref).max()
-    # ragged tail: sizes that are not multiples of the 16-row tile
-    for n in (1, 15, 17, 33):
+    # ragged tails of the 128-row tensor-core tile, and more tiles than CTAs
+    for n in (1, 127, 129, 257, 2999):
         g = wob.mlp_forward(flat, y[:n]).cpu().numpy()
         assert np.allclose(g, got[:n], rtol=0, atol=1e-6)
+    big = _sphere_points(200_000, 9)
+    gb = wob.mlp_forward(flat, big).cpu().numpy()
+    rb, _ = C.mlp_forward(params, big[:5000].astype(np.float64))
+    assert np.abs(gb[:5000] - rb).max() <= 2e-2 * np.abs(rb).max()
+    assert np.allclose(gb[-1000:], wob.mlp_forward(flat, big[-1000:]).cpu().numpy(), rtol=0,
+                       atol=1e-6)
 
 
 def test_mlp_init_matches_oracle(wob):
