@@ -65,29 +65,34 @@ __device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// Forward on the 5th-generation tensor cores (tcgen05): a CTA of 128 threads
-// takes tiles of 128 points; thread t owns row t of the tile.  Per tile the
-// features (BF16) go to shared memory in the canonical K-major layout (the
-// A operand), one thread issues the layer's tcgen05.mma (M 128, N 64, K 16
-// per instruction) into a 64-column FP32 accumulator in tensor memory, the
-// commit arrives on an mbarrier, every thread loads its row of the
-// accumulator (tcgen05.ld), adds the bias, applies SiLU and writes the BF16
-// activations back as the next layer's A operand.  The weights (B operand,
-// W as stored: out x in = N x K, K-major) stay in shared memory for the
-// whole launch.  The 64 -> 1 output layer runs in FP32 per thread on the
+// Forward on the 5th-generation tensor cores (tcgen05).  A CTA of 256
+// threads is two independent halves of 128 threads; each half takes tiles of
+// 128 points in turn (thread t of the half owns row t), so that one half's
+// products run on the tensor cores while the other converts and activates.
+// Per tile the features (BF16) go to the half's A buffer in the canonical
+// K-major layout, one thread issues the layer's tcgen05.mma (M 128, N 64,
+// K 16 per instruction) into the half's 64 FP32 columns of tensor memory,
+// the commit arrives on the half's mbarrier, every thread loads its row of
+// the accumulator (tcgen05.ld), adds the bias, applies SiLU and writes the
+// BF16 activations back as the next layer's A operand.  The weights (B
+// operand, W as stored: out x in = N x K, K-major) stay in shared memory for
+// the whole launch.  The 64 -> 1 output layer runs in FP32 per thread on the
 // BF16-rounded activations, as the tensor cores would see them.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
-constexpr int kTcCols = 64;                          // tensor-memory columns per CTA
+constexpr int kTcThreads = 2 * kTcRows;              // two halves
+constexpr int kTcCols = 128;                         // tensor-memory columns per CTA (64 per half)
 constexpr int kTcOffW0 = 0;                          // 64 x 96 BF16, canonical K-major
-constexpr int kTcOffW1 = kTcOffW0 + 64 * kFeat * 2;  // W1..W3: 64 x 64 each
-constexpr int kTcOffA = kTcOffW1 + 3 * 64 * kWidth * 2;  // 128 x 96 BF16 (layers 1-3: 128 x 64)
-constexpr int kTcOffBias = kTcOffA + kTcRows * kFeat * 2;  // 4 x 64 FP32
-constexpr int kTcOffW5 = kTcOffBias + 4 * 64 * 4;          // 64 FP32, then b5
-constexpr int kTcOffMisc = kTcOffW5 + 64 * 4 + 16;         // mbarrier (8 B), TMEM address (4 B)
-constexpr int kTcFwdSmem = kTcOffMisc + 16;
+constexpr int kTcOffW1 = kTcOffW0 + 64 * kFeat * 2;  // W1..W3: 64 x 64
+constexpr int kTcOffA = kTcOffW1 + 3 * 64 * kWidth * 2;  // per half 128 x 96 BF16 (layers 1-3: 128 x 64)
+constexpr int kTcABytes = kTcRows * kFeat * 2;
+constexpr int kTcOffBias = kTcOffA + 2 * kTcABytes;       // 4 x 64 FP32
+constexpr int kTcOffW5 = kTcOffBias + 4 * 64 * 4;         // 64 FP32, then b5
+constexpr int kTcOffMisc = kTcOffW5 + 64 * 4 + 16;        // 2 mbarriers (8 B each), TMEM address
+constexpr int kTcFwdSmem = kTcOffMisc + 32;
 constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before giving up (seconds)
-static_assert(kTcOffA % 1024 == 0 && kTcOffW1 % 1024 == 0, "operand alignment");
+static_assert(kTcOffA % 1024 == 0 && kTcOffW1 % 1024 == 0 && kTcABytes % 1024 == 0,
+              "operand alignment");
 
 // One layer's matrix (64 x IN, row-major FP32 in params) into shared memory
 // as BF16 in the canonical K-major layout (rows = outputs, K = inputs).
@@ -113,45 +118,46 @@ __device__ __forceinline__ void load_layer_kmajor(const float* __restrict__ W, u
     }
 }
 
-__global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restrict__ params,
-                                                           const float* __restrict__ x,
-                                                           int stride, int64_t n,
-                                                           float* __restrict__ out)
+__global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const float* __restrict__ params,
+                                                              const float* __restrict__ x,
+                                                              int stride, int64_t n,
+                                                              float* __restrict__ out)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int half = threadIdx.x >> 7, tid = threadIdx.x & 127, warp = threadIdx.x >> 5;
     float* bias = reinterpret_cast<float*>(smem + kTcOffBias);
     float* w5 = reinterpret_cast<float*>(smem + kTcOffW5);
-    const uint32_t mbar = tc::smem_addr(smem + kTcOffMisc);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcOffMisc + 8);
+    const uint32_t mbar = tc::smem_addr(smem + kTcOffMisc + 8 * half);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcOffMisc + 16);
+    unsigned char* A = smem + kTcOffA + half * kTcABytes;
 
-    // the network into shared memory, the accumulator into tensor memory
+    // the network into shared memory, the accumulators into tensor memory
     const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
     load_layer_kmajor<kFeat>(params + w_off(0), smem + kTcOffW0, vec);
     for (int l = 1; l < 4; ++l)
         load_layer_kmajor<kWidth>(params + w_off(l), smem + kTcOffW1 + (l - 1) * 64 * kWidth * 2,
                                   vec);
-    for (int i = tid; i < 4 * 64; i += blockDim.x) bias[i] = params[b_off(i >> 6) + (i & 63)];
-    for (int i = tid; i < 64; i += blockDim.x) w5[i] = params[kW5 + i];
-    if (tid == 0) {
-        w5[64] = params[kB5];
-        tc::mbar_init(mbar, 1);
-    }
+    for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) bias[i] = params[b_off(i >> 6) + (i & 63)];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) w5[i] = params[kW5 + i];
+    if (threadIdx.x == 0) w5[64] = params[kB5];
+    if (tid == 0) tc::mbar_init(mbar, 1);
     __syncwarp();
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTcCols);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tslot;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's lanes
+    const uint32_t tmem = *tslot + 64u * half;                 // this half's columns
+    const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
     constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTcRows, 64);
-    const uint32_t a_base = tc::smem_addr(smem + kTcOffA);
+    const uint32_t a_base = tc::smem_addr(A);
+    const int bar = 1 + half;  // the half's named barrier
     uint32_t phase = 0;
     bool failed = false;
 
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
-    for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+    for (int64_t tile = 2 * (int64_t)blockIdx.x + half; tile < tiles && !failed;
+         tile += 2 * (int64_t)gridDim.x) {
         const int64_t r = tile * kTcRows + tid;
         float y[3];
         load_point(x, n, r, y, stride);
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restr
             float f[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) f[j] = feature(y, 8 * c + j);
-            *reinterpret_cast<uint4*>(smem + kTcOffA + tc::kmajor_offset(tid, 8 * c, kFeat)) =
+            *reinterpret_cast<uint4*>(A + tc::kmajor_offset(tid, 8 * c, kFeat)) =
                 make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
                            pack_bf16(f[6], f[7]));
         }
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restr
             const int K = l == 0 ? kFeat : kWidth;
             tc::fence_proxy_async();
             tc::fence_before_sync();
-            __syncthreads();
+            tc::bar_sync(bar, kTcRows);
             if (tid == 0) {
                 tc::fence_after_sync();
                 const uint32_t b_base =
@@ -181,10 +187,9 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restr
                 tc::commit(mbar);
             }
             const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
-            if (__syncthreads_or(!ok)) {  // block-uniform: every thread stops together
+            if (tc::bar_sync_or(bar, kTcRows, !ok)) {  // the half stops together
                 failed = true;
-                if (ok) break;
-                tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the product in flight, bounded
+                if (!ok) tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the product in flight, bounded
                 break;
             }
             phase ^= 1u;
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restr
             if (l < 3) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    *reinterpret_cast<uint4*>(smem + kTcOffA + tc::kmajor_offset(tid, 8 * c, kWidth)) =
+                    *reinterpret_cast<uint4*>(A + tc::kmajor_offset(tid, 8 * c, kWidth)) =
                         make_uint4(pack_bf16(h[8 * c], h[8 * c + 1]), pack_bf16(h[8 * c + 2], h[8 * c + 3]),
                                    pack_bf16(h[8 * c + 4], h[8 * c + 5]),
                                    pack_bf16(h[8 * c + 6], h[8 * c + 7]));
@@ -218,75 +223,55 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(const float* __restr
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, kTcCols);
+    if (warp == 0) tc::tmem_free(*tslot, kTcCols);
 }
 
 // ---------------------------------------------------------------------------
 // Training step on the tensor cores: forward and backward of 128 rows per
-// CTA (thread t owns row t), per-CTA partial gradients (summed in a fixed
-// order by k_mlp_adam).  Every product is a tcgen05.mma of M 128 with the
-// accumulator in tensor memory:
-//   forward    a_l = h_l W_l^T          (A = h_l [rows x in], B = W_l)
-//   weights    dW_l^T = h_l^T da_l      (A = h_l^T [in x rows], B = da_l^T)
-//   inputs     dh_l = da_l W_l          (A = da_l [rows x 64], B = W_l^T)
-// The pre-activations of the four hidden layers stay in tensor memory
-// (columns 64 l .. 64 l + 63) until the backward pass reads them; h_l^T
-// carries a row of ones after its K_l inputs, so row K_l of dW_l^T is the
-// bias gradient.  Operands are BF16 in the canonical K-major layout, the
-// transposes written by the threads that own the rows.
+// CTA, per-CTA partial gradients (summed in a fixed order by k_mlp_adam).
+// 256 threads: thread (w, lane) owns row 32 (w % 4) + lane and the columns
+// [32 (w / 4), 32 (w / 4) + 32) of every 64-wide layer.  Every product is a
+// tcgen05.mma of M 128 with the accumulator in tensor memory:
+//   forward   a_l = h_l W_l^T         A = h_l (K-major), B = W_l (K-major)
+//   weights   dW_l^T = h_l^T da_l     A = h_l read MN-major, B = da_l read MN-major
+//   inputs    dh_l = da_l W_l          A = da_l (K-major), B = W_l read MN-major
+// so no operand is ever transposed: the MN-major reads see the same bytes.
+// The pre-activations of the hidden layers stay in tensor memory (columns
+// 64 l .. 64 l + 63) until the backward pass needs them; every h_l carries a
+// column of ones after its K_l inputs, so row K_l of dW_l^T is the bias
+// gradient.
 // ---------------------------------------------------------------------------
 constexpr int kTrainRows = 128;
-constexpr int kTrOffW0 = 0;                               // W0: 64 x 96
-constexpr int kTrOffW1 = kTrOffW0 + 64 * kFeat * 2;       // W1..W3: 64 x 64
-constexpr int kTrOffWT1 = kTrOffW1 + 3 * 64 * kWidth * 2;  // W1^T..W3^T: 64 (in) x 64 (out)
-constexpr int kTrOffA = kTrOffWT1 + 3 * 64 * kWidth * 2;   // forward A: 128 x 96
-constexpr int kHt0Rows = 104;                             // 96 inputs, the ones row, padding
-constexpr int kHtRows = 72;                               // 64 inputs, the ones row, padding
-constexpr int kTrOffHT0 = kTrOffA + kTrainRows * kFeat * 2;  // h0^T: 104 x 128
-constexpr int kTrOffHT1 = kTrOffHT0 + kHt0Rows * kTrainRows * 2;  // h1^T..h3^T: 72 x 128
-constexpr int kTrOffDA = kTrOffHT1 + 3 * kHtRows * kTrainRows * 2;  // da: 128 x 64
-constexpr int kTrOffDAT = kTrOffDA + kTrainRows * kWidth * 2;        // da^T: 64 x 128
-constexpr int kTrOffBias = kTrOffDAT + kWidth * kTrainRows * 2;      // 4 x 64 FP32
-constexpr int kTrOffW5 = kTrOffBias + 4 * 64 * 4;                    // 64 FP32 + b5
-constexpr int kTrOffRed = kTrOffW5 + 64 * 4 + 16;                    // 4 warps x 66 FP32
-constexpr int kTrOffMisc = kTrOffRed + 4 * 66 * 4;                   // mbarrier, TMEM address
-constexpr int kTrainSmem = kTrOffMisc + 16;
+constexpr int kTrThreads = 2 * kTrainRows;
+constexpr int kH0Cols = kFeat + 8;   // 96 inputs, the ones column, padding
+constexpr int kHCols = kWidth + 8;   // 64 inputs, the ones column, padding
+constexpr int kTrOffW0 = 0;                                // W0: 64 x 96
+constexpr int kTrOffW1 = kTrOffW0 + 64 * kFeat * 2;        // W1..W3: 64 x 64
+constexpr int kTrOffH0 = kTrOffW1 + 3 * 64 * kWidth * 2;   // h0: 128 x 104
+constexpr int kTrOffH1 = kTrOffH0 + 27 * 1024;             // h1..h3: 128 x 72 (18 KB each)
+constexpr int kTrOffDA = kTrOffH1 + 3 * kTrainRows * kHCols * 2;  // da: 128 x 64
+constexpr int kTrOffBias = kTrOffDA + kTrainRows * kWidth * 2;    // 4 x 64 FP32
+constexpr int kTrOffW5 = kTrOffBias + 4 * 64 * 4;                 // 64 FP32 + b5
+constexpr int kTrOffRed = kTrOffW5 + 64 * 4 + 16;                 // reductions across warps
+constexpr int kTrRedFloats = 8 * 34 + 2 * 128;
+constexpr int kTrOffMisc = kTrOffRed + kTrRedFloats * 4;          // mbarrier, TMEM address
+// Slack after the last operand: the products read up to 128 MN-major rows
+// of an h_l whose own buffer has fewer, and the slack keeps every operand
+// read inside the block's shared memory.
+constexpr int kTrainSmem = kTrOffMisc + 16 + 32 * 1024;
+static_assert(kTrainRows * kH0Cols * 2 <= 27 * 1024, "h0 buffer");
 static_assert(kTrainSmem <= 227 * 1024, "training tile exceeds shared memory");
-static_assert(kTrOffA % 1024 == 0 && kTrOffHT0 % 1024 == 0 && kTrOffDA % 1024 == 0 &&
-                  kTrOffDAT % 1024 == 0,
+static_assert(kTrOffH0 % 1024 == 0 && kTrOffH1 % 1024 == 0 && kTrOffDA % 1024 == 0,
               "operand alignment");
-// The weight-gradient product reads 128 rows of h_l^T: rows past the
-// buffer's own (padding rows of h0^T, of h3^T) lie inside shared memory.
-static_assert(kTrOffHT1 + 2 * kHtRows * kTrainRows * 2 + kTrainRows * kTrainRows * 2 <= kTrainSmem,
-              "weight-gradient operand stays inside shared memory");
 constexpr int kTrCols = 512;  // 4 x 64 pre-activations, 64 dh, 64 dW^T (+ unused)
 constexpr uint32_t kColDX = 256, kColDW = 320;
+constexpr int kSboH0 = kH0Cols * 16, kSboH = kHCols * 16, kSboDA = kWidth * 16;
 
-// W_l^T (rows = inputs, K = outputs) of a 64 x 64 layer, canonical K-major.
-__device__ __forceinline__ void load_layer_transposed(const float* __restrict__ W,
-                                                      unsigned char* dst)
-{
-    for (int c = threadIdx.x; c < 64 * 64 / 8; c += blockDim.x) {
-        const int i = c / 8, o0 = (c % 8) * 8;  // 8 outputs of input i
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __ldg(W + (o0 + j) * 64 + i);
-        *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(i, o0, 64)) =
-            make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                       pack_bf16(v[6], v[7]));
-    }
-}
-
-__device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float v)
-{
-    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
-}
-
-// 64 FP32 columns [col, col + 64) of the calling thread's tensor-memory row.
-__device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&h)[64])
+// 32 FP32 columns [col, col + 32) of the calling thread's tensor-memory row.
+__device__ __forceinline__ void tmem_row32(uint32_t taddr, float (&h)[32])
 {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
         float v[16];
         tc::tmem_ld16(taddr + 16 * q, v);
 #pragma unroll
@@ -295,7 +280,19 @@ __device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&h)[64])
     tc::tmem_wait_ld();
 }
 
-__global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train_tc(const float* __restrict__ params,
+// 32 values of row r, columns [c0, c0 + 32), into a K-major BF16 matrix with
+// `cols` columns (four 16-byte stores).
+__device__ __forceinline__ void store_row32(unsigned char* base, int r, int c0, int cols,
+                                            const float (&v)[32])
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(base + tc::kmajor_offset(r, c0 + 8 * c, cols)) =
+            make_uint4(pack_bf16(v[8 * c], v[8 * c + 1]), pack_bf16(v[8 * c + 2], v[8 * c + 3]),
+                       pack_bf16(v[8 * c + 4], v[8 * c + 5]), pack_bf16(v[8 * c + 6], v[8 * c + 7]));
+}
+
+__global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const float* __restrict__ params,
                                                                const float* __restrict__ x,
                                                                const float* __restrict__ target,
                                                                int64_t n,
@@ -303,37 +300,32 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train_tc(const float* __r
                                                                float* __restrict__ loss_partial)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = 32 * (warp & 3) + lane;  // the row this thread owns
+    const int ch = warp >> 2;              // its half of the columns
+    const int c0 = 32 * ch;
     float* bias = reinterpret_cast<float*>(smem + kTrOffBias);
     float* w5 = reinterpret_cast<float*>(smem + kTrOffW5);
     float* red = reinterpret_cast<float*>(smem + kTrOffRed);
     const uint32_t mbar = tc::smem_addr(smem + kTrOffMisc);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTrOffMisc + 8);
-    unsigned char* A = smem + kTrOffA;
     unsigned char* DA = smem + kTrOffDA;
-    unsigned char* DAT = smem + kTrOffDAT;
-    auto ht = [&](int l) { return smem + (l == 0 ? kTrOffHT0 : kTrOffHT1 + (l - 1) * kHtRows * kTrainRows * 2); };
-    auto wsm = [&](int l) { return smem + (l == 0 ? kTrOffW0 : kTrOffW1 + (l - 1) * 64 * kWidth * 2); };
+    auto hb = [&](int l) { return smem + (l == 0 ? kTrOffH0 : kTrOffH1 + (l - 1) * kTrainRows * kHCols * 2); };
+    auto wb = [&](int l) { return smem + (l == 0 ? kTrOffW0 : kTrOffW1 + (l - 1) * 64 * kWidth * 2); };
 
     const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
-    load_layer_kmajor<kFeat>(params + w_off(0), smem + kTrOffW0, vec);
-    for (int l = 1; l < 4; ++l) {
-        load_layer_kmajor<kWidth>(params + w_off(l), wsm(l), vec);
-        load_layer_transposed(params + w_off(l), smem + kTrOffWT1 + (l - 1) * 64 * kWidth * 2);
+    load_layer_kmajor<kFeat>(params + w_off(0), wb(0), vec);
+    for (int l = 1; l < 4; ++l) load_layer_kmajor<kWidth>(params + w_off(l), wb(l), vec);
+    for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) bias[i] = params[b_off(i >> 6) + (i & 63)];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) w5[i] = params[kW5 + i];
+    // the ones column (bias gradients) and the padding of every h_l
+    if (ch == 0) {
+        const uint4 ones = make_uint4(pack_bf16(1.f, 0.f), 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(hb(0) + tc::kmajor_offset(r, kFeat, kH0Cols)) = ones;
+        for (int l = 1; l < 4; ++l)
+            *reinterpret_cast<uint4*>(hb(l) + tc::kmajor_offset(r, kWidth, kHCols)) = ones;
     }
-    for (int i = tid; i < 4 * 64; i += blockDim.x) bias[i] = params[b_off(i >> 6) + (i & 63)];
-    for (int i = tid; i < 64; i += blockDim.x) w5[i] = params[kW5 + i];
-    // the ones rows (bias gradients) and the padding rows of the transposes
-    for (int i = tid; i < (kHt0Rows - kFeat) * kTrainRows; i += blockDim.x) {
-        const int row = kFeat + i / kTrainRows, r = i % kTrainRows;
-        store_bf16(ht(0), tc::kmajor_offset(row, r, kTrainRows), row == kFeat ? 1.f : 0.f);
-    }
-    for (int l = 1; l < 4; ++l)
-        for (int i = tid; i < (kHtRows - kWidth) * kTrainRows; i += blockDim.x) {
-            const int row = kWidth + i / kTrainRows, r = i % kTrainRows;
-            store_bf16(ht(l), tc::kmajor_offset(row, r, kTrainRows), row == kWidth ? 1.f : 0.f);
-        }
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         w5[64] = params[kB5];
         tc::mbar_init(mbar, 1);
     }
@@ -344,8 +336,10 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train_tc(const float* __r
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTrainRows, 64);
+    const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+    constexpr uint32_t kIdFwd = tc::idesc_bf16_f32(kTrainRows, 64);
+    constexpr uint32_t kIdDW = tc::idesc_bf16_f32(kTrainRows, 64, true, true);
+    constexpr uint32_t kIdDX = tc::idesc_bf16_f32(kTrainRows, 64, false, true);
     uint32_t phase = 0;
     bool failed = false;
 
@@ -354,7 +348,7 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train_tc(const float* __r
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
             tc::fence_after_sync();
             issue();
             tc::commit(mbar);
@@ -368,122 +362,124 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train_tc(const float* __r
         tc::fence_after_sync();
         return true;
     };
-    auto gemm = [&](uint32_t dcol, const unsigned char* a, int a_k, const unsigned char* b, int b_k,
-                    int K) {
-        const uint32_t ab = tc::smem_addr(a), bb = tc::smem_addr(b);
-        for (int kb = 0; kb < K / 16; ++kb)
-            tc::mma_bf16(tmem + dcol, tc::smem_desc(ab + 256 * kb, 128, a_k * 16),
-                         tc::smem_desc(bb + 256 * kb, 128, b_k * 16), kIdesc, kb > 0);
-    };
-
-    const int64_t row = (int64_t)blockIdx.x * kTrainRows + tid;
+    const int64_t row = (int64_t)blockIdx.x * kTrainRows + r;
     float y[3];
     load_point(x, n, row, y);
-    // ---- forward: features -> A and h0^T
+    // ---- forward: features -> h0 (this thread's 48 of the 96)
 #pragma unroll 1
-    for (int c = 0; c < kFeat / 8; ++c) {
+    for (int c = 6 * ch; c < 6 * ch + 6; ++c) {
         float f[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) f[j] = feature(y, 8 * c + j);
-        *reinterpret_cast<uint4*>(A + tc::kmajor_offset(tid, 8 * c, kFeat)) =
+        *reinterpret_cast<uint4*>(hb(0) + tc::kmajor_offset(r, 8 * c, kH0Cols)) =
             make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
                        pack_bf16(f[6], f[7]));
-#pragma unroll
-        for (int j = 0; j < 8; ++j) store_bf16(ht(0), tc::kmajor_offset(8 * c + j, tid, kTrainRows), f[j]);
     }
+    float h[32];
     float out = 0.f;
-    float h[64];
-    for (int l = 0; l < 4 && !failed; ++l) {
+    for (int l = 0; l < 4; ++l) {
         const int K = l == 0 ? kFeat : kWidth;
-        if (!run([&] { gemm(64u * l, A, K, wsm(l), K, K); })) {
+        const int sbo = l == 0 ? kSboH0 : kSboH;
+        if (!run([&] {
+                const uint32_t ab = tc::smem_addr(hb(l)), bb = tc::smem_addr(wb(l));
+                for (int kb = 0; kb < K / 16; ++kb)
+                    tc::mma_bf16(tmem + 64u * l, tc::smem_desc(ab + 256 * kb, 128, sbo),
+                                 tc::smem_desc(bb + 256 * kb, 128, K * 16), kIdFwd, kb > 0);
+            })) {
             failed = true;
             break;
         }
-        tmem_row64(trow + 64u * l, h);
+        tmem_row32(trow + 64u * l, h);
 #pragma unroll
-        for (int j = 0; j < 64; ++j) h[j] = silu(h[j] + bias[64 * l + j]);
+        for (int j = 0; j < 32; ++j) h[j] = silu(h[j] + bias[64 * l + c0 + j]);
         if (l < 3) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                *reinterpret_cast<uint4*>(A + tc::kmajor_offset(tid, 8 * c, kWidth)) =
-                    make_uint4(pack_bf16(h[8 * c], h[8 * c + 1]), pack_bf16(h[8 * c + 2], h[8 * c + 3]),
-                               pack_bf16(h[8 * c + 4], h[8 * c + 5]), pack_bf16(h[8 * c + 6], h[8 * c + 7]));
-#pragma unroll
-            for (int j = 0; j < 64; ++j) store_bf16(ht(l + 1), tc::kmajor_offset(j, tid, kTrainRows), h[j]);
+            store_row32(hb(l + 1), r, c0, kHCols, h);
         } else {
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
+            for (int j = 0; j < 32; ++j) {
                 h[j] = __bfloat162float(__float2bfloat16_rn(h[j]));  // h4 as the layers see it
-                out = fmaf(h[j], w5[j], out);
+                out = fmaf(h[j], w5[c0 + j], out);
             }
-            out += w5[64];
         }
     }
     float* gpart = partial + (int64_t)blockIdx.x * kParams;
+    float* outs = red + 8 * 34;  // per row: the two column halves of the output
     if (!failed) {
         // ---- output layer: dout, dw5, db5, da3
-        const float e = row < n ? out - target[row] : 0.f;
-        const float dout = 2.f * e / (float)n;
-        float le = e * e;
-        for (int o = 16; o > 0; o >>= 1) le += __shfl_xor_sync(kFull, le, o);
-        for (int j = 0; j < 64; ++j) {
-            float v = dout * h[j];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0) red[warp * 66 + j] = v;
-        }
-        float dsum = dout;
-        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-        if (lane == 0) {
-            red[warp * 66 + 64] = dsum;
-            red[warp * 66 + 65] = le;
-        }
-        float a[64];
-        tmem_row64(trow + 192u, a);
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            const float d = dout * w5[j] * silu_grad(a[j] + bias[192 + j]);
-            store_bf16(DA, tc::kmajor_offset(tid, j, kWidth), d);
-            store_bf16(DAT, tc::kmajor_offset(j, tid, kTrainRows), d);
-        }
+        outs[ch * 128 + r] = out;
         __syncthreads();
-        if (tid < 65) {
-            const float v = red[tid] + red[66 + tid] + red[132 + tid] + red[198 + tid];
-            gpart[tid < 64 ? kW5 + tid : kB5] = v;
+        const float o = outs[r] + outs[128 + r] + w5[64];
+        const float e = row < n ? o - target[row] : 0.f;
+        const float dout = 2.f * e / (float)n;
+#pragma unroll 1
+        for (int j = 0; j < 32; ++j) {
+            float v = dout * h[j];
+            for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(kFull, v, s);
+            if (lane == 0) red[warp * 34 + j] = v;
         }
-        if (tid == 0) loss_partial[blockIdx.x] = red[65] + red[131] + red[197] + red[263];
+        float dsum = dout, le = e * e;
+        for (int s = 16; s > 0; s >>= 1) {
+            dsum += __shfl_xor_sync(kFull, dsum, s);
+            le += __shfl_xor_sync(kFull, le, s);
+        }
+        if (lane == 0) {
+            red[warp * 34 + 32] = dsum;
+            red[warp * 34 + 33] = le;
+        }
+        float a[32];
+        tmem_row32(trow + 192u, a);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = dout * w5[c0 + j] * silu_grad(a[j] + bias[192 + c0 + j]);
+        store_row32(DA, r, c0, kWidth, h);
+        __syncthreads();
+        if (threadIdx.x < 64) {  // w5 column j: warps 0-3 (j < 32) or 4-7
+            const int j = threadIdx.x, w0 = (j >> 5) * 4, jj = j & 31;
+            gpart[kW5 + j] = ((red[w0 * 34 + jj] + red[(w0 + 1) * 34 + jj]) +
+                              red[(w0 + 2) * 34 + jj]) + red[(w0 + 3) * 34 + jj];
+        } else if (threadIdx.x == 64) {
+            gpart[kB5] = ((red[32] + red[34 + 32]) + red[68 + 32]) + red[102 + 32];
+            loss_partial[blockIdx.x] = ((red[33] + red[34 + 33]) + red[68 + 33]) + red[102 + 33];
+        }
         // ---- layers 3 .. 0: weight gradients, then the previous layer's da
         for (int l = 3; l >= 0; --l) {
             const int K = l == 0 ? kFeat : kWidth;
+            const int sbo = l == 0 ? kSboH0 : kSboH;
             if (!run([&] {
-                    gemm(kColDW, ht(l), kTrainRows, DAT, kTrainRows, kTrainRows);
-                    if (l > 0)
-                        gemm(kColDX, DA, kWidth, smem + kTrOffWT1 + (l - 1) * 64 * kWidth * 2, kWidth, kWidth);
+                    const uint32_t hbase = tc::smem_addr(hb(l)), dbase = tc::smem_addr(DA);
+                    for (int kb = 0; kb < kTrainRows / 16; ++kb)
+                        tc::mma_bf16(tmem + kColDW, tc::smem_desc(hbase + 2 * sbo * kb, sbo, 128),
+                                     tc::smem_desc(dbase + 2 * kSboDA * kb, kSboDA, 128), kIdDW,
+                                     kb > 0);
+                    if (l > 0) {
+                        const uint32_t wbase = tc::smem_addr(wb(l));
+                        for (int kb = 0; kb < kWidth / 16; ++kb)
+                            tc::mma_bf16(tmem + kColDX, tc::smem_desc(dbase + 256 * kb, 128, kSboDA),
+                                         tc::smem_desc(wbase + 2 * (kWidth * 16) * kb, kWidth * 16, 128),
+                                         kIdDX, kb > 0);
+                    }
                 })) {
                 failed = true;
                 break;
             }
-            float g[64];
-            tmem_row64(trow + kColDW, g);  // row tid of dW_l^T: input tid, 64 outputs
-            if (tid < K) {
-                for (int o = 0; o < 64; ++o) gpart[w_off(l) + o * K + tid] = g[o];
-            } else if (tid == K) {
-                for (int o = 0; o < 64; ++o) gpart[b_off(l) + o] = g[o];
+            float g[32];
+            tmem_row32(trow + kColDW, g);  // row r of dW_l^T: input r, outputs c0 .. c0 + 31
+            if (r < K) {
+                for (int j = 0; j < 32; ++j) gpart[w_off(l) + (c0 + j) * K + r] = g[j];
+            } else if (r == K) {
+                for (int j = 0; j < 32; ++j) gpart[b_off(l) + c0 + j] = g[j];
             }
             if (l == 0) break;
-            float dh[64];
-            tmem_row64(trow + kColDX, dh);
-            tmem_row64(trow + 64u * (l - 1), a);
+            tmem_row32(trow + kColDX, g);
+            tmem_row32(trow + 64u * (l - 1), a);
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const float d = dh[j] * silu_grad(a[j] + bias[64 * (l - 1) + j]);
-                store_bf16(DA, tc::kmajor_offset(tid, j, kWidth), d);
-                store_bf16(DAT, tc::kmajor_offset(j, tid, kTrainRows), d);
-            }
+            for (int j = 0; j < 32; ++j) h[j] = g[j] * silu_grad(a[j] + bias[64 * (l - 1) + c0 + j]);
+            store_row32(DA, r, c0, kWidth, h);
         }
     }
     if (failed) {  // a wait gave up: this block's gradients and loss are NaN
-        for (int i = tid; i < kParams; i += blockDim.x) gpart[i] = __int_as_float(0x7FC00000);
-        if (tid == 0) loss_partial[blockIdx.x] = __int_as_float(0x7FC00000);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kParams; i += blockDim.x) gpart[i] = __int_as_float(0x7FC00000);
+        if (threadIdx.x == 0) loss_partial[blockIdx.x] = __int_as_float(0x7FC00000);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -566,8 +562,9 @@ int mlp_forward(const float* params, const float* x, int64_t n, float* out, cuda
     if (n <= 0) return WOB_OK;
     WOB_TRY(allow_smem(g_fwd_configured, (const void*)k_mlp_forward_tc, kTcFwdSmem));
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
-    const int grid = grid_for((const void*)k_mlp_forward_tc, kTcRows, kTcFwdSmem, tiles * kTcRows);
-    k_mlp_forward_tc<<<grid, kTcRows, kTcFwdSmem, s>>>(params, x, stride, n, out);
+    const int grid = grid_for((const void*)k_mlp_forward_tc, kTcThreads, kTcFwdSmem,
+                              (tiles + 1) / 2 * kTcThreads);
+    k_mlp_forward_tc<<<grid, kTcThreads, kTcFwdSmem, s>>>(params, x, stride, n, out);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
@@ -587,7 +584,7 @@ int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const f
     const int blocks = (int)((n + kTrainRows - 1) / kTrainRows);
     float* partial = ws;
     float* lp = ws + (int64_t)blocks * kParams;
-    k_mlp_train_tc<<<blocks, kTrainRows, kTrainSmem, s>>>(params, x, target, n, partial, lp);
+    k_mlp_train_tc<<<blocks, kTrThreads, kTrainSmem, s>>>(params, x, target, n, partial, lp);
     WOB_CUDA_TRY(cudaGetLastError());
     k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out, lr,
                                                      0.9f, 0.999f, 1e-8f, step);

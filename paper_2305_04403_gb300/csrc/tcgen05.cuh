@@ -16,6 +16,15 @@
 //     byte offset of (r, k) = (r / 8) * sbo + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
 // One tcgen05.mma of kind::f16 consumes K = 16, i.e. two core matrices
 // along K: the descriptor of k-block kb starts at base + 256 * kb.
+//
+// The same bytes read as an MN-major operand (the transposed matrix: M or N
+// along the 16-byte rows, K along the 8-row groups) need no copy: its core
+// matrices are the same 8 x 16-byte blocks.  Without swizzle the MN-major
+// descriptor takes the distance between core matrices adjacent along K (the
+// stored matrix's row-group stride, `sbo` above) as its leading offset and
+// the distance between core matrices adjacent along MN (128 bytes) as its
+// stride offset (measured: the other assignment gives wrong products); k-block
+// kb (16 rows of the stored matrix) starts at base + 2 * sbo * kb.
 #pragma once
 
 #include <cstdint>
@@ -48,12 +57,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A
-// and B BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+// and B BF16 (bits 7-9 and 10-12 = 1), A and B K-major (bits 15, 16 = 0) or
+// MN-major (1), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool a_mn = false,
+                                                      bool b_mn = false)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T for one K = 16 block; issued by one thread.
@@ -129,6 +139,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 __device__ __forceinline__ void tmem_wait_ld()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// Barrier of the `count` threads that use named barrier `id` (1..15).
+__device__ __forceinline__ void bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+// As bar_sync, returning whether any of the threads passed true.
+__device__ __forceinline__ bool bar_sync_or(int id, int count, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
