@@ -35,10 +35,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ float silu(float a) { return a / (1.0f + __expf(-a)); }
+// SiLU and its derivative with the fast exponential and reciprocal (relative
+// error ~1e-6, far below the BF16 rounding of the activations).
+__device__ __forceinline__ float silu(float a) { return __fdividef(a, 1.0f + __expf(-a)); }
 __device__ __forceinline__ float silu_grad(float a)
 {
-    const float s = 1.0f / (1.0f + __expf(-a));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-a));
     return s * (1.0f + a * (1.0f - s));
 }
 
@@ -65,14 +67,15 @@ __device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// Forward on the 5th-generation tensor cores (tcgen05).  A CTA of 256
-// threads is two independent halves of 128 threads; each half takes tiles of
-// 128 points in turn (thread t of the half owns row t), so that one half's
-// products run on the tensor cores while the other converts and activates.
-// Per tile the features (BF16) go to the half's A buffer in the canonical
+// Forward on the 5th-generation tensor cores (tcgen05).  A CTA of 512
+// threads is four independent quarters of 128 threads; each quarter takes
+// tiles of 128 points in turn (thread t of the quarter owns row t), so that
+// one quarter's products run on the tensor cores while the others convert
+// and activate (one CTA per SM: four tiles in flight).
+// Per tile the features (BF16) go to the quarter's A buffer in the canonical
 // K-major layout, one thread issues the layer's tcgen05.mma (M 128, N 64,
-// K 16 per instruction) into the half's 64 FP32 columns of tensor memory,
-// the commit arrives on the half's mbarrier, every thread loads its row of
+// K 16 per instruction) into the quarter's 64 FP32 columns of tensor memory,
+// the commit arrives on the quarter's mbarrier, every thread loads its row of
 // the accumulator (tcgen05.ld), adds the bias, applies SiLU and writes the
 // BF16 activations back as the next layer's A operand.  The weights (B
 // operand, W as stored: out x in = N x K, K-major) stay in shared memory for
@@ -80,16 +83,16 @@ __device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t 
 // BF16-rounded activations, as the tensor cores would see them.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 2 * kTcRows;              // two halves
-constexpr int kTcCols = 128;                         // tensor-memory columns per CTA (64 per half)
+constexpr int kTcThreads = 4 * kTcRows;              // four quarters
+constexpr int kTcCols = 256;                         // tensor-memory columns per CTA (64 per quarter)
 constexpr int kTcOffW0 = 0;                          // 64 x 96 BF16, canonical K-major
 constexpr int kTcOffW1 = kTcOffW0 + 64 * kFeat * 2;  // W1..W3: 64 x 64
-constexpr int kTcOffA = kTcOffW1 + 3 * 64 * kWidth * 2;  // per half 128 x 96 BF16 (layers 1-3: 128 x 64)
+constexpr int kTcOffA = kTcOffW1 + 3 * 64 * kWidth * 2;  // per quarter 128 x 96 BF16 (layers 1-3: 128 x 64)
 constexpr int kTcABytes = kTcRows * kFeat * 2;
-constexpr int kTcOffBias = kTcOffA + 2 * kTcABytes;       // 4 x 64 FP32
+constexpr int kTcOffBias = kTcOffA + 4 * kTcABytes;       // 4 x 64 FP32
 constexpr int kTcOffW5 = kTcOffBias + 4 * 64 * 4;         // 64 FP32, then b5
-constexpr int kTcOffMisc = kTcOffW5 + 64 * 4 + 16;        // 2 mbarriers (8 B each), TMEM address
-constexpr int kTcFwdSmem = kTcOffMisc + 32;
+constexpr int kTcOffMisc = kTcOffW5 + 64 * 4 + 16;        // 4 mbarriers (8 B each), TMEM address
+constexpr int kTcFwdSmem = kTcOffMisc + 48;
 constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before giving up (seconds)
 static_assert(kTcOffA % 1024 == 0 && kTcOffW1 % 1024 == 0 && kTcABytes % 1024 == 0,
               "operand alignment");
@@ -124,12 +127,12 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const float* __re
                                                               float* __restrict__ out)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int half = threadIdx.x >> 7, tid = threadIdx.x & 127, warp = threadIdx.x >> 5;
+    const int qtr = threadIdx.x >> 7, tid = threadIdx.x & 127, warp = threadIdx.x >> 5;
     float* bias = reinterpret_cast<float*>(smem + kTcOffBias);
     float* w5 = reinterpret_cast<float*>(smem + kTcOffW5);
-    const uint32_t mbar = tc::smem_addr(smem + kTcOffMisc + 8 * half);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcOffMisc + 16);
-    unsigned char* A = smem + kTcOffA + half * kTcABytes;
+    const uint32_t mbar = tc::smem_addr(smem + kTcOffMisc + 8 * qtr);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcOffMisc + 32);
+    unsigned char* A = smem + kTcOffA + qtr * kTcABytes;
 
     // the network into shared memory, the accumulators into tensor memory
     const bool vec = (reinterpret_cast<uintptr_t>(params) & 15) == 0;
@@ -147,17 +150,17 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const float* __re
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tslot + 64u * half;                 // this half's columns
+    const uint32_t tmem = *tslot + 64u * qtr;                 // this quarter's columns
     const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
     constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTcRows, 64);
     const uint32_t a_base = tc::smem_addr(A);
-    const int bar = 1 + half;  // the half's named barrier
+    const int bar = 1 + qtr;  // the quarter's named barrier
     uint32_t phase = 0;
     bool failed = false;
 
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
-    for (int64_t tile = 2 * (int64_t)blockIdx.x + half; tile < tiles && !failed;
-         tile += 2 * (int64_t)gridDim.x) {
+    for (int64_t tile = 4 * (int64_t)blockIdx.x + qtr; tile < tiles && !failed;
+         tile += 4 * (int64_t)gridDim.x) {
         const int64_t r = tile * kTcRows + tid;
         float y[3];
         load_point(x, n, r, y, stride);
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const float* __re
                 tc::commit(mbar);
             }
             const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
-            if (tc::bar_sync_or(bar, kTcRows, !ok)) {  // the half stops together
+            if (tc::bar_sync_or(bar, kTcRows, !ok)) {  // the quarter stops together
                 failed = true;
                 if (!ok) tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the product in flight, bounded
                 break;
@@ -563,7 +566,7 @@ int mlp_forward(const float* params, const float* x, int64_t n, float* out, cuda
     WOB_TRY(allow_smem(g_fwd_configured, (const void*)k_mlp_forward_tc, kTcFwdSmem));
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
     const int grid = grid_for((const void*)k_mlp_forward_tc, kTcThreads, kTcFwdSmem,
-                              (tiles + 1) / 2 * kTcThreads);
+                              (tiles + 3) / 4 * kTcThreads);
     k_mlp_forward_tc<<<grid, kTcThreads, kTcFwdSmem, s>>>(params, x, stride, n, out);
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
