@@ -457,7 +457,9 @@ def run_sl(args):
         "metric": METRIC, "value": verts * args.steps / (total_ms / 1e3), "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 geometry / f64 walk arithmetic",
+        "vs_baseline": None,
+        "dtype": ("f32 + compensated f32 (float-float) / f64 accumulation" if args.sl_ris <= 1
+                  else "f32 geometry / f64 walk arithmetic"),
         "data": "synthetic (seeded displaced torus, seeded queries)",
         "config": {"workload": f"displaced torus ({len(f)} tris), single layer, "
                                f"{'area sampling' if args.sl_ris <= 1 else f'RIS ({args.sl_ris} candidates)'}: "

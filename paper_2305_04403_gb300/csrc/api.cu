@@ -122,7 +122,10 @@ void fill_params(WalkParams& p, const wob_problem* prob, const float* queries,
     p.verts_d = m.verts_d;
     p.tris = m.tris;
     p.tri_n = m.tri_n;
+    p.tri_f = m.tri_f;
     p.cdf = m.cdf;
+    p.guide = m.guide;
+    p.guide_bits = m.guide_bits;
     p.T = m.T;
     p.area = m.area;
     p.L = m.L;

@@ -77,7 +77,8 @@ __global__ void k_vertex_bounds(const float* __restrict__ verts, int64_t V,
 // longest-edge reductions, index and degeneracy checks.
 __global__ void k_triangles(const float* __restrict__ verts, int64_t V,
                             const int32_t* __restrict__ tris, int64_t T,
-                            NormalArea* __restrict__ tri_n, double* __restrict__ area,
+                            NormalArea* __restrict__ tri_n, TriFrame* __restrict__ tri_f,
+                            double* __restrict__ area,
                             double* __restrict__ volume, unsigned int* __restrict__ max_edge,
                             int* __restrict__ err)
 {
@@ -108,6 +109,19 @@ __global__ void k_triangles(const float* __restrict__ verts, int64_t V,
         }
         tri_n[j] = NormalArea{n[0] / nl, n[1] / nl, n[2] / nl, 0.5 * nl};
         area[j] = 0.5 * nl;
+        TriFrame fr;
+        for (int c = 0; c < 3; ++c) {
+            const double nc = n[c] / nl;
+            fr.v0[c] = (float)a[c];
+            fr.e1h[c] = (float)e1[c];
+            fr.e1l[c] = (float)(e1[c] - (double)fr.e1h[c]);
+            fr.e2h[c] = (float)e2[c];
+            fr.e2l[c] = (float)(e2[c] - (double)fr.e2h[c]);
+            fr.nh[c] = (float)nc;
+            fr.nl[c] = (float)(nc - (double)fr.nh[c]);
+            fr.pad[c] = 0.f;
+        }
+        tri_f[j] = fr;
         // signed volume: a . (b x c) / 6
         vol += (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
                 a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
@@ -224,18 +238,45 @@ __global__ void k_to_f64(const float* __restrict__ in, int64_t n, double* __rest
         out[i] = (double)in[i];
 }
 
+// Guide table of the area CDF (indexed search, Chen and Asau 1974): the
+// area sample of the 53-bit uniform U picks the first j with cdf[j] >
+// fl(U 2^-53 |Gamma|) (else T - 1).  For every U whose top `bits` bits are
+// b that pick lies in [guide[b], guide[b + 1]], where guide[b] is the pick of
+// U = b 2^(53 - bits): the rounded product is monotone in U.  Each entry is
+// a binary search with the same comparison (doubles' bit patterns).
+static __global__ void k_area_guide(const double* __restrict__ cdf, int64_t T, double area, int bits,
+                             int32_t* __restrict__ guide)
+{
+    const int64_t nb = ((int64_t)1 << bits) + 1;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const long long t =
+            __double_as_longlong((double)((uint64_t)b << (53 - bits)) * 0x1p-53 * area);
+        int64_t lo = 0, hi = T - 1;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (__double_as_longlong(cdf[mid]) > t) hi = mid; else lo = mid + 1;
+        }
+        guide[b] = (int32_t)lo;
+    }
+}
+
 void free_mesh(MeshDev& m)
 {
     cudaFree(m.verts);
     cudaFree(m.verts_d);
     cudaFree(m.tris);
     cudaFree(m.tri_n);
+    cudaFree(m.tri_f);
     cudaFree(m.cdf);
+    cudaFree(m.guide);
     m.verts = nullptr;
     m.verts_d = nullptr;
     m.tris = nullptr;
     m.tri_n = nullptr;
+    m.tri_f = nullptr;
     m.cdf = nullptr;
+    m.guide = nullptr;
 }
 
 int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t T,
@@ -248,6 +289,7 @@ int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t 
     WOB_CUDA_TRY(cudaMalloc((void**)&m.verts_d, V * 3 * sizeof(double)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.tris, T * 3 * sizeof(int32_t)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.tri_n, T * sizeof(NormalArea)));
+    WOB_CUDA_TRY(cudaMalloc((void**)&m.tri_f, T * sizeof(TriFrame)));
     WOB_CUDA_TRY(cudaMalloc((void**)&m.cdf, T * sizeof(double)));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     WOB_CUDA_TRY(cudaMemcpyAsync(m.verts, verts, V * 3 * sizeof(float), kind, s));
@@ -281,7 +323,7 @@ int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t 
         m.verts, V, sc->bounds, &sc->err);
     WOB_CUDA_TRY(cudaGetLastError());
     k_triangles<<<grid_for((const void*)k_triangles, threads, 0, T), threads, 0, s>>>(
-        m.verts, V, m.tris, T, m.tri_n, area, &sc->volume, &sc->max_edge, &sc->err);
+        m.verts, V, m.tris, T, m.tri_n, m.tri_f, area, &sc->volume, &sc->max_edge, &sc->err);
     WOB_CUDA_TRY(cudaGetLastError());
     int rc = inclusive_scan<double>(area, m.cdf, T, s);
     Scratch h;
@@ -320,6 +362,16 @@ int build_mesh_impl(const float* verts, int64_t V, const int32_t* tris, int64_t 
                   "outside the interior domain", m.volume);
         return WOB_ERR_DEGENERATE_MESH;
     }
+    // guide table: about one triangle per bucket, at most 2^24 buckets
+    int bits = 1;
+    while (bits < 24 && ((int64_t)1 << bits) < T) ++bits;
+    const int64_t nb = ((int64_t)1 << bits) + 1;
+    WOB_CUDA_TRY(cudaMalloc((void**)&m.guide, nb * sizeof(int32_t)));
+    m.guide_bits = bits;
+    k_area_guide<<<grid_for((const void*)k_area_guide, threads, 0, nb), threads, 0, s>>>(
+        m.cdf, T, m.area, bits, m.guide);
+    WOB_CUDA_TRY(cudaGetLastError());
+    WOB_CUDA_TRY(cudaStreamSynchronize(s));
     return WOB_OK;
 }
 

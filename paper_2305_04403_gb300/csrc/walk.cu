@@ -13,8 +13,10 @@
 // fixed order, so results do not depend on scheduling.  Debug solves also
 // write every walk's value.
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 
+#include "ff.cuh"
 #include "wob_device.cuh"
 #include "wob_host.h"
 
@@ -26,6 +28,13 @@ constexpr double kFourPi = 12.566370614359172953850573533118;
 
 #ifndef WOB_DL_MIN_BLOCKS
 #define WOB_DL_MIN_BLOCKS 8
+#endif
+// Single-layer walks with area sampling: 6 blocks of 128 threads per SM (71
+// registers, no spills) hide the latency of the CDF search better than the
+// unbounded 121 registers (4 blocks; 8% slower) or 8 blocks (64 registers,
+// spills; 3% slower).
+#ifndef WOB_SL_MIN_BLOCKS
+#define WOB_SL_MIN_BLOCKS 6
 #endif
 
 // One thread owns one walk; warps take tiles of 32 consecutive walks from a
@@ -135,9 +144,31 @@ __device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double
     return bc == WOB_BC_ROBIN ? dhdn + (double)p.alpha * h : dhdn;
 }
 
+// Index of the triangle whose area-CDF interval holds the 53-bit uniform
+// U = (hi, lo) times the total area: the first j with cdf[j] > fl(U 2^-53
+// |Gamma|), else T - 1 (inverse CDF).  The guide table brackets the answer
+// by the top bits of U (about one triangle per bucket), and a binary search
+// inside the bracket makes the same comparisons as one over the whole CDF.
+// Non-negative doubles order as their bit patterns: the search compares
+// 64-bit integers (the same decisions as double compares, off the FP64
+// pipe, which issues at 1/64 of the FP32 rate on this GPU).
+__device__ __forceinline__ int64_t area_pick(const WalkParams& p, uint32_t hi, uint32_t lo)
+{
+    const long long target = __double_as_longlong(u53(hi, lo) * p.area);
+    const uint32_t b = hi >> (32 - p.guide_bits);  // top guide_bits bits of U
+    int64_t a = __ldg(p.guide + b);
+    int64_t e = __ldg(p.guide + b + 1);
+    e = e < p.T - 1 ? e : p.T - 1;
+    while (a < e) {
+        const int64_t mid = a + ((e - a) >> 1);
+        if (__double_as_longlong(__ldg(p.cdf + mid)) > target) e = mid; else a = mid + 1;
+    }
+    return a;
+}
+
 // Area-uniform boundary point of stream (q, w, step, attempt): triangle j (original
-// order) by inverse CDF of the areas (53-bit uniform), then a uniform point
-// on it (square-root warp), barycentrics b0..b2; n = the triangle's unit normal.
+// order) by inverse CDF of the areas (area_pick), then a uniform point on it
+// (square-root warp), barycentrics b0..b2; n = the triangle's unit normal.
 struct AreaPoint {
     int64_t j;
     double3 y, n;
@@ -149,15 +180,7 @@ __device__ __forceinline__ AreaPoint area_point(const WalkParams& p, StreamKey k
 {
     AreaPoint a;
     const u32x4 u = stream_block(key, q, w, step, kPurposeArea, attempt, 0u);
-    // Non-negative doubles order as their bit patterns: the search compares
-    // 64-bit integers (the same decisions as double compares, off the FP64
-    // pipe, which issues at 1/64 of the FP32 rate on this GPU).
-    const long long target = __double_as_longlong(u53(u.x, u.y) * p.area);
-    int64_t lo = 0, hi = p.T - 1;
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if (__double_as_longlong(__ldg(p.cdf + mid)) > target) hi = mid; else lo = mid + 1;
-    }
+    const int64_t lo = area_pick(p, u.x, u.y);
     const double su = sqrt(u24(u.z)), u2 = u24(u.w);
     a.b0 = 1.0 - su;
     a.b1 = su * (1.0 - u2);
@@ -335,6 +358,207 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
                 nx = a.n;
                 bx = by;
                 jx = a.j;
+            }
+            value = W0 * S;
+            if (p.per_walk) p.per_walk[idx] = value;
+            if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
+        }
+        if (p.part) add_tile_partials(value, live, qi, wi, p.tpq, p.part);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-layer walks with area sampling in compensated FP32.  Each sample
+// point is kept as its triangle's first vertex v0 (FP32, exact) plus the
+// offset p = b1 e1 + b2 e2 in float-float (hi + lo, about 44 bits); the
+// difference of two points is (v0_y - v0_x) + (p_y - p_x), with the vertex
+// difference exact (Knuth's two-sum), so it is accurate relative to its own
+// length however close the points are.  r . n_x (which cancels to ~r^2 / 2
+// near x on a smooth surface) and the Robin numerator alpha r^2 + r . n_x
+// (whose terms can cancel) are float-float sums; 1 / r, G and dG/dn_x are
+// FP32 with relative error ~1e-7.  FP64 holds only the accumulated product
+// of weights, the sum of terms and the CDF target.
+// ---------------------------------------------------------------------------
+
+// A boundary point in the compensated representation.
+struct FFPoint {
+    float v0[3];  // the triangle's first vertex
+    ff p[3];      // offset from v0
+    ff n[3];      // unit normal of the triangle
+};
+
+// Sum of products a_i b_i of three float-float pairs, as a float-float
+// (two-product and two-sum on the hi parts, the lo cross terms added to the
+// error; the lo x lo products, below 2^-48 relative, are dropped).
+__device__ __forceinline__ ff ff_dot3(const ff (&a)[3], const ff (&b)[3])
+{
+    ff s = two_prod(a[0].hi, b[0].hi);
+    float e = __fmaf_rn(a[0].hi, b[0].lo, __fmul_rn(a[0].lo, b[0].hi));
+#pragma unroll
+    for (int c = 1; c < 3; ++c) {
+        const ff pc = two_prod(a[c].hi, b[c].hi);
+        const ff t = two_sum(s.hi, pc.hi);
+        s.hi = t.hi;
+        e = __fadd_rn(e, __fadd_rn(t.lo, pc.lo));
+        e = __fmaf_rn(a[c].hi, b[c].lo, __fmaf_rn(a[c].lo, b[c].hi, e));
+    }
+    e = __fadd_rn(e, s.lo);
+    return fast_two_sum(s.hi, e);
+}
+
+// Data of the single-layer problems at the point (v0 + p, normal n, on
+// triangle j with barycentrics b0..b2), as sl_data, rounded to FP32: P1
+// values in FP32, the point-source field in FP32 with n . grad h by FMAs (its
+// error ~1e-7 of |grad h|), polynomial data in FP64 at the FP64 position
+// (its monomials cancel) and then rounded.
+__device__ __forceinline__ float sl_data_ff(const WalkParams& p, int64_t j, const FFPoint& y,
+                                            float b0, float b1, float b2, int bc)
+{
+    const DataDev& D = p.data;
+    if (D.mode == WOB_DATA_VERTEX_P1) {
+        const int32_t* t = D.tris + 3 * j;
+        return __fmaf_rn(b0, __ldg(D.vdata + t[0]),
+                         __fmaf_rn(b1, __ldg(D.vdata + t[1]), b2 * __ldg(D.vdata + t[2])));
+    }
+    if (D.mode == WOB_DATA_POLY) {
+        double3 yd, nd;
+        yd.x = (double)y.v0[0] + ((double)y.p[0].hi + (double)y.p[0].lo);
+        yd.y = (double)y.v0[1] + ((double)y.p[1].hi + (double)y.p[1].lo);
+        yd.z = (double)y.v0[2] + ((double)y.p[2].hi + (double)y.p[2].lo);
+        nd = make_double3((double)y.n[0].hi + (double)y.n[0].lo, (double)y.n[1].hi + (double)y.n[1].lo,
+                          (double)y.n[2].hi + (double)y.n[2].lo);
+        return (float)sl_data(p, j, yd, (double)b0, (double)b1, (double)b2, nd, bc);
+    }
+    const float dx = (y.v0[0] - D.x0[0]) + y.p[0].hi;
+    const float dy = (y.v0[1] - D.x0[1]) + y.p[1].hi;
+    const float dz = (y.v0[2] - D.x0[2]) + y.p[2].hi;
+    const float ri = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)));
+    const float h = D.scale * ri;
+    if (bc == WOB_BC_DIRICHLET) return h;
+    const float dn = __fmaf_rn(y.n[0].hi, dx, __fmaf_rn(y.n[1].hi, dy, y.n[2].hi * dz));
+    const float dhdn = -h * ri * ri * dn;
+    return bc == WOB_BC_ROBIN ? __fmaf_rn(p.alpha, h, dhdn) : dhdn;
+}
+
+// The single-layer walks of k_sl_walks for area sampling (p.ris <= 1), in
+// the compensated FP32 arithmetic above; the transition kernel and the
+// sources are those of sl_kernel / sl_data (Table 1, Sec. 4.3).
+template <bool DEBUG>
+__global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkParams p)
+{
+    constexpr float kInv4Pi = 0.0795774715459476678f;
+    const StreamKey key{p.key0, p.key1};
+    const int64_t total = p.Q * (int64_t)p.N;
+    const float two_phi = 2.f * (float)p.phi;
+    const float rmin2 = (float)(1e-24 * p.L * p.L);
+    const int uniform_bc = p.kind == WOB_ROBIN_SL ? WOB_BC_ROBIN : WOB_BC_NEUMANN;
+    // weight factors: |Gamma| (query), -|Gamma| k / p_k (Dirichlet parts),
+    // -2 phi |Gamma| (Neumann / Robin), rounded to FP32 once
+    const float w_query = (float)p.area;
+    const float w_dirichlet = (float)(-p.area * (double)(p.kmix / p.pk));
+    const float w_layer = (float)(-2.0 * (double)p.phi * p.area);
+    const double w_stay = 1.0 / (1.0 - (double)p.pk);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = base + lane;
+        const bool live = idx < total;
+        const int64_t qi = live ? idx / p.N : 0;
+        const int64_t wi = idx - qi * p.N;
+        double value = 0.0;
+        if (live) {
+            const uint32_t q = p.q_base + (uint32_t)qi;
+            const uint32_t w = (uint32_t)(p.walk_begin + wi);
+            // x: the query (v0 = its coordinates, p = 0) or the last sample
+            FFPoint x;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                x.v0[c] = p.queries[3 * qi + c];
+                x.p[c] = {0.f, 0.f};
+                x.n[c] = {0.f, 0.f};
+            }
+            int bx = -1;
+            int64_t jx = -1;
+            double S = 0.0, P = 1.0, W0 = 0.0;
+            for (int k = 0; k < p.M; ++k) {
+                bool stay = false;
+                if (bx == WOB_BC_DIRICHLET) {
+                    const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeBranch, 0u, 0u);
+                    stay = u24(u.x) >= (double)p.pk;
+                }
+                FFPoint y;
+                int64_t j;
+                float b0 = 0.f, b1f = 0.f, b2f = 0.f;  // mixed problems' stays take analytic data
+                double wfac;
+                if (stay) {
+                    y = x;
+                    j = jx;
+                    wfac = w_stay;
+                } else {
+                    const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeArea, 0u, 0u);
+                    j = area_pick(p, u.x, u.y);
+                    // the triangle's frame: six 16-byte loads, unpacked by field
+                    float fr[24];
+                    const float4* F = reinterpret_cast<const float4*>(p.tri_f + j);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const float4 t = __ldg(F + i);
+                        fr[4 * i] = t.x; fr[4 * i + 1] = t.y; fr[4 * i + 2] = t.z; fr[4 * i + 3] = t.w;
+                    }
+                    constexpr int o_e1h = offsetof(TriFrame, e1h) / 4, o_e1l = offsetof(TriFrame, e1l) / 4;
+                    constexpr int o_e2h = offsetof(TriFrame, e2h) / 4, o_e2l = offsetof(TriFrame, e2l) / 4;
+                    constexpr int o_nh = offsetof(TriFrame, nh) / 4, o_nl = offsetof(TriFrame, nl) / 4;
+                    ff e1[3], e2[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        y.v0[c] = fr[c];
+                        e1[c] = {fr[o_e1h + c], fr[o_e1l + c]};
+                        e2[c] = {fr[o_e2h + c], fr[o_e2l + c]};
+                        y.n[c] = {fr[o_nh + c], fr[o_nl + c]};
+                    }
+                    // square-root warp: b1 = sqrt(u1) (1 - u2), b2 = sqrt(u1) u2
+                    const float u2 = u24f(u.w);
+                    const ff su = ff_sqrt(u24f(u.z));
+                    const ff b1 = ff_mul_f(su, 1.f - u2), b2 = ff_mul_f(su, u2);
+                    b0 = 1.f - su.hi;
+                    b1f = b1.hi;
+                    b2f = b2.hi;
+                    ff r[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        y.p[c] = ff_add(ff_mul(e1[c], b1), ff_mul(e2[c], b2));
+                        r[c] = ff_add(two_sum(y.v0[c], -x.v0[c]), ff_sub(y.p[c], x.p[c]));
+                    }
+                    const float r2 =
+                        __fmaf_rn(r[0].hi, r[0].hi, __fmaf_rn(r[1].hi, r[1].hi, r[2].hi * r[2].hi));
+                    if (r2 < rmin2) break;  // empty sample
+                    const float ri = rsqrtf(r2);
+                    const float G = kInv4Pi * ri;
+                    float wf;
+                    if (bx < 0) {
+                        wf = w_query * G;
+                    } else if (bx == WOB_BC_DIRICHLET) {
+                        wf = w_dirichlet * G;
+                    } else {
+                        ff num = ff_dot3(x.n, r);  // r . n_x
+                        if (bx == WOB_BC_ROBIN) {
+                            // alpha r^2 + r . n_x, r^2 as a float-float sum of squares
+                            const ff rr = ff_dot3(r, r);
+                            num = ff_add(num, ff_mul_f(rr, p.alpha));
+                        }
+                        wf = w_layer * (num.hi * (ri * ri) * G);
+                    }
+                    wfac = (double)wf;
+                }
+                if (k == 0) W0 = wfac; else P *= wfac;
+                const int by = p.bc_type ? (int)__ldg(p.bc_type + j) : uniform_bc;
+                const float dat = sl_data_ff(p, j, y, b0, b1f, b2f, by);
+                float src = (by == WOB_BC_DIRICHLET ? p.kmix : two_phi) * dat;
+                if (k == p.M - 1) src *= 0.5f;
+                S = fma(P, (double)src, S);
+                x = y;
+                bx = by;
+                jx = j;
             }
             value = W0 * S;
             if (p.per_walk) p.per_walk[idx] = value;
@@ -966,10 +1190,16 @@ int launch_sl_walks(const WalkParams& p, bool debug, cudaStream_t s)
 {
     const int threads = 128;
     const int64_t work = p.Q * (int64_t)p.N;
-    if (debug)
-        k_sl_walks<true><<<grid_for((const void*)k_sl_walks<true>, threads, 0, work), threads, 0, s>>>(p);
-    else
-        k_sl_walks<false><<<grid_for((const void*)k_sl_walks<false>, threads, 0, work), threads, 0, s>>>(p);
+    if (p.ris > 1) {  // resampling: FP64 kernels (its pick compares running sums)
+        if (debug)
+            k_sl_walks<true><<<grid_for((const void*)k_sl_walks<true>, threads, 0, work), threads, 0, s>>>(p);
+        else
+            k_sl_walks<false><<<grid_for((const void*)k_sl_walks<false>, threads, 0, work), threads, 0, s>>>(p);
+    } else if (debug) {
+        k_sl_walks_ff<true><<<grid_for((const void*)k_sl_walks_ff<true>, threads, 0, work), threads, 0, s>>>(p);
+    } else {
+        k_sl_walks_ff<false><<<grid_for((const void*)k_sl_walks_ff<false>, threads, 0, work), threads, 0, s>>>(p);
+    }
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }

@@ -40,12 +40,28 @@ struct alignas(32) NormalArea {
     double nx, ny, nz, area;
 };
 
+// Per-triangle frame for area samples in compensated FP32 (original order):
+// vertex v0 and, as pairs hi + lo of FP32 values whose sum is the FP64
+// value, the edges e1 = v1 - v0 and e2 = v2 - v0 (exact: differences of FP32
+// coordinates) and the unit normal; 96 bytes, read as six float4.
+struct alignas(16) TriFrame {
+    float v0[3];
+    float e1h[3], e1l[3];
+    float e2h[3], e2l[3];
+    float nh[3], nl[3];
+    float pad[3];
+};
+static_assert(sizeof(TriFrame) == 96, "six float4");
+
 struct MeshDev {
     float* verts = nullptr;   // V x 3
     double* verts_d = nullptr;  // V x 3, the same positions in FP64 (area sampling)
     int32_t* tris = nullptr;  // T x 3
     NormalArea* tri_n = nullptr;  // unit normal (FP64), area
+    TriFrame* tri_f = nullptr;    // compensated FP32 frame of each triangle
     double* cdf = nullptr;    // inclusive prefix sums of areas
+    int32_t* guide = nullptr; // guide table of the area CDF: 2^guide_bits + 1 entries
+    int guide_bits = 0;
     int64_t V = 0, T = 0;
     double lo[3], hi[3];
     double L = 0, area = 0, volume = 0, max_edge = 0;
@@ -88,7 +104,10 @@ struct WalkParams {
     const double* verts_d;  // FP64 copy of verts
     const int32_t* tris;
     const NormalArea* tri_n;
+    const TriFrame* tri_f;
     const double* cdf;
+    const int32_t* guide;  // guide table of the area CDF (see area_pick)
+    int guide_bits;
     int64_t T;
     double area;
     double L;
