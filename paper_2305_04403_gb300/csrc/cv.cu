@@ -12,7 +12,7 @@
 // Gauss) and skips the target's own flat triangle.  The walk is the
 // double-layer recursion with r in place of 2 phi g.
 //
-// Residual walks run as a small wavefront per step: traverse + FP64 refine
+// Residual walks run as a small wavefront per step: traverse + refine
 // (one thread per walk), the network at every new vertex (batched on the
 // tensor cores), then quadrature + accumulation (one thread per walk; the
 // far-field loop over triangles is the same for every lane of a warp, so its
@@ -411,8 +411,9 @@ __global__ void k_cvw_init(WalkParams p, CvWalk st)
     }
 }
 
-// Line of step k from the current vertex: traversal, pick, FP64 refine and
-// the weight (first step (m/2)s, later -phi m s).
+// Line of step k from the current vertex: traversal, pick, float-float
+// refine (positions kept as doubles holding the float-float values) and the
+// weight (first step (m/2)s, later -phi m s).
 __global__ void __launch_bounds__(128, 4) k_cvw_trace(WalkParams p, CvWalk st, int k)
 {
     const StreamKey key{p.key0, p.key1};
@@ -425,11 +426,12 @@ __global__ void __launch_bounds__(128, 4) k_cvw_trace(WalkParams p, CvWalk st, i
         const int64_t qi = i / p.N;
         const uint32_t q = p.q_base + (uint32_t)qi;
         const uint32_t w = (uint32_t)(p.walk_begin + (i - qi * p.N));
-        const double3 x = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
+        const ff x[3] = {ff_split(st.x[i]), ff_split(st.x[st.W + i]), ff_split(st.x[2 * st.W + i])};
         const int self = st.self[i];
-        const double3 d = line_axis(key, q, w, (uint32_t)k);
-        const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
-                                   make_float3((float)d.x, (float)d.y, (float)d.z));
+        ff d[3];
+        line_axis_ff(key, q, w, (uint32_t)k, d);
+        const LinePre L = line_pre(make_float3(x[0].hi, x[1].hi, x[2].hi),
+                                   make_float3(d[0].hi, d[1].hi, d[2].hi));
         const float Tthr = p.edge_thr_L * fabsf(L.Sz);
         Trav t;
         trav_init(t);
@@ -443,15 +445,16 @@ __global__ void __launch_bounds__(128, 4) k_cvw_trace(WalkParams p, CvWalk st, i
             continue;
         }
         const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
-        const Refined r = refine_hit(p.tv, pos, x, d);
-        const double ms = (double)t.m * (double)r.s;
+        ff y[3];
+        const int sgn = refine_hit_ff(p.tv, pos, x, d, y);
+        const double ms = (double)(t.m * sgn);
         st.P[i] = (k == 0) ? 0.5 * ms : st.P[i] * (-(double)p.phi * ms);
-        st.x[i] = r.y.x;
-        st.x[st.W + i] = r.y.y;
-        st.x[2 * st.W + i] = r.y.z;
-        st.vpos[3 * i] = (float)r.y.x;
-        st.vpos[3 * i + 1] = (float)r.y.y;
-        st.vpos[3 * i + 2] = (float)r.y.z;
+        st.x[i] = ff_join(y[0]);
+        st.x[st.W + i] = ff_join(y[1]);
+        st.x[2 * st.W + i] = ff_join(y[2]);
+        st.vpos[3 * i] = y[0].hi;
+        st.vpos[3 * i + 1] = y[1].hi;
+        st.vpos[3 * i + 2] = y[2].hi;
         st.self[i] = pos;
         st.own[i] = (int)prim_of(p.tv, pos);
     }
@@ -551,10 +554,11 @@ __global__ void __launch_bounds__(128, 4) k_cvmc_lines(WalkParams p, CvWalk st, 
         const uint32_t q = p.q_base + (uint32_t)qi;
         const uint32_t w = (uint32_t)(p.walk_begin + (i - qi * p.N)) | kMcWalkBit;
         const uint32_t step = (uint32_t)(v * mc.K + j);
-        const double3 x = make_double3(st.x[i], st.x[st.W + i], st.x[2 * st.W + i]);
-        const double3 d = line_axis(key, q, w, step);
-        const LinePre L = line_pre(make_float3((float)x.x, (float)x.y, (float)x.z),
-                                   make_float3((float)d.x, (float)d.y, (float)d.z));
+        const ff x[3] = {ff_split(st.x[i]), ff_split(st.x[st.W + i]), ff_split(st.x[2 * st.W + i])};
+        ff d[3];
+        line_axis_ff(key, q, w, step, d);
+        const LinePre L = line_pre(make_float3(x[0].hi, x[1].hi, x[2].hi),
+                                   make_float3(d[0].hi, d[1].hi, d[2].hi));
         const float Tthr = p.edge_thr_L * fabsf(L.Sz);
         Trav tr;
         trav_init(tr);
@@ -568,12 +572,12 @@ __global__ void __launch_bounds__(128, 4) k_cvmc_lines(WalkParams p, CvWalk st, 
             continue;
         }
         const int pos = select_hit(p.tv, tr, hits, key, q, w, step);
-        const Refined r = refine_hit(p.tv, pos, x, d);
-        const float ms = (float)(tr.m * r.s);
+        ff y[3];
+        const float ms = (float)(tr.m * refine_hit_ff(p.tv, pos, x, d, y));
         mc.wgt[t] = v == 0 ? 0.5f * ms : -(float)p.phi * ms;
-        pp[0] = (float)r.y.x;
-        pp[1] = (float)r.y.y;
-        pp[2] = (float)r.y.z;
+        pp[0] = y[0].hi;
+        pp[1] = y[1].hi;
+        pp[2] = y[2].hi;
     }
     if (err) atomicOr(p.error_word, err);
 }

@@ -1,8 +1,11 @@
 // walk.cu -- the walk-on-boundary kernels:
 //   k_dl_walks   Dirichlet problems, double-layer formulation, ray (line)
 //                sampling with all-hits queries (Sec. 4.1, 4.4.1)
-//   k_sl_walks   Neumann / Robin problems, single-layer formulation, area
-//                sampling (Sec. 4.3)
+//   k_sl_walks_ff / k_sl_walks
+//                Neumann / Robin problems, single-layer formulation, area
+//                sampling / resampled importance sampling (Sec. 4.3)
+//   k_nd_walks   Neumann problems through the direct boundary integral
+//                equation (Sec. 4.2)
 //   k_reduce*    per-query FP64 mean and variance (Sec. 4.1.1)
 // plus the debug kernels behind wob_trace_lines / wob_line_axes /
 // wob_philox4x32_10.
@@ -151,10 +154,13 @@ __device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double
 // inside the bracket makes the same comparisons as one over the whole CDF.
 // Non-negative doubles order as their bit patterns: the search compares
 // 64-bit integers (the same decisions as double compares, off the FP64
-// pipe, which issues at 1/64 of the FP32 rate on this GPU).
+// pipe, which issues at 1/64 of the FP32 rate on this GPU).  The target is
+// one conversion and one FP64 multiply: U (|Gamma| 2^-53) rounds exactly as
+// (U 2^-53) |Gamma| does, the scaling by 2^-53 being exact.
 __device__ __forceinline__ int64_t area_pick(const WalkParams& p, uint32_t hi, uint32_t lo)
 {
-    const long long target = __double_as_longlong(u53(hi, lo) * p.area);
+    const uint64_t U = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+    const long long target = __double_as_longlong((double)U * (p.area * 0x1p-53));
     const uint32_t b = hi >> (32 - p.guide_bits);  // top guide_bits bits of U
     int64_t a = __ldg(p.guide + b);
     int64_t e = __ldg(p.guide + b + 1);
@@ -220,33 +226,6 @@ __device__ __forceinline__ double sl_kernel(const WalkParams& p, int bx, double3
     return -2.0 * phi * (dgdn + (double)p.alpha * G);
 }
 
-// The same kernel with the FP64 difference vector, squared distance and
-// r . n_x (r . n_x ~ r^2 / 2 for nearby points of a smooth surface: it
-// cancels, and in FP32 its relative error would grow as 1 / r) and the rest
-// in FP32: 1 / r by rsqrt, G, dG/dn_x.  Relative error about 1e-6 -- inside
-// the 1e-5 walk tolerance -- at a fraction of the FP64 cost (an FP64 sqrt
-// and two FP64 divides).  Caller guarantees r >= rmin.  Used where the
-// kernel value only weights a sample; resampling (whose pick compares
-// running sums) keeps sl_kernel.
-__device__ __forceinline__ double sl_kernel32(const WalkParams& p, int bx, double3 r, double r2,
-                                              double3 nx)
-{
-    constexpr float kInv4Pi = 0.0795774715459476678f;
-    const float ri = rsqrtf((float)r2);
-    const float G = kInv4Pi * ri;
-    if (bx < 0) return (double)G;
-    if (bx == WOB_BC_DIRICHLET) return -(double)(p.kmix / p.pk * G);
-    const double rn = r.x * nx.x + r.y * nx.y + r.z * nx.z;
-    const double phi = (double)p.phi;
-    if (bx == WOB_BC_NEUMANN) return -2.0 * phi * (double)((float)rn * ri * ri * G);
-    // Robin: G (alpha + r.n / r^2), the bracket in FP64 (its terms can cancel,
-    // and the walk's later terms inherit its relative error); 1 / r^2 from
-    // the FP32 rsqrt and one FP64 Newton step (relative error ~1e-13).
-    double ri2 = (double)ri * (double)ri;
-    ri2 = ri2 * (2.0 - r2 * ri2);
-    return -2.0 * phi * (double)G * ((double)p.alpha + rn * ri2);
-}
-
 // sl_data with the point-source field in FP32 from an FP64 difference and
 // the normal derivative n . grad h in FP64 (it cancels where the field runs
 // along the surface); polynomial and P1 data as sl_data (a polynomial's
@@ -275,9 +254,11 @@ __device__ __forceinline__ double sl_data32(const WalkParams& p, int64_t j, doub
 // (Neumann), 2 phi (q + alpha h) (Robin), k u_D (Dirichlet parts of mixed
 // problems, whose mu(x) = mu(x) - k S mu + k u_D is sampled by moving with
 // probability p_k or staying at x with weight 1 / (1 - p_k)).  The last
-// source is halved (Sec. 4.1.2).  Next points: area-uniform, or resampled
-// importance sampling (Talbot et al. 2005) from p.ris uniform candidates
-// with target |K|: weight sign(K) |Gamma| (sum of |K| over the candidates) / ris.
+// source is halved (Sec. 4.1.2).  This kernel (FP64 kernels) serves
+// resampled importance sampling (Talbot et al. 2005): the next point is
+// drawn from p.ris area-uniform candidates with target |K|, weight sign(K)
+// |Gamma| (sum of |K| over the candidates) / ris.  Plain area sampling runs
+// in k_sl_walks_ff.
 template <bool DEBUG>
 __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
 {
@@ -319,12 +300,6 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
                     a.n = nx;
                     a.b0 = a.b1 = a.b2 = 0.0;  // mixed problems take analytic data
                     wfac = 1.0 / (1.0 - (double)p.pk);
-                } else if (p.ris <= 1) {
-                    a = area_point(p, key, q, w, (uint32_t)k);
-                    const double3 r = make_double3(a.y.x - x.x, a.y.y - x.y, a.y.z - x.z);
-                    const double r2 = r.x * r.x + r.y * r.y + r.z * r.z;
-                    if (r2 < rmin * rmin) break;  // empty sample
-                    wfac = area * sl_kernel32(p, bx, r, r2, nx);
                 } else {
                     double sumw = 0.0;
                     for (int c = 0; c < p.ris; ++c) {
@@ -406,13 +381,60 @@ __device__ __forceinline__ ff ff_dot3(const ff (&a)[3], const ff (&b)[3])
     return fast_two_sum(s.hi, e);
 }
 
+// Area-uniform boundary point of stream (q, w, step) in the compensated
+// form: triangle j by area_pick, then (frame_point_ff, uniforms uz, uw) the
+// square-root warp b1 = sqrt(u1) (1 - u2), b2 = sqrt(u1) u2 with sqrt(u1) in
+// float-float and the offset p = b1 e1 + b2 e2 in float-float from the
+// triangle's frame (six 16-byte loads); b0..b2 in FP32 for P1 data.
+__device__ __forceinline__ void frame_point_ff(const WalkParams& p, int64_t j, uint32_t uz,
+                                               uint32_t uw, FFPoint& y, float& b0, float& b1f,
+                                               float& b2f)
+{
+    float fr[24];
+    const float4* F = reinterpret_cast<const float4*>(p.tri_f + j);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float4 t = __ldg(F + i);
+        fr[4 * i] = t.x; fr[4 * i + 1] = t.y; fr[4 * i + 2] = t.z; fr[4 * i + 3] = t.w;
+    }
+    constexpr int o_e1h = offsetof(TriFrame, e1h) / 4, o_e1l = offsetof(TriFrame, e1l) / 4;
+    constexpr int o_e2h = offsetof(TriFrame, e2h) / 4, o_e2l = offsetof(TriFrame, e2l) / 4;
+    constexpr int o_nh = offsetof(TriFrame, nh) / 4, o_nl = offsetof(TriFrame, nl) / 4;
+    const float u2 = u24f(uw);
+    const ff su = ff_sqrt(u24f(uz));
+    const ff b1 = ff_mul_f(su, 1.f - u2), b2 = ff_mul_f(su, u2);
+    b0 = 1.f - su.hi;
+    b1f = b1.hi;
+    b2f = b2.hi;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        y.v0[c] = fr[c];
+        const ff e1 = {fr[o_e1h + c], fr[o_e1l + c]}, e2 = {fr[o_e2h + c], fr[o_e2l + c]};
+        y.n[c] = {fr[o_nh + c], fr[o_nl + c]};
+        y.p[c] = ff_add(ff_mul(e1, b1), ff_mul(e2, b2));
+    }
+}
+
+__device__ __forceinline__ int64_t area_sample_ff(const WalkParams& p, StreamKey key, uint32_t q,
+                                                  uint32_t w, uint32_t step, FFPoint& y,
+                                                  float& b0, float& b1f, float& b2f)
+{
+    const u32x4 u = stream_block(key, q, w, step, kPurposeArea, 0u, 0u);
+    const int64_t j = area_pick(p, u.x, u.y);
+    frame_point_ff(p, j, u.z, u.w, y, b0, b1f, b2f);
+    return j;
+}
+
 // Data of the single-layer problems at the point (v0 + p, normal n, on
 // triangle j with barycentrics b0..b2), as sl_data, rounded to FP32: P1
 // values in FP32, the point-source field in FP32 with n . grad h by FMAs (its
-// error ~1e-7 of |grad h|), polynomial data in FP64 at the FP64 position
-// (its monomials cancel) and then rounded.
+// error ~1e-7 of |grad h|; with precise_dn the projection n . (y - x0) is a
+// float-float dot product, so the error is ~1e-7 of n . grad h itself),
+// polynomial data in FP64 at the FP64 position (its monomials cancel) and
+// then rounded.
 __device__ __forceinline__ float sl_data_ff(const WalkParams& p, int64_t j, const FFPoint& y,
-                                            float b0, float b1, float b2, int bc)
+                                            float b0, float b1, float b2, int bc,
+                                            bool precise_dn = false)
 {
     const DataDev& D = p.data;
     if (D.mode == WOB_DATA_VERTEX_P1) {
@@ -435,7 +457,14 @@ __device__ __forceinline__ float sl_data_ff(const WalkParams& p, int64_t j, cons
     const float ri = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)));
     const float h = D.scale * ri;
     if (bc == WOB_BC_DIRICHLET) return h;
-    const float dn = __fmaf_rn(y.n[0].hi, dx, __fmaf_rn(y.n[1].hi, dy, y.n[2].hi * dz));
+    float dn = __fmaf_rn(y.n[0].hi, dx, __fmaf_rn(y.n[1].hi, dy, y.n[2].hi * dz));
+    if (precise_dn) {  // n . (y - x0) as a float-float dot product (it cancels where
+                       // the field runs along the surface)
+        ff d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = ff_add(two_sum(y.v0[c], -D.x0[c]), y.p[c]);
+        dn = ff_dot3(y.n, d).hi;
+    }
     const float dhdn = -h * ri * ri * dn;
     return bc == WOB_BC_ROBIN ? __fmaf_rn(p.alpha, h, dhdn) : dhdn;
 }
@@ -484,7 +513,7 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
                 bool stay = false;
                 if (bx == WOB_BC_DIRICHLET) {
                     const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeBranch, 0u, 0u);
-                    stay = u24(u.x) >= (double)p.pk;
+                    stay = u24f(u.x) >= p.pk;  // both exact in FP32
                 }
                 FFPoint y;
                 int64_t j;
@@ -495,40 +524,11 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
                     j = jx;
                     wfac = w_stay;
                 } else {
-                    const u32x4 u = stream_block(key, q, w, (uint32_t)k, kPurposeArea, 0u, 0u);
-                    j = area_pick(p, u.x, u.y);
-                    // the triangle's frame: six 16-byte loads, unpacked by field
-                    float fr[24];
-                    const float4* F = reinterpret_cast<const float4*>(p.tri_f + j);
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        const float4 t = __ldg(F + i);
-                        fr[4 * i] = t.x; fr[4 * i + 1] = t.y; fr[4 * i + 2] = t.z; fr[4 * i + 3] = t.w;
-                    }
-                    constexpr int o_e1h = offsetof(TriFrame, e1h) / 4, o_e1l = offsetof(TriFrame, e1l) / 4;
-                    constexpr int o_e2h = offsetof(TriFrame, e2h) / 4, o_e2l = offsetof(TriFrame, e2l) / 4;
-                    constexpr int o_nh = offsetof(TriFrame, nh) / 4, o_nl = offsetof(TriFrame, nl) / 4;
-                    ff e1[3], e2[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        y.v0[c] = fr[c];
-                        e1[c] = {fr[o_e1h + c], fr[o_e1l + c]};
-                        e2[c] = {fr[o_e2h + c], fr[o_e2l + c]};
-                        y.n[c] = {fr[o_nh + c], fr[o_nl + c]};
-                    }
-                    // square-root warp: b1 = sqrt(u1) (1 - u2), b2 = sqrt(u1) u2
-                    const float u2 = u24f(u.w);
-                    const ff su = ff_sqrt(u24f(u.z));
-                    const ff b1 = ff_mul_f(su, 1.f - u2), b2 = ff_mul_f(su, u2);
-                    b0 = 1.f - su.hi;
-                    b1f = b1.hi;
-                    b2f = b2.hi;
+                    j = area_sample_ff(p, key, q, w, (uint32_t)k, y, b0, b1f, b2f);
                     ff r[3];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        y.p[c] = ff_add(ff_mul(e1[c], b1), ff_mul(e2[c], b2));
+                    for (int c = 0; c < 3; ++c)
                         r[c] = ff_add(two_sum(y.v0[c], -x.v0[c]), ff_sub(y.p[c], x.p[c]));
-                    }
                     const float r2 =
                         __fmaf_rn(r[0].hi, r[0].hi, __fmaf_rn(r[1].hi, r[1].hi, r[2].hi * r[2].hi));
                     if (r2 < rmin2) break;  // empty sample
@@ -582,9 +582,11 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
     const StreamKey key{p.key0, p.key1};
     const int64_t total = p.Q * (int64_t)p.N;
     const double phi = (double)p.phi;
-    const double rmin = 1e-12 * p.L;
-    // FP64 walk state parked in shared memory during the traversal (as in
-    // k_dl_walks), which leaves the postponed-leaf traversal its registers
+    const float phi_f = (float)p.phi, area_f = (float)p.area;
+    const float rmin2 = (float)(1e-24 * p.L * p.L);
+    // walk state (point and axis as float-float pairs, S and P in FP64)
+    // parked in shared memory during the traversal (as in k_dl_walks), which
+    // leaves the postponed-leaf traversal its registers
     __shared__ double slots[8 * 128];
     __shared__ int leafq[kLeafQ * 128];
     const WalkSlot ws{slots + threadIdx.x, 128};
@@ -605,9 +607,9 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
         if (live) {
             const uint32_t q = p.q_base + (uint32_t)qi;
             const uint32_t w = (uint32_t)(p.walk_begin + wi);
-            ws.set(X0, p.queries[3 * qi]);
-            ws.set(X1, p.queries[3 * qi + 1]);
-            ws.set(X2, p.queries[3 * qi + 2]);
+            ws.set(X0, pack_ff({p.queries[3 * qi], 0.f}));
+            ws.set(X1, pack_ff({p.queries[3 * qi + 1], 0.f}));
+            ws.set(X2, pack_ff({p.queries[3 * qi + 2], 0.f}));
             ws.set(SS, 0.0);
             ws.set(PP, 1.0);
             const LineOut lo{DEBUG && p.line_m ? p.line_m + idx * p.M : nullptr,
@@ -626,29 +628,36 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
             for (int k = k0; k <= p.M; ++k) {
                 // source at vertex k
                 {
-                    const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
-                    const AreaPoint a = area_point(p, key, q, w, (uint32_t)k);
-                    const double rx = a.y.x - x.x, ry = a.y.y - x.y, rz = a.y.z - x.z;
-                    const double r2 = rx * rx + ry * ry + rz * rz;
-                    if (r2 >= rmin * rmin) {
-                        const double f =
-                            sl_data32(p, a.j, a.y, a.b0, a.b1, a.b2, a.n, WOB_BC_NEUMANN);
-                        double c = (k == 0) ? phi : 2.0 * phi;
-                        if (k == p.M) c *= 0.5;
-                        const double G = (double)(0.0795774715459476678f * rsqrtf((float)r2));
-                        ws.set(SS, fma(ws.get(PP) * c * p.area * G, f, ws.get(SS)));
+                    FFPoint y;
+                    float b0, b1, b2;
+                    const int64_t j = area_sample_ff(p, key, q, w, (uint32_t)k, y, b0, b1, b2);
+                    float r2 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const ff x = unpack_ff(ws.get(X0 + c));
+                        const float rc = ff_add(ff_sub({y.v0[c], 0.f}, x), y.p[c]).hi;
+                        r2 = __fmaf_rn(rc, rc, r2);
+                    }
+                    if (r2 >= rmin2) {
+                        const float f = sl_data_ff(p, j, y, b0, b1, b2, WOB_BC_NEUMANN);
+                        float c = (k == 0) ? phi_f : 2.f * phi_f;
+                        if (k == p.M) c *= 0.5f;
+                        const float G = 0.0795774715459476678f * rsqrtf(r2);
+                        ws.set(SS, fma(ws.get(PP), (double)(c * area_f * G * f), ws.get(SS)));
                     }
                 }
                 if (k == p.M) break;
                 // line from vertex k to vertex k + 1
                 LinePre L;
                 {
-                    const double3 d = line_axis(key, q, w, (uint32_t)k);
-                    ws.set(D0, d.x);
-                    ws.set(D1, d.y);
-                    ws.set(D2, d.z);
-                    L = line_pre(make_float3((float)ws.get(X0), (float)ws.get(X1), (float)ws.get(X2)),
-                                 make_float3((float)d.x, (float)d.y, (float)d.z));
+                    ff d[3];
+                    line_axis_ff(key, q, w, (uint32_t)k, d);
+                    ws.set(D0, pack_ff(d[0]));
+                    ws.set(D1, pack_ff(d[1]));
+                    ws.set(D2, pack_ff(d[2]));
+                    L = line_pre(make_float3(unpack_ff(ws.get(X0)).hi, unpack_ff(ws.get(X1)).hi,
+                                             unpack_ff(ws.get(X2)).hi),
+                                 make_float3(d[0].hi, d[1].hi, d[2].hi));
                 }
                 const float Tthr = p.edge_thr_L * fabsf(L.Sz);
                 Trav t;
@@ -664,14 +673,14 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
                 }
                 const int pos = select_hit(p.tv, t, hits, key, q, w, (uint32_t)k);
                 if (DEBUG) lo.put(k, t.m, (int)prim_of(p.tv, pos), t.flag);
-                const double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
-                const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
-                const Refined r = refine_hit(p.tv, pos, x, d);
-                const double ms = (double)t.m * (double)r.s;
+                const ff x[3] = {unpack_ff(ws.get(X0)), unpack_ff(ws.get(X1)), unpack_ff(ws.get(X2))};
+                const ff d[3] = {unpack_ff(ws.get(D0)), unpack_ff(ws.get(D1)), unpack_ff(ws.get(D2))};
+                ff y[3];
+                const double ms = (double)(t.m * refine_hit_ff(p.tv, pos, x, d, y));
                 ws.set(PP, ws.get(PP) * ((k == 0) ? 0.5 * phi * ms : phi * ms));
-                ws.set(X0, r.y.x);
-                ws.set(X1, r.y.y);
-                ws.set(X2, r.y.z);
+                ws.set(X0, pack_ff(y[0]));
+                ws.set(X1, pack_ff(y[1]));
+                ws.set(X2, pack_ff(y[2]));
                 self = pos;
             }
             value = ws.get(SS);
@@ -748,38 +757,33 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS)
         }
         const uint32_t q = (uint32_t)path;
         const u32x4 u = stream_block(key, q, kForwardWalk, 0u, kPurposeArea, 0u, 0u);
-        const double target = u53(u.x, u.y) * tot;
+        const long long target = __double_as_longlong(u53(u.x, u.y) * tot);
         int64_t lo = 0, hi = p.T - 1;
         while (lo < hi) {
             const int64_t mid = lo + ((hi - lo) >> 1);
-            if (__ldg(cdf + mid) > target) hi = mid; else lo = mid + 1;
+            if (__double_as_longlong(__ldg(cdf + mid)) > target) hi = mid; else lo = mid + 1;
         }
-        const double su = sqrt(u24(u.z)), u2 = u24(u.w);
-        const double b0 = 1.0 - su, b1 = su * (1.0 - u2), b2 = su * u2;
-        const int32_t* t = p.tris + 3 * lo;
-        const float* v0 = p.verts + 3 * (int64_t)__ldg(t);
-        const float* v1 = p.verts + 3 * (int64_t)__ldg(t + 1);
-        const float* v2 = p.verts + 3 * (int64_t)__ldg(t + 2);
-        double3 z = make_double3(b0 * __ldg(v0) + b1 * __ldg(v1) + b2 * __ldg(v2),
-                                 b0 * __ldg(v0 + 1) + b1 * __ldg(v1 + 1) + b2 * __ldg(v2 + 1),
-                                 b0 * __ldg(v0 + 2) + b1 * __ldg(v1 + 2) + b2 * __ldg(v2 + 2));
-        const NormalArea na = p.tri_n[lo];
+        FFPoint y;
+        float b0, b1, b2;
+        frame_point_ff(p, lo, u.z, u.w, y, b0, b1, b2);
         const double pdf = start_mode == 1
-                               ? ((cdf[lo] - (lo > 0 ? cdf[lo - 1] : 0.0)) / na.area) / tot
+                               ? ((cdf[lo] - (lo > 0 ? cdf[lo - 1] : 0.0)) / p.tri_n[lo].area) / tot
                                : 1.0 / p.area;
-        double a = 2.0 * phi *
-                   sl_data(p, lo, z, b0, b1, b2, make_double3(na.nx, na.ny, na.nz), WOB_BC_NEUMANN) /
-                   pdf;
+        double a = 2.0 * phi * (double)sl_data_ff(p, lo, y, b0, b1, b2, WOB_BC_NEUMANN, true) / pdf;
+        ff z[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z[c] = ff_add({y.v0[c], 0.f}, y.p[c]);
         int self = p.inv_order[lo], flag = 0;
         for (int j = 0; j < p.M; ++j) {
-            zp[3 * j] = z.x;
-            zp[3 * j + 1] = z.y;
-            zp[3 * j + 2] = z.z;
+            zp[3 * j] = ff_join(z[0]);
+            zp[3 * j + 1] = ff_join(z[1]);
+            zp[3 * j + 2] = ff_join(z[2]);
             wp[j] = (j == p.M - 1 ? 0.5 : 1.0) * a;
             if (j == p.M - 1) break;
-            const double3 d = line_axis(key, q, kForwardWalk, (uint32_t)j);
-            const LinePre L = line_pre(make_float3((float)z.x, (float)z.y, (float)z.z),
-                                       make_float3((float)d.x, (float)d.y, (float)d.z));
+            ff d[3];
+            line_axis_ff(key, q, kForwardWalk, (uint32_t)j, d);
+            const LinePre L = line_pre(make_float3(z[0].hi, z[1].hi, z[2].hi),
+                                       make_float3(d[0].hi, d[1].hi, d[2].hi));
             const float Tthr = p.edge_thr_L * fabsf(L.Sz);
             Trav tr;
             trav_init(tr);
@@ -790,9 +794,10 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS)
             flag |= tr.flag;
             if (tr.m == 0) break;
             const int pos = select_hit(p.tv, tr, hits, key, q, kForwardWalk, (uint32_t)j);
-            const Refined r = refine_hit(p.tv, pos, z, d);
-            a *= phi * (double)tr.m * (double)r.s;
-            z = r.y;
+            ff yz[3];
+            a *= phi * (double)(tr.m * refine_hit_ff(p.tv, pos, z, d, yz));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[c] = yz[c];
             self = pos;
         }
         if (flags) flags[path] = (uint8_t)flag;

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
 #include "wob_internal.h"
 
 namespace wob {
@@ -67,7 +68,9 @@ __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
 // a^2 + b^2 < 1 (an exact integer test), then
 // d = (2 a sqrt(1 - s), 2 b sqrt(1 - s), 1 - 2 s).  Computed in double; the
 // operations are exact except for the correctly rounded sqrt and one
-// product, so the axis is bit-reproducible.
+// product, so the axis is bit-reproducible.  The debug entry points
+// (wob_line_axes, wob_trace_lines) use this form; the walk kernels use
+// line_axis_ff below (the same axis to about 2^-44).
 __device__ __forceinline__ double3 line_axis(StreamKey key, uint32_t q, uint32_t walk,
                                              uint32_t step)
 {
@@ -91,6 +94,46 @@ __device__ __forceinline__ double3 line_axis(StreamKey key, uint32_t q, uint32_t
         }
     }
     return make_double3(0.0, 0.0, 1.0);
+}
+
+// The same axis in float-float: s = S 2^-48, 1 - s and 1 - 2 s are exact
+// as float-float (48-bit integers), sqrt(1 - s) by one correction step.
+__device__ __forceinline__ ff ff_of_int48(int64_t v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (int64_t)h)};
+}
+__device__ __forceinline__ void line_axis_ff(StreamKey key, uint32_t q, uint32_t walk,
+                                             uint32_t step, ff (&d)[3])
+{
+    for (uint32_t call = 0; call < 256u; ++call) {
+        const u32x4 x = stream_block(key, q, walk, step, kPurposeDir, call, 0u);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const uint32_t xa = a ? x.z : x.x;
+            const uint32_t xb = a ? x.w : x.y;
+            const int64_t A = 2 * (int64_t)(xa >> 8) - (int64_t(1) << 24) + 1;
+            const int64_t B = 2 * (int64_t)(xb >> 8) - (int64_t(1) << 24) + 1;
+            const int64_t S = A * A + B * B;
+            if (S < (int64_t(1) << 48)) {
+                const ff r = ff_of_int48((int64_t(1) << 48) - S);  // (1 - s) 2^48
+                const float s0 = __fsqrt_rn(r.hi);                 // sqrt((1 - s)) 2^24
+                const ff sq = two_prod(s0, s0);
+                const float e = __fadd_rn(__fadd_rn(__fsub_rn(r.hi, sq.hi), -sq.lo), r.lo);
+                ff root = s0 > 0.f ? fast_two_sum(s0, __fdiv_rn(e, __fmul_rn(2.f, s0))) : ff{0.f, 0.f};
+                root.hi *= 0x1p-24f;
+                root.lo *= 0x1p-24f;
+                d[0] = ff_mul_f(root, (float)A * 0x1p-23f);
+                d[1] = ff_mul_f(root, (float)B * 0x1p-23f);
+                const ff z = ff_of_int48((int64_t(1) << 48) - 2 * S);
+                d[2] = {z.hi * 0x1p-48f, z.lo * 0x1p-48f};
+                return;
+            }
+        }
+    }
+    d[0] = {0.f, 0.f};
+    d[1] = {0.f, 0.f};
+    d[2] = {1.f, 0.f};
 }
 
 // ---------------------------------------------------------------------------
@@ -577,8 +620,9 @@ __device__ __forceinline__ int trace_line(const float4* __restrict__ nodes,
     return select_hit(tv, t, hits, key, q, walk, step);
 }
 
-// FP64 refinement of the picked hit: intersection of the line x + t d with
-// the triangle's plane, t = N.(v0 - x) / N.d, and s = sign(t) sign(d . N).
+// FP64 refinement of the picked hit (the line-query debug entry point):
+// intersection of the line x + t d with the triangle's plane,
+// t = N.(v0 - x) / N.d, and s = sign(t) sign(d . N).
 struct Refined {
     double3 y;
     int s;
@@ -604,11 +648,51 @@ __device__ __forceinline__ Refined refine_hit(const float4* __restrict__ tv, int
     return r;
 }
 
-// Dirichlet data g at a boundary point y of the triangle in leaf order `pos`.
-__device__ __forceinline__ float dl_data(const DataDev& D, const float4* __restrict__ tv, int pos,
-                                         double3 yd)
+// The same refinement in float-float (the walk kernels): the edges b - a,
+// c - a are exact (two-sum of FP32 vertices), the normal N, N.d and
+// N.(a - x) are float-float products and sums, t = N.(a - x) / N.d takes one
+// correction step, y = x + t d; relative error about 2^-44, so the hit
+// point agrees with the FP64 refinement far below the walk tolerance.  x and
+// d are float-float, the hit y is returned as float-float and the sign
+// s = sign(t) sign(d . N) as the result.
+__device__ __forceinline__ int refine_hit_ff(const float4* __restrict__ tv, int pos,
+                                             const ff (&x)[3], const ff (&d)[3], ff (&y)[3])
 {
-    const float3 y = make_float3((float)yd.x, (float)yd.y, (float)yd.z);
+    const float4 a4 = __ldg(tv + 3 * pos + 0);
+    const float4 b4 = __ldg(tv + 3 * pos + 1);
+    const float4 c4 = __ldg(tv + 3 * pos + 2);
+    const ff e1[3] = {two_sum(b4.x, -a4.x), two_sum(b4.y, -a4.y), two_sum(b4.z, -a4.z)};
+    const ff e2[3] = {two_sum(c4.x, -a4.x), two_sum(c4.y, -a4.y), two_sum(c4.z, -a4.z)};
+    const ff n[3] = {ff_sub(ff_mul(e1[1], e2[2]), ff_mul(e1[2], e2[1])),
+                     ff_sub(ff_mul(e1[2], e2[0]), ff_mul(e1[0], e2[2])),
+                     ff_sub(ff_mul(e1[0], e2[1]), ff_mul(e1[1], e2[0]))};
+    const ff w[3] = {ff_sub({a4.x, 0.f}, x[0]), ff_sub({a4.y, 0.f}, x[1]), ff_sub({a4.z, 0.f}, x[2])};
+    ff dn = ff_mul(d[0], n[0]), num = ff_mul(n[0], w[0]);
+    dn = ff_add(dn, ff_mul(d[1], n[1]));
+    dn = ff_add(dn, ff_mul(d[2], n[2]));
+    num = ff_add(num, ff_mul(n[1], w[1]));
+    num = ff_add(num, ff_mul(n[2], w[2]));
+    const float q1 = __fdiv_rn(num.hi, dn.hi);
+    const ff r = ff_sub(num, ff_mul_f(dn, q1));
+    const ff t = fast_two_sum(q1, __fdiv_rn(r.hi, dn.hi));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = ff_add(x[c], ff_mul(t, d[c]));
+    return ((t.hi > 0.f) == (dn.hi > 0.f)) ? 1 : -1;
+}
+
+// A double that holds a float-float value exactly (hi + lo, |lo| <= ulp(hi)
+// / 2) and back.
+__device__ __forceinline__ ff ff_split(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double ff_join(ff v) { return (double)v.hi + (double)v.lo; }
+
+// Dirichlet data g at a boundary point y of the triangle in leaf order `pos`.
+__device__ __forceinline__ float dl_data_f(const DataDev& D, const float4* __restrict__ tv, int pos,
+                                           float3 y)
+{
     if (D.mode == WOB_DATA_POLY) {
         const float* c = D.poly;
         return c[0] + c[1] * y.x + c[2] * y.y + c[3] * y.z + c[4] * y.x * y.x +
@@ -636,23 +720,10 @@ __device__ __forceinline__ float dl_data(const DataDev& D, const float4* __restr
            b2 * __ldg(D.vdata + t[2]);
 }
 
-// One double-layer step after the line from x picked the hit at leaf
-// position `pos` among m hits (Sec. 4.1.1, 4.1.2): refine the hit in FP64,
-// update the weight product (first step -dG/dn_y/p = (m/2)s, later steps
-// 2 phi dG/dn_y/p = -phi m s) and add the source term (2 phi g, halved on the
-// last vertex).  Shared by every double-layer kernel so that they compute
-// identical values.
-__device__ __forceinline__ void dl_accumulate(const float4* __restrict__ tv, const DataDev& D,
-                                              int pos, int m, int k, int M, double phi,
-                                              double3& x, double3 d, double& S, double& P)
+__device__ __forceinline__ float dl_data(const DataDev& D, const float4* __restrict__ tv, int pos,
+                                         double3 yd)
 {
-    const Refined r = refine_hit(tv, pos, x, d);
-    const double ms = (double)m * (double)r.s;
-    P = (k == 0) ? 0.5 * ms : P * (-phi * ms);
-    const double g = (double)dl_data(D, tv, pos, r.y);
-    const double c = (k == M - 1) ? phi : 2.0 * phi;
-    S = fma(P * c, g, S);
-    x = r.y;
+    return dl_data_f(D, tv, pos, make_float3((float)yd.x, (float)yd.y, (float)yd.z));
 }
 
 // Geometry a double-layer walk needs.
@@ -669,11 +740,23 @@ struct WalkCount {
     unsigned long long lines, nodes, tris, hits, flag;
 };
 
-// Where a walk keeps its FP64 state (point, axis, S, P) while its lines are
-// traversed: eight doubles per thread in shared memory, structure of arrays
+// Where a walk keeps its state (point and axis as float-float pairs, S and
+// P in FP64) while its lines are traversed: eight 8-byte slots per thread in
+// shared memory, structure of arrays
 // (field j of thread t at base[j * stride + t]) so that a warp's accesses
 // are conflict-free.  The state is touched once per line; keeping it out of
 // registers leaves the traversal loop its 64 registers.
+// A float-float value in one double-sized slot (the two floats' bits, no
+// arithmetic).
+__device__ __forceinline__ double pack_ff(ff v)
+{
+    return __hiloint2double(__float_as_int(v.hi), __float_as_int(v.lo));
+}
+__device__ __forceinline__ ff unpack_ff(double v)
+{
+    return {__int_as_float(__double2hiint(v)), __int_as_float(__double2loint(v))};
+}
+
 struct WalkSlot {
     volatile double* base;  // &smem[threadIdx.x]
     int stride;             // threads per block
@@ -727,10 +810,10 @@ struct LineOut {
 
 // One double-layer walk from x (Sec. 4.1.1-4.1.2, ray sampling of Sec.
 // 4.4.1): per line, draw the axis, traverse (descend to a leaf, test it,
-// repeat), pick the hit (keys only when m > 1), refine it in FP64 and
-// accumulate.  Returns the walk value; `lo` (DEBUG only) receives the
-// per-line outputs.  start_pos >= 0: x0 lies on
-// that triangle (leaf position) and the walk estimates the density nu(x0)
+// repeat), pick the hit (keys only when m > 1), refine it in float-float
+// and accumulate (weight product and sum in FP64).  Returns the walk value;
+// `lo` (DEBUG only) receives the per-line outputs.  start_pos >= 0: x0 lies
+// on that triangle (leaf position) and the walk estimates the density nu(x0)
 // (Eq. indirect_double_boundary_reordered2): x0 is vertex 1 with weight 1
 // and lines 1 .. M-1 follow.  HIT_MASK: the node-test form of trace_wide_q.
 template <bool COUNT, bool DEBUG, bool GRAD = false, bool HIT_MASK = true>
@@ -746,9 +829,9 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         ws.set(GY, 0.0);
         ws.set(GZ, 0.0);
     }
-    ws.set(X0, x0.x);
-    ws.set(X1, x0.y);
-    ws.set(X2, x0.z);
+    ws.set(X0, pack_ff({(float)x0.x, 0.f}));
+    ws.set(X1, pack_ff({(float)x0.y, 0.f}));
+    ws.set(X2, pack_ff({(float)x0.z, 0.f}));
     ws.set(SS, 0.0);
     ws.set(PP, 1.0);
     int self = -1, k = 0;
@@ -762,12 +845,14 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
     for (; k < M; ++k) {
         LinePre L;
         {
-            const double3 d = line_axis(key, q, w, (uint32_t)k);
-            ws.set(D0, d.x);
-            ws.set(D1, d.y);
-            ws.set(D2, d.z);
-            L = line_pre(make_float3((float)ws.get(X0), (float)ws.get(X1), (float)ws.get(X2)),
-                         make_float3((float)d.x, (float)d.y, (float)d.z));
+            ff d[3];
+            line_axis_ff(key, q, w, (uint32_t)k, d);
+            ws.set(D0, pack_ff(d[0]));
+            ws.set(D1, pack_ff(d[1]));
+            ws.set(D2, pack_ff(d[2]));
+            L = line_pre(make_float3(unpack_ff(ws.get(X0)).hi, unpack_ff(ws.get(X1)).hi,
+                                     unpack_ff(ws.get(X2)).hi),
+                         make_float3(d[0].hi, d[1].hi, d[2].hi));
         }
         const float Tthr = G.edge_thr_L * fabsf(L.Sz);
         Trav t;
@@ -791,20 +876,26 @@ __device__ __forceinline__ double dl_walk(const DLGeom& G, const DataDev& D, dou
         }
         const int pos = select_hit(G.tv, t, hits, key, q, w, (uint32_t)k);
         if (DEBUG) lo.put(k, t.m, (int)prim_of(G.tv, pos), t.flag);
-        double3 x = make_double3(ws.get(X0), ws.get(X1), ws.get(X2));
-        const double3 d = make_double3(ws.get(D0), ws.get(D1), ws.get(D2));
+        const ff x[3] = {unpack_ff(ws.get(X0)), unpack_ff(ws.get(X1)), unpack_ff(ws.get(X2))};
+        const ff d[3] = {unpack_ff(ws.get(D0)), unpack_ff(ws.get(D1)), unpack_ff(ws.get(D2))};
         double S = ws.get(SS), P = ws.get(PP);
-        const double3 xk = x;
-        dl_accumulate(G.tv, D, pos, t.m, k, M, phi, x, d, S, P);
+        ff y[3];
+        const int sgn = refine_hit_ff(G.tv, pos, x, d, y);
+        const double ms = (double)(t.m * sgn);
+        P = (k == 0) ? 0.5 * ms : P * (-phi * ms);
+        const double g = (double)dl_data_f(D, G.tv, pos, make_float3(y[0].hi, y[1].hi, y[2].hi));
+        const double cc = (k == M - 1) ? phi : 2.0 * phi;
+        S = fma(P * cc, g, S);
         if (GRAD && k == 0 && start_pos < 0) {
-            const double3 gf = grad_factor(G.tv, pos, xk, x);
+            const double3 gf = grad_factor(G.tv, pos, make_double3((double)x[0].hi + x[0].lo, (double)x[1].hi + x[1].lo, (double)x[2].hi + x[2].lo),
+                                           make_double3((double)y[0].hi + y[0].lo, (double)y[1].hi + y[1].lo, (double)y[2].hi + y[2].lo));
             ws.set(GX, gf.x);
             ws.set(GY, gf.y);
             ws.set(GZ, gf.z);
         }
-        ws.set(X0, x.x);
-        ws.set(X1, x.y);
-        ws.set(X2, x.z);
+        ws.set(X0, pack_ff(y[0]));
+        ws.set(X1, pack_ff(y[1]));
+        ws.set(X2, pack_ff(y[2]));
         ws.set(SS, S);
         ws.set(PP, P);
         self = pos;

@@ -2,8 +2,11 @@
 wob_solve_forward) against the oracle's fwd_paths / fwd_connect.
 
 Paths: same counter-based draws on both sides, so on paths neither side
-flags the vertices agree to 1e-9 and the weights to 1e-9 relative (FP64
-refinement; the weighted start's CDF is summed in another order).
+flags the vertices agree to 1e-9 (float-float refinement) and the weights
+to 2e-6 relative: the start weight 2 phi q(z_0) / p(z_0) takes the data
+term in FP32 (rsqrt, products; n . (z_0 - x0) float-float), about five
+roundings of up to 2.4e-7 each; the weighted start's CDF is summed in
+another order.
 Connection: the GPU sums distances and G in FP32 per path, over runs of 32
 paths in FP32 and over those runs in FP64: per query within 1e-5 of the
 mean of sum_j |w_j| G(x, z_j)."""
@@ -59,7 +62,7 @@ def test_forward_paths_and_connection_parity(wob, start_mode, phi):
     assert ok.mean() > 0.9
     assert np.allclose(g["zpos"][ok], r["zpos"][ok], rtol=0, atol=1e-9)
     scale = np.abs(r["zw"][ok]).max()
-    close = np.isclose(g["zw"], r["zw"], rtol=1e-9, atol=1e-12 * scale).all(1)
+    close = np.isclose(g["zw"], r["zw"], rtol=2e-6, atol=1e-12 * scale).all(1)
     bad = np.flatnonzero(ok & ~close)
     assert bad.size == 0, (bad.size, bad[:4], g["zw"][bad[:2]], r["zw"][bad[:2]])
     # connection of the GPU's own paths

@@ -210,6 +210,24 @@ def test_sl_parity(wob, kind, phi, alpha):
     assert np.all(err <= 1e-5 * at + 1e-12)
 
 
+@pytest.mark.parametrize("kind,phi,alpha", [(1, 1, 0.0), (2, -1, 0.5)])
+def test_sl_vertex_data_parity(wob, kind, phi, alpha):
+    """Single-layer walks with piecewise-linear vertex data (the P1 mode of
+    Sec. 4.3's sources): per walk against the oracle."""
+    v, f = I.icosphere(3)
+    vd = np.random.default_rng(5).standard_normal(len(v)).astype(np.float32)
+    q = (I.ball_queries(32, 0.8, 3) if phi == 1 else
+         (_axes(32, 4) * np.random.default_rng(1).uniform(1.2, 2, (32, 1))).astype(np.float32))
+    bvh = wob.build_bvh(wob.build_mesh(v, f))
+    prob = wob.Problem(bvh, kind=kind, side=phi, alpha=alpha, data_mode=wob.DATA_VERTEX_P1,
+                       vertex_data=torch.from_numpy(vd).cuda())
+    g = wob.solve_debug(prob, q, 128, 6, seed=3, want_lines=False)
+    pw, at = O.sl_walks(v, f, q, 128, 6, kind=kind, alpha=alpha, phi=phi,
+                        mode=O.DATA_VERTEX_P1, vertex_data=vd, seed=3, want_abs=True)
+    err = np.abs(g["per_walk"].cpu().numpy() - pw)
+    assert np.all(err <= 1e-5 * at + 1e-12), (err / np.maximum(1e-5 * at, 1e-300)).max()
+
+
 def test_sl_boundary_queries_torus(wob):
     v, f, tsh = I.displaced_torus(100, 40)
     bp, prim = I.boundary_points(v, f, 32, 3)
