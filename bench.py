@@ -47,11 +47,11 @@ BYTES_NODE, BYTES_TRI = 96, 48
 # workload (queries, leaf size, bytes) from ncu dram__bytes_read.sum +
 # dram__bytes_write.sum (profiles/k_dl_walks_star6_wide.md); None while the
 # kernel has changed since the last capture.
-TRAFFIC_FULL = (29497, 1, 27.11e6 + 106.24e6)
+TRAFFIC_FULL = (29497, 1, 27.07e6 + 135.12e6)
 # The walk kernel's issue-slot use from the same profile: fraction of cycles
 # with an instruction issued, and active threads per warp instruction; None
 # while the kernel has changed since the last capture.
-ISSUE_PROFILE = (0.735, 10.74)
+ISSUE_PROFILE = (0.722, 10.77)
 
 
 def _peaks():

@@ -351,8 +351,10 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
 // length however close the points are.  r . n_x (which cancels to ~r^2 / 2
 // near x on a smooth surface) and the Robin numerator alpha r^2 + r . n_x
 // (whose terms can cancel) are float-float sums; 1 / r, G and dG/dn_x are
-// FP32 with relative error ~1e-7.  FP64 holds only the accumulated product
-// of weights, the sum of terms and the CDF target.
+// FP32 with relative error ~1e-7.  The product of weights is an FP32
+// significand renormalised every step with an integer exponent; FP64 holds
+// only the sum of terms (one conversion and one add per step) and the CDF
+// target.
 // ---------------------------------------------------------------------------
 
 // A boundary point in the compensated representation.
@@ -469,6 +471,18 @@ __device__ __forceinline__ float sl_data_ff(const WalkParams& p, int64_t j, cons
     return bc == WOB_BC_ROBIN ? __fmaf_rn(p.alpha, h, dhdn) : dhdn;
 }
 
+// The double t 2^e of an FP32 value t (exact): the exponent is added in
+// the double's bit pattern, off the FP64 pipe; ldexp only where the result
+// would leave the normal range.
+__device__ __forceinline__ double scale2(float t, int e)
+{
+    const double d = (double)t;
+    const int hi = __double2hiint(d);
+    const int ex = ((hi >> 20) & 0x7FF) + e;
+    if (t == 0.f || !(ex > 0 && ex < 2047)) return t == 0.f ? 0.0 : ldexp(d, e);
+    return __hiloint2double((hi & ~(0x7FF << 20)) | (ex << 20), __double2loint(d));
+}
+
 // The single-layer walks of k_sl_walks for area sampling (p.ris <= 1), in
 // the compensated FP32 arithmetic above; the transition kernel and the
 // sources are those of sl_kernel / sl_data (Table 1, Sec. 4.3).
@@ -486,7 +500,7 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
     const float w_query = (float)p.area;
     const float w_dirichlet = (float)(-p.area * (double)(p.kmix / p.pk));
     const float w_layer = (float)(-2.0 * (double)p.phi * p.area);
-    const double w_stay = 1.0 / (1.0 - (double)p.pk);
+    const float w_stay = (float)(1.0 / (1.0 - (double)p.pk));
     const int lane = threadIdx.x & 31;
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < total;
          base += (int64_t)gridDim.x * blockDim.x) {
@@ -508,7 +522,12 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
             }
             int bx = -1;
             int64_t jx = -1;
-            double S = 0.0, P = 1.0, W0 = 0.0;
+            // the weight product P = Pm 2^Pe (FP32 significand renormalised to
+            // [1, 2) every step, integer exponent: no overflow over long walks)
+            // and the sum of terms S in FP64
+            double S = 0.0;
+            float Pm = 1.f, W0 = 0.f;
+            int Pe = 0;
             for (int k = 0; k < p.M; ++k) {
                 bool stay = false;
                 if (bx == WOB_BC_DIRICHLET) {
@@ -518,11 +537,11 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
                 FFPoint y;
                 int64_t j;
                 float b0 = 0.f, b1f = 0.f, b2f = 0.f;  // mixed problems' stays take analytic data
-                double wfac;
+                float wf;
                 if (stay) {
                     y = x;
                     j = jx;
-                    wfac = w_stay;
+                    wf = w_stay;
                 } else {
                     j = area_sample_ff(p, key, q, w, (uint32_t)k, y, b0, b1f, b2f);
                     ff r[3];
@@ -534,7 +553,6 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
                     if (r2 < rmin2) break;  // empty sample
                     const float ri = rsqrtf(r2);
                     const float G = kInv4Pi * ri;
-                    float wf;
                     if (bx < 0) {
                         wf = w_query * G;
                     } else if (bx == WOB_BC_DIRICHLET) {
@@ -548,19 +566,28 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
                         }
                         wf = w_layer * (num.hi * (ri * ri) * G);
                     }
-                    wfac = (double)wf;
                 }
-                if (k == 0) W0 = wfac; else P *= wfac;
+                if (k == 0) {
+                    W0 = wf;
+                } else {
+                    Pm *= wf;
+                    const uint32_t pb = __float_as_uint(Pm);
+                    const int pe = (int)((pb >> 23) & 0xFFu);
+                    if (pe != 0 && pe != 255) {  // zero, subnormal, inf, NaN stay as they are
+                        Pe += pe - 127;
+                        Pm = __uint_as_float((pb & 0x807FFFFFu) | 0x3F800000u);
+                    }
+                }
                 const int by = p.bc_type ? (int)__ldg(p.bc_type + j) : uniform_bc;
                 const float dat = sl_data_ff(p, j, y, b0, b1f, b2f, by);
                 float src = (by == WOB_BC_DIRICHLET ? p.kmix : two_phi) * dat;
                 if (k == p.M - 1) src *= 0.5f;
-                S = fma(P, (double)src, S);
+                S += scale2(Pm * src, Pe);
                 x = y;
                 bx = by;
                 jx = j;
             }
-            value = W0 * S;
+            value = (double)W0 * S;
             if (p.per_walk) p.per_walk[idx] = value;
             if (DEBUG && p.walk_flag) p.walk_flag[idx] = 0;
         }
