@@ -557,8 +557,10 @@ int wob_trace_lines(wob_bvh b, const double *origins, const double *dirs,
                     uint32_t problem, float tau, int32_t *m, int32_t *sum_s, int32_t *prim,
                     int32_t *s, double *t, double *y, uint8_t *flag, void *stream);
 
-/* Line axes the walks use, for (query, walk, step) triples (device, n x 3)
- * -> device n x 3 doubles.  Marsaglia (1972) sampling of the unit sphere. */
+/* Line axes of the walks' streams, for (query, walk, step) triples (device,
+ * n x 3) -> device n x 3 doubles.  Marsaglia (1972) sampling of the unit
+ * sphere, formed in FP64 (the walk kernels carry the same axis as a
+ * float-float pair, equal to it within about 2^-44 relative). */
 int wob_line_axes(uint64_t seed, uint32_t problem, const uint32_t *qws, int64_t n, double *d,
                   void *stream);
 

@@ -19,7 +19,7 @@ import pytest
 
 import oracle as O
 from paper_2305_04403_gb300 import inputs as I
-from _meshes import l_prism
+from _meshes import cube, l_prism, tetrahedron
 from _parity import compare_walks
 
 torch = pytest.importorskip("torch")
@@ -226,6 +226,41 @@ def test_sl_vertex_data_parity(wob, kind, phi, alpha):
                         mode=O.DATA_VERTEX_P1, vertex_data=vd, seed=3, want_abs=True)
     err = np.abs(g["per_walk"].cpu().numpy() - pw)
     assert np.all(err <= 1e-5 * at + 1e-12), (err / np.maximum(1e-5 * at, 1e-300)).max()
+
+
+def _inside_points(v, f, n, seed):
+    """n points inside a small closed integer mesh: random points of its box
+    kept where the oracle's Gauss invariant (sum of s over a line's hits)
+    says inside."""
+    rng = np.random.default_rng(seed)
+    lo, hi = v.min(0), v.max(0)
+    out = []
+    while len(out) < n:
+        p = rng.uniform(lo + 0.1, hi - 0.1, (4 * n, 3)).astype(np.float32)
+        r = O.trace_lines(v, f, p, _axes(len(p), seed + len(out)).astype(np.float32))
+        out += list(p[(r["sum_s"] == 2) & (r["flag"] == 0)])
+    return np.array(out[:n], np.float32)
+
+
+@pytest.mark.parametrize("name", ["tetrahedron", "cube", "l_prism"])
+def test_small_meshes_parity(wob, name):
+    """Meshes of 4, 12 and 20 triangles (integer coordinates; the area-CDF
+    guide table has 4 to 32 buckets, the tree one or two levels): double-
+    layer walks line by line and single-layer Neumann walks per walk against
+    the oracle."""
+    v, f = {"tetrahedron": tetrahedron, "cube": cube, "l_prism": l_prism}[name]()
+    q = _inside_points(v, f, 24, 3)
+    poly = (0.1, 0.3, -0.2, 0.5, 1.0, -1.0, 0.0, 0.4, 0.0, 0.0)
+    g, r = _run_dl(wob, v, f, q, 64, 6, poly=poly, seed=4, problem=1)
+    same, st = compare_walks(g, r, np.abs(I.poly_eval(poly, v)).max())
+    assert st["walks_compared"] > 0.95, st
+    bvh = wob.build_bvh(wob.build_mesh(v, f))
+    x0 = (10.0, 1.0, -3.0)
+    prob = wob.Problem(bvh, kind=wob.NEUMANN_SL, side=1, data_mode=wob.DATA_POINT, x0=x0)
+    gs = wob.solve_debug(prob, q, 64, 6, seed=5, want_lines=False)["per_walk"].cpu().numpy()
+    pw, at = O.sl_walks(v, f, q, 64, 6, kind=O.KIND_NEUMANN_SL, phi=1, mode=O.DATA_POINT,
+                        x0=x0, seed=5, want_abs=True)
+    assert np.all(np.abs(gs - pw) <= 1e-5 * at + 1e-12), (np.abs(gs - pw) / at).max()
 
 
 def test_sl_boundary_queries_torus(wob):
