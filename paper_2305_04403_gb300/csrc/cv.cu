@@ -1038,8 +1038,10 @@ int wob_cv_train(const wob_problem* prob, wob_cv c, const wob_cv_train_params* t
     const int64_t b = tp->batch < n ? tp->batch : n;
     const int64_t steps = (n + b - 1) / b;
     const int64_t ws_floats = mlp_train_workspace(b);
-    // one allocation: points (3n f32), prims (n i32), est / var (2n f64), targets (n f32), ws
-    const size_t bytes = (size_t)n * (12 + 4 + 16 + 4) + (size_t)ws_floats * 4 + 256;
+    // one allocation: points (3n f32), prims (n i32), est / var (2n f64), targets (n f32), ws,
+    // the training control word and one epoch's losses
+    const size_t bytes =
+        (size_t)n * (12 + 4 + 16 + 4) + (size_t)(ws_floats + 2 + steps) * 4 + 256;
     char* buf = nullptr;
     WOB_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
     double* est = (double*)buf;
@@ -1056,16 +1058,53 @@ int wob_cv_train(const wob_problem* prob, wob_cv c, const wob_cv_train_params* t
         k_to_float<<<grid_for((const void*)k_to_float, 256, 0, n), 256, 0, s>>>(est, n, targets);
         if (cudaGetLastError() != cudaSuccess) rc = WOB_ERR_CUDA;
     }
-    int step = tp->step0;
-    for (int e = 0; e < tp->epochs && rc == WOB_OK; ++e) {
-        // step schedule: the last tail_epochs epochs run at lr_end
-        const float lr = e >= tp->epochs - tp->tail_epochs ? tp->lr_end : tp->lr;
-        for (int64_t j = 0; j < steps && rc == WOB_OK; ++j) {
-            const int64_t r0 = j * b, nb = (r0 + b <= n) ? b : n - r0;
-            const int64_t t = (int64_t)e * steps + j;
-            rc = mlp_train_step_ws(params, adam_m, adam_v, pts + 3 * r0, targets + r0, nb, lr,
-                                   ++step, nullptr, loss_out ? loss_out + t : nullptr, ws, s);
+    // One epoch (every minibatch: training kernel, Adam, loss) is captured
+    // once as a CUDA graph on a private stream and replayed per epoch on the
+    // caller's stream: the step number and learning rate live in device
+    // memory (TrainCtl), the epoch's losses in a scratch row copied out
+    // after each replay.  The same kernels as unrolled launches.
+    // step schedule: the last tail_epochs epochs run at lr_end
+    auto epoch_lr = [&](int e) { return e >= tp->epochs - tp->tail_epochs ? tp->lr_end : tp->lr; };
+    TrainCtl* ctl = reinterpret_cast<TrainCtl*>(ws + ws_floats);
+    float* lrow = ws + ws_floats + 2;
+    if (rc == WOB_OK && tp->epochs > 0) {
+        rc = mlp_train_prepare();
+        if (rc == WOB_OK) rc = train_ctl_set(ctl, tp->step0 + 1, epoch_lr(0), true, s);
+    }
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (rc == WOB_OK && tp->epochs > 0) {
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = WOB_ERR_CUDA;
+        if (rc == WOB_OK &&
+            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            rc = WOB_ERR_CUDA;
+        if (rc == WOB_OK) {
+            for (int64_t j = 0; j < steps && rc == WOB_OK; ++j) {
+                const int64_t r0 = j * b, nb = (r0 + b <= n) ? b : n - r0;
+                rc = mlp_train_step_ws(params, adam_m, adam_v, pts + 3 * r0, targets + r0, nb, 0.f,
+                                       0, nullptr, lrow + j, ws, cs, ctl);
+            }
+            const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            if (rc == WOB_OK && (ce != cudaSuccess ||
+                                 cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess))
+                rc = WOB_ERR_CUDA;
         }
+        for (int e = 0; e < tp->epochs && rc == WOB_OK; ++e) {
+            if (e > 0 && epoch_lr(e) != epoch_lr(e - 1))
+                rc = train_ctl_set(ctl, 0, epoch_lr(e), false, s);
+            if (rc == WOB_OK && cudaGraphLaunch(exec, s) != cudaSuccess) rc = WOB_ERR_CUDA;
+            if (rc == WOB_OK && loss_out &&
+                cudaMemcpyAsync(loss_out + (int64_t)e * steps, lrow, steps * sizeof(float),
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                rc = WOB_ERR_CUDA;
+        }
+        if (rc == WOB_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = WOB_ERR_CUDA;
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        if (rc != WOB_OK && wob_last_error()[0] == 0)
+            set_error("wob_cv_train: training graph failed (%s)", cudaGetErrorString(cudaGetLastError()));
     }
     if (rc == WOB_OK) rc = wob_cv_set_network(c, params, stream);
     cudaFreeAsync(buf, s);

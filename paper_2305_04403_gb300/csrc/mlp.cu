@@ -494,8 +494,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const float* __r
 __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m,
                            float* __restrict__ v, const float* __restrict__ partial, int blocks,
                            float* __restrict__ grad_out, float lr, float b1, float b2, float eps,
-                           int step)
+                           int step, const TrainCtl* __restrict__ ctl)
 {
+    if (ctl) {  // graph-replayed steps: step number and rate from device memory
+        step = ctl->step;
+        lr = ctl->lr;
+    }
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
         float gsum = 0.f;
@@ -511,13 +515,24 @@ __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m,
     }
 }
 
-// loss = (sum of the blocks' squared errors, in block order) / n
-__global__ void k_mlp_loss(const float* __restrict__ lp, int blocks, float n, float* out)
+// loss = (sum of the blocks' squared errors, in block order) / n; with a
+// control word, also advances its step number (after the step's Adam update)
+__global__ void k_mlp_loss(const float* __restrict__ lp, int blocks, float n, float* out,
+                           TrainCtl* __restrict__ ctl)
 {
     float s = 0.f;
     for (int b = threadIdx.x; b < blocks; b += 32) s += lp[b];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (threadIdx.x == 0) *out = s / n;
+    if (threadIdx.x == 0) {
+        if (out) *out = s / n;
+        if (ctl) ctl->step += 1;
+    }
+}
+
+__global__ void k_train_ctl(TrainCtl* ctl, int step, float lr, int set_step)
+{
+    if (set_step) ctl->step = step;
+    ctl->lr = lr;
 }
 
 // He-uniform initial weights from the counter-based stream: parameter i
@@ -580,7 +595,7 @@ int64_t mlp_train_workspace(int64_t n)
 
 int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const float* target,
                       int64_t n, float lr, int step, float* grad_out, float* loss_out, float* ws,
-                      cudaStream_t s)
+                      cudaStream_t s, TrainCtl* ctl)
 {
     if (n <= 0) return WOB_OK;
     WOB_TRY(allow_smem(g_train_configured, (const void*)k_mlp_train_tc, kTrainSmem));
@@ -590,13 +605,25 @@ int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const f
     k_mlp_train_tc<<<blocks, kTrThreads, kTrainSmem, s>>>(params, x, target, n, partial, lp);
     WOB_CUDA_TRY(cudaGetLastError());
     k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out, lr,
-                                                     0.9f, 0.999f, 1e-8f, step);
+                                                     0.9f, 0.999f, 1e-8f, step, ctl);
     WOB_CUDA_TRY(cudaGetLastError());
-    if (loss_out) {
-        k_mlp_loss<<<1, 32, 0, s>>>(lp, blocks, (float)n, loss_out);
+    if (loss_out || ctl) {
+        k_mlp_loss<<<1, 32, 0, s>>>(lp, blocks, (float)n, loss_out, ctl);
         WOB_CUDA_TRY(cudaGetLastError());
     }
     return WOB_OK;
+}
+
+int train_ctl_set(TrainCtl* ctl, int step, float lr, bool set_step, cudaStream_t s)
+{
+    k_train_ctl<<<1, 1, 0, s>>>(ctl, step, lr, set_step ? 1 : 0);
+    WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int mlp_train_prepare()
+{
+    return allow_smem(g_train_configured, (const void*)k_mlp_train_tc, kTrainSmem);
 }
 
 int mlp_train_step(float* params, float* m, float* v, const float* x, const float* target,

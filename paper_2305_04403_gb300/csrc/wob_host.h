@@ -87,8 +87,16 @@ int mlp_train_step(float* params, float* m, float* v, const float* x, const floa
                    cudaStream_t s);
 // floats of workspace a training step on n samples needs
 int64_t mlp_train_workspace(int64_t n);
+// Step number and learning rate of graph-replayed training steps, in device
+// memory: Adam reads them, the step's loss kernel advances the step.
+struct TrainCtl {
+    int step;
+    float lr;
+};
 int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const float* target,
                       int64_t n, float lr, int step, float* grad_out, float* loss_out, float* ws,
-                      cudaStream_t s);
+                      cudaStream_t s, TrainCtl* ctl = nullptr);
+int train_ctl_set(TrainCtl* ctl, int step, float lr, bool set_step, cudaStream_t s);
+int mlp_train_prepare();
 
 }  // namespace wob

@@ -239,6 +239,37 @@ def trained(wob, sphere_cv):
     return prob, p, loss.cpu().numpy()
 
 
+def test_cv_train_graph_equals_unrolled_steps(wob, sphere_cv):
+    """wob_cv_train replays one captured epoch per epoch (step number and
+    learning rate in device memory); the parameters and losses equal those
+    of the same minibatch steps launched one by one (boundary points, their
+    density targets, Adam at the step numbers and the tail epoch's rate)."""
+    v, f, mesh, bvh, cvo, nodes = sphere_cv
+    prob = wob.Problem(bvh, data_mode=wob.DATA_POLY, poly=I.POLY_CONFIG1)
+    flat, _ = _params32()
+    n, b, epochs = 1 << 14, 4096, 3
+    p = torch.from_numpy(flat).cuda()
+    m, vv = torch.zeros_like(p), torch.zeros_like(p)
+    loss = cvo.train(prob, p, m, vv, points=n, walks=16, max_len=3, point_seed=3, walk_seed=1,
+                     epochs=epochs, batch=b, lr=1e-3, lr_end=2e-4, tail_epochs=1, step0=5)
+    pts, prims = wob.sample_boundary(mesh, n, seed=3)
+    est, _ = wob.solve_density(prob, pts, prims, 16, 3, seed=1)
+    tgt = est.float()
+    p2 = torch.from_numpy(flat).cuda()
+    m2, v2 = torch.zeros_like(p2), torch.zeros_like(p2)
+    l2 = torch.empty((epochs, n // b), dtype=torch.float32, device="cuda")
+    step = 5
+    for e in range(epochs):
+        lr = 2e-4 if e == epochs - 1 else 1e-3
+        for j in range(n // b):
+            step += 1
+            wob.mlp_train_step(p2, m2, v2, pts[j * b:(j + 1) * b], tgt[j * b:(j + 1) * b], lr,
+                               step, loss=l2[e, j:j + 1])
+    torch.cuda.synchronize()
+    assert torch.equal(p, p2) and torch.equal(m, m2) and torch.equal(vv, v2)
+    assert torch.equal(loss, l2)
+
+
 def test_cv_training_fits_the_sphere_density(wob, sphere_cv, trained):
     v, f, mesh, bvh, cvo, nodes = sphere_cv
     prob, p, loss = trained
