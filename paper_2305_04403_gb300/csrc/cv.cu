@@ -211,7 +211,7 @@ __device__ __forceinline__ bool is_near(float4 tc, float3 x)
 __device__ __forceinline__ void node_acc(float4 nd, float omega, float3 x, float& s1, float& s0)
 {
     const float rx = nd.x - x.x, ry = nd.y - x.y, rz = nd.z - x.z;
-    const float ri = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+    const float ri = rsqrt_ftz(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
     const float t = ri * ri * ri;
     s1 = fmaf(nd.w, t, s1);
     s0 = fmaf(omega, t, s0);
@@ -232,7 +232,7 @@ __device__ __forceinline__ void node_acc2(float4 a, float4 b, float2 omega, cons
     const float2 ry = __fadd2_rn(make_float2(a.z, a.w), nx.y);
     const float2 rz = __fadd2_rn(make_float2(b.x, b.y), nx.z);
     const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
-    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
     const float2 t = __fmul2_rn(__fmul2_rn(ri, ri), ri);
     s1 = __ffma2_rn(make_float2(b.z, b.w), t, s1);
     s0 = __ffma2_rn(omega, t, s0);

@@ -456,7 +456,7 @@ __device__ __forceinline__ float sl_data_ff(const WalkParams& p, int64_t j, cons
     const float dx = (y.v0[0] - D.x0[0]) + y.p[0].hi;
     const float dy = (y.v0[1] - D.x0[1]) + y.p[1].hi;
     const float dz = (y.v0[2] - D.x0[2]) + y.p[2].hi;
-    const float ri = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)));
+    const float ri = rsqrt_ftz(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)));
     const float h = D.scale * ri;
     if (bc == WOB_BC_DIRICHLET) return h;
     float dn = __fmaf_rn(y.n[0].hi, dx, __fmaf_rn(y.n[1].hi, dy, y.n[2].hi * dz));
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(128, WOB_SL_MIN_BLOCKS) k_sl_walks_ff(WalkPara
                     const float r2 =
                         __fmaf_rn(r[0].hi, r[0].hi, __fmaf_rn(r[1].hi, r[1].hi, r[2].hi * r[2].hi));
                     if (r2 < rmin2) break;  // empty sample
-                    const float ri = rsqrtf(r2);
+                    const float ri = rsqrt_ftz(r2);
                     const float G = kInv4Pi * ri;
                     if (bx < 0) {
                         wf = w_query * G;
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(128, WOB_DL_MIN_BLOCKS) k_nd_walks(WalkParams 
                         const float f = sl_data_ff(p, j, y, b0, b1, b2, WOB_BC_NEUMANN);
                         float c = (k == 0) ? phi_f : 2.f * phi_f;
                         if (k == p.M) c *= 0.5f;
-                        const float G = 0.0795774715459476678f * rsqrtf(r2);
+                        const float G = 0.0795774715459476678f * rsqrt_ftz(r2);
                         ws.set(SS, fma(ws.get(PP), (double)(c * area_f * G * f), ws.get(SS)));
                     }
                 }
@@ -878,16 +878,6 @@ __global__ void k_fwd_pack(const double* __restrict__ zpos, const double* __rest
         }
         live[path] = (uint8_t)any;
     }
-}
-
-// 1 / sqrt(x), the approximate MUFU form (relative error below 2^-22), with
-// subnormal inputs and results flushed to zero: a squared distance here is
-// either 0 (a query on a path vertex) or far above the subnormal range.
-__device__ __forceinline__ float rsqrt_ftz(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
 }
 
 __global__ void __launch_bounds__(kFwdThreads)

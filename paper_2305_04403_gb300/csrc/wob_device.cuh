@@ -56,6 +56,17 @@ __device__ __forceinline__ u32x4 stream_block(StreamKey key, uint32_t q, uint32_
                          key.k1);
 }
 
+// 1 / sqrt(x), the approximate MUFU form (relative error below 2^-22), with
+// subnormal inputs and results flushed to zero: for the squared distances it
+// is used on (0, or far above the subnormal range) it is the same value as
+// rsqrtf without the instructions that handle subnormal inputs.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ double u24(uint32_t x) { return (double)(x >> 8) * 0x1p-24; }
 __device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
