@@ -1061,15 +1061,16 @@ int wob_cv_train(const wob_problem* prob, wob_cv c, const wob_cv_train_params* t
     // One epoch (every minibatch: training kernel, Adam, loss) is captured
     // once as a CUDA graph on a private stream and replayed per epoch on the
     // caller's stream: the step number and learning rate live in device
-    // memory (TrainCtl), the epoch's losses in a scratch row copied out
-    // after each replay.  The same kernels as unrolled launches.
+    // memory (TrainCtl: the training kernel advances the step, Adam reads
+    // it), the epoch's losses in a scratch row copied out after each
+    // replay.  The same kernels as unrolled launches.
     // step schedule: the last tail_epochs epochs run at lr_end
     auto epoch_lr = [&](int e) { return e >= tp->epochs - tp->tail_epochs ? tp->lr_end : tp->lr; };
     TrainCtl* ctl = reinterpret_cast<TrainCtl*>(ws + ws_floats);
     float* lrow = ws + ws_floats + 2;
     if (rc == WOB_OK && tp->epochs > 0) {
         rc = mlp_train_prepare();
-        if (rc == WOB_OK) rc = train_ctl_set(ctl, tp->step0 + 1, epoch_lr(0), true, s);
+        if (rc == WOB_OK) rc = train_ctl_set(ctl, tp->step0, epoch_lr(0), true, s);
     }
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;

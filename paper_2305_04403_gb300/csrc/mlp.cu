@@ -300,8 +300,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const float* __r
                                                                const float* __restrict__ target,
                                                                int64_t n,
                                                                float* __restrict__ partial,
-                                                               float* __restrict__ loss_partial)
+                                                               float* __restrict__ loss_partial,
+                                                               TrainCtl* __restrict__ ctl)
 {
+    // graph-replayed steps: advance the step number (the previous step's
+    // Adam update has completed; this step's reads it after this kernel)
+    if (ctl && blockIdx.x == 0 && threadIdx.x == 0) ctl->step += 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = 32 * (warp & 3) + lane;  // the row this thread owns
@@ -494,11 +498,19 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const float* __r
 __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m,
                            float* __restrict__ v, const float* __restrict__ partial, int blocks,
                            float* __restrict__ grad_out, float lr, float b1, float b2, float eps,
-                           int step, const TrainCtl* __restrict__ ctl)
+                           int step, const TrainCtl* __restrict__ ctl,
+                           const float* __restrict__ lp, float n, float* __restrict__ loss_out)
 {
     if (ctl) {  // graph-replayed steps: step number and rate from device memory
         step = ctl->step;
         lr = ctl->lr;
+    }
+    if (loss_out && blockIdx.x == 0 && threadIdx.x < 32) {
+        // loss = (sum of the blocks' squared errors, in block order) / n
+        float ls = 0.f;
+        for (int b = threadIdx.x; b < blocks; b += 32) ls += lp[b];
+        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(kFull, ls, o);
+        if (threadIdx.x == 0) *loss_out = ls / n;
     }
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
@@ -512,20 +524,6 @@ __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m,
         m[i] = mi;
         v[i] = vi;
         params[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    }
-}
-
-// loss = (sum of the blocks' squared errors, in block order) / n; with a
-// control word, also advances its step number (after the step's Adam update)
-__global__ void k_mlp_loss(const float* __restrict__ lp, int blocks, float n, float* out,
-                           TrainCtl* __restrict__ ctl)
-{
-    float s = 0.f;
-    for (int b = threadIdx.x; b < blocks; b += 32) s += lp[b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (threadIdx.x == 0) {
-        if (out) *out = s / n;
-        if (ctl) ctl->step += 1;
     }
 }
 
@@ -602,15 +600,12 @@ int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const f
     const int blocks = (int)((n + kTrainRows - 1) / kTrainRows);
     float* partial = ws;
     float* lp = ws + (int64_t)blocks * kParams;
-    k_mlp_train_tc<<<blocks, kTrThreads, kTrainSmem, s>>>(params, x, target, n, partial, lp);
+    k_mlp_train_tc<<<blocks, kTrThreads, kTrainSmem, s>>>(params, x, target, n, partial, lp, ctl);
     WOB_CUDA_TRY(cudaGetLastError());
     k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out, lr,
-                                                     0.9f, 0.999f, 1e-8f, step, ctl);
+                                                     0.9f, 0.999f, 1e-8f, step, ctl, lp, (float)n,
+                                                     loss_out);
     WOB_CUDA_TRY(cudaGetLastError());
-    if (loss_out || ctl) {
-        k_mlp_loss<<<1, 32, 0, s>>>(lp, blocks, (float)n, loss_out, ctl);
-        WOB_CUDA_TRY(cudaGetLastError());
-    }
     return WOB_OK;
 }
 

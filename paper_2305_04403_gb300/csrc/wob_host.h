@@ -88,7 +88,7 @@ int mlp_train_step(float* params, float* m, float* v, const float* x, const floa
 // floats of workspace a training step on n samples needs
 int64_t mlp_train_workspace(int64_t n);
 // Step number and learning rate of graph-replayed training steps, in device
-// memory: Adam reads them, the step's loss kernel advances the step.
+// memory: the training kernel advances the step, Adam reads both.
 struct TrainCtl {
     int step;
     float lr;
