@@ -424,6 +424,15 @@ int wob_mlp_train_step(float *params, float *adam_m, float *adam_v, const float 
                        const float *target, int64_t n, float lr, int32_t step, float *grad_out,
                        float *loss_out, void *stream);
 
+/* Test hook: the tensor-core network kernels give up the first wait on
+ * each product after `polls` mbarrier polls (default 2^26, about a second);
+ * a kernel that gives up waits (bounded) for its products in flight, frees
+ * its tensor memory and writes NaN outputs (forward) or NaN gradients and
+ * loss (training), and the context stays usable.  0 makes every first wait
+ * give up at once.  Process-wide; the previous value is returned in
+ * *previous (optional).  Calls in flight keep the value they started with. */
+int wob_debug_set_tc_wait_limit(uint32_t polls, uint32_t *previous);
+
 typedef struct wob_cv_s *wob_cv;
 /* Quadrature nodes for a mesh (level 0..3, near > 0); node values start at 0.
  * Synchronises.  The mesh must outlive the object. */

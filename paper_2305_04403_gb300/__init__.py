@@ -24,7 +24,7 @@ __all__ = [
     "WobError", "Mesh", "BVH", "Problem", "Batch", "build_mesh", "build_bvh", "solve", "solve_range",
     "solve_debug", "solve_counted", "solve_host", "solve_noalloc", "solve_density",
     "solve_batched", "get_stats",
-    "mlp_num_params", "mlp_forward", "mlp_train_step", "ControlVariate", "trace_lines", "line_axes", "philox4x32_10",
+    "mlp_num_params", "mlp_forward", "mlp_train_step", "debug_set_tc_wait_limit", "ControlVariate", "trace_lines", "line_axes", "philox4x32_10",
     "library_path", "load_library",
 ]
 
@@ -152,6 +152,7 @@ def load_library() -> ctypes.CDLL:
             "wob_mlp_num_params": ([], ctypes.c_int),
             "wob_mlp_init": ([P, U64, P], ctypes.c_int),
             "wob_mlp_forward": ([P, P, I64, P, P], ctypes.c_int),
+            "wob_debug_set_tc_wait_limit": ([U32, ctypes.POINTER(U32)], ctypes.c_int),
             "wob_mlp_train_step": ([P, P, P, P, P, I64, F, I32, P, P, P], ctypes.c_int),
             "wob_cv_create": ([P, I32, F, P, ctypes.POINTER(P)], ctypes.c_int),
             "wob_cv_set_network": ([P, P, P], ctypes.c_int),
@@ -529,6 +530,14 @@ def mlp_init(seed: int = 2, stream=None):
     p = torch.empty(mlp_num_params(), dtype=torch.float32, device="cuda")
     _check(load_library().wob_mlp_init(_ptr(p), seed, _stream(stream)))
     return p
+
+
+def debug_set_tc_wait_limit(polls: int) -> int:
+    """wob_debug_set_tc_wait_limit: polls of the first wait on each
+    tensor-core product (0: give up at once); returns the previous value."""
+    prev = ctypes.c_uint32(0)
+    _check(load_library().wob_debug_set_tc_wait_limit(polls, ctypes.byref(prev)))
+    return prev.value
 
 
 def mlp_forward(params, x, stream=None):

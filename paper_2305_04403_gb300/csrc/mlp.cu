@@ -94,6 +94,11 @@ constexpr int kTcOffW5 = kTcOffBias + 4 * 64 * 4;         // 64 FP32, then b5
 constexpr int kTcOffMisc = kTcOffW5 + 64 * 4 + 16;        // 4 mbarriers (8 B each), TMEM address
 constexpr int kTcFwdSmem = kTcOffMisc + 48;
 constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before giving up (seconds)
+// Polls of the first wait on each product (the wait that detects a failure);
+// the drain of a product still in flight after a failure always takes
+// kTcWaitLimit.  wob_debug_set_tc_wait_limit lowers it (0: every first wait
+// gives up at once) so that tests can run the failure path.
+std::atomic<uint32_t> g_tc_first_wait{kTcWaitLimit};
 static_assert(kTcOffA % 1024 == 0 && kTcOffW1 % 1024 == 0 && kTcABytes % 1024 == 0,
               "operand alignment");
 
@@ -124,7 +129,8 @@ __device__ __forceinline__ void load_layer_kmajor(const float* __restrict__ W, u
 __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const float* __restrict__ params,
                                                               const float* __restrict__ x,
                                                               int stride, int64_t n,
-                                                              float* __restrict__ out)
+                                                              float* __restrict__ out,
+                                                              uint32_t first_wait)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int qtr = threadIdx.x >> 7, tid = threadIdx.x & 127, warp = threadIdx.x >> 5;
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const float* __re
                                  tc::smem_desc(b_base + 256 * kb, 128, K * 16), kIdesc, kb > 0);
                 tc::commit(mbar);
             }
-            const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+            const bool ok = tc::mbar_wait(mbar, phase, first_wait);
             if (tc::bar_sync_or(bar, kTcRows, !ok)) {  // the quarter stops together
                 failed = true;
                 if (!ok) tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the product in flight, bounded
@@ -301,7 +307,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const float* __r
                                                                int64_t n,
                                                                float* __restrict__ partial,
                                                                float* __restrict__ loss_partial,
-                                                               TrainCtl* __restrict__ ctl)
+                                                               TrainCtl* __restrict__ ctl,
+                                                               uint32_t first_wait)
 {
     // graph-replayed steps: advance the step number (the previous step's
     // Adam update has completed; this step's reads it after this kernel)
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const float* __r
             issue();
             tc::commit(mbar);
         }
-        const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+        const bool ok = tc::mbar_wait(mbar, phase, first_wait);
         if (__syncthreads_or(!ok)) {
             if (!ok) tc::mbar_wait(mbar, phase, kTcWaitLimit);  // the products in flight, bounded
             return false;
@@ -580,7 +587,8 @@ int mlp_forward(const float* params, const float* x, int64_t n, float* out, cuda
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
     const int grid = grid_for((const void*)k_mlp_forward_tc, kTcThreads, kTcFwdSmem,
                               (tiles + 3) / 4 * kTcThreads);
-    k_mlp_forward_tc<<<grid, kTcThreads, kTcFwdSmem, s>>>(params, x, stride, n, out);
+    k_mlp_forward_tc<<<grid, kTcThreads, kTcFwdSmem, s>>>(params, x, stride, n, out,
+                                                          g_tc_first_wait.load());
     WOB_CUDA_TRY(cudaGetLastError());
     return WOB_OK;
 }
@@ -600,7 +608,8 @@ int mlp_train_step_ws(float* params, float* m, float* v, const float* x, const f
     const int blocks = (int)((n + kTrainRows - 1) / kTrainRows);
     float* partial = ws;
     float* lp = ws + (int64_t)blocks * kParams;
-    k_mlp_train_tc<<<blocks, kTrThreads, kTrainSmem, s>>>(params, x, target, n, partial, lp, ctl);
+    k_mlp_train_tc<<<blocks, kTrThreads, kTrainSmem, s>>>(params, x, target, n, partial, lp, ctl,
+                                                          g_tc_first_wait.load());
     WOB_CUDA_TRY(cudaGetLastError());
     k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, m, v, partial, blocks, grad_out, lr,
                                                      0.9f, 0.999f, 1e-8f, step, ctl, lp, (float)n,
@@ -650,6 +659,14 @@ int wob_mlp_init(float* params, uint64_t seed, void* stream)
     wob::k_mlp_init<<<(wob::kParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
         params, (uint32_t)seed, (uint32_t)(seed >> 32));
     WOB_CUDA_TRY(cudaGetLastError());
+    return WOB_OK;
+}
+
+int wob_debug_set_tc_wait_limit(uint32_t polls, uint32_t* previous)
+{
+    wob::clear_error();
+    const uint32_t old = wob::g_tc_first_wait.exchange(polls);
+    if (previous) *previous = old;
     return WOB_OK;
 }
 

@@ -58,3 +58,36 @@ def test_iteration_bound_in_other_kernels(wob):
     assert torch.isnan(out["est"]).all()
     with pytest.raises(wob.WobError):
         wob.solve(wob.Problem(bvh, iter_limit=-1), q, 4, 2)
+
+
+def test_tensor_core_wait_limit_fails_cleanly(wob):
+    """The network kernels' first wait on each tensor-core product gives up
+    after a poll limit; forced to 0, every wait gives up at once: the
+    kernels drain their products in flight, free their tensor memory and
+    write NaN (forward outputs; training gradients and loss), and the
+    context stays usable (the next calls reproduce the earlier results)."""
+    from oracle import cv as C
+    flat = torch.from_numpy(C.flatten(C.mlp_init(2)).astype(np.float32)).cuda()
+    y = torch.from_numpy(I.ball_queries(1000, 0.9, 4)).cuda()
+    tgt = torch.zeros(1000, dtype=torch.float32, device="cuda")
+    ref = wob.mlp_forward(flat, y)
+    g_ref = torch.empty_like(flat)
+    wob.mlp_train_step(flat.clone(), torch.zeros_like(flat), torch.zeros_like(flat), y, tgt, 0.0,
+                       1, grad=g_ref)
+    prev = wob.debug_set_tc_wait_limit(0)
+    try:
+        bad = wob.mlp_forward(flat, y)
+        g = torch.empty_like(flat)
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        wob.mlp_train_step(flat.clone(), torch.zeros_like(flat), torch.zeros_like(flat), y, tgt,
+                           0.0, 1, grad=g, loss=loss)
+        torch.cuda.synchronize()
+    finally:
+        wob.debug_set_tc_wait_limit(prev)
+    assert torch.isnan(bad).all()
+    assert torch.isnan(g).all() and torch.isnan(loss).all()
+    assert torch.equal(wob.mlp_forward(flat, y), ref)
+    g2 = torch.empty_like(flat)
+    wob.mlp_train_step(flat.clone(), torch.zeros_like(flat), torch.zeros_like(flat), y, tgt, 0.0,
+                       1, grad=g2)
+    assert torch.equal(g2, g_ref)
