@@ -267,6 +267,7 @@ __device__ __forceinline__ float fine_tri(const CvGeom& c, int j, float3 x, floa
     const NegPoint2 nx{make_float2(-x.x, -x.x), make_float2(-x.y, -x.y), make_float2(-x.z, -x.z)};
     float2 s1p = make_float2(0.f, 0.f), s0p = make_float2(0.f, 0.f);
     const int pairs = c.F >> 1;
+#pragma unroll 4  // four pairs' loads in flight (the far loop unrolled too runs slower)
     for (int q = 0; q < pairs; ++q)
         node_acc2(__ldg(nd + 2 * q), __ldg(nd + 2 * q + 1),
                   make_float2(c_fine_w[2 * q], c_fine_w[2 * q + 1]), nx, s1p, s0p);
