@@ -253,34 +253,47 @@ __device__ __forceinline__ float tri_term(float4 tp, float area, float3 x, float
 // shared memory by the whole block.
 constexpr int kQuadThreads = 256;
 constexpr int kTileTris = 64;
+// Near-field stage: the fine nodes of up to kNearStage / F candidate
+// triangles (at least one: F <= kMaxFine <= kNearStage).
+constexpr int kNearStage = 512;
+static_assert(kMaxFine <= kNearStage, "one triangle's fine nodes fit the stage");
 struct FarTile {
     float4 tc[kTileTris];
     float4 tp[kTileTris];
     float ta[kTileTris];
     float4 node[kTileTris * kCoarse];
+    float4 fine[kNearStage];
+    int own0;
 };
 
-// Fine-node sum of triangle j (its 4^level sub-triangles).
-__device__ __forceinline__ float fine_tri(const CvGeom& c, int j, float3 x, float fx)
+// Fine-node sum of triangle j (its 4^level sub-triangles) from its F nodes
+// at nd: global memory (read-only path) or a block's shared-memory stage.
+template <bool SHARED>
+__device__ __forceinline__ float fine_sum(const CvGeom& c, const float4* nd, int j, float3 x,
+                                          float fx)
 {
-    const float4* nd = c.fine_pk + (int64_t)c.F * j;
     const NegPoint2 nx{make_float2(-x.x, -x.x), make_float2(-x.y, -x.y), make_float2(-x.z, -x.z)};
     float2 s1p = make_float2(0.f, 0.f), s0p = make_float2(0.f, 0.f);
     const int pairs = c.F >> 1;
 #pragma unroll 4  // four pairs' loads in flight (the far loop unrolled too runs slower)
     for (int q = 0; q < pairs; ++q)
-        node_acc2(__ldg(nd + 2 * q), __ldg(nd + 2 * q + 1),
+        node_acc2(SHARED ? nd[2 * q] : __ldg(nd + 2 * q), SHARED ? nd[2 * q + 1] : __ldg(nd + 2 * q + 1),
                   make_float2(c_fine_w[2 * q], c_fine_w[2 * q + 1]), nx, s1p, s0p);
     float s1 = s1p.x + s1p.y, s0 = s0p.x + s0p.y;
-    if (c.F & 1) node_acc(__ldg(nd + c.F - 1), c_fine_w[c.F - 1], x, s1, s0);
+    if (c.F & 1) node_acc(SHARED ? nd[c.F - 1] : __ldg(nd + c.F - 1), c_fine_w[c.F - 1], x, s1, s0);
     return tri_term(__ldg(c.tri_p + j), __ldg(c.tri_a + j), x, fx, s1, s0);
+}
+
+__device__ __forceinline__ float fine_tri(const CvGeom& c, int j, float3 x, float fx)
+{
+    return fine_sum<false>(c, c.fine_pk + (int64_t)c.F * j, j, x, fx);
 }
 
 // sum over quadrature nodes of w (r . n)/(4 pi r^3) (f(y) - fx), r = y - x,
 // i.e. -int dG/dn_y (f - fx) dA, skipping triangle `own` (-1: none).
-// Called by EVERY thread of the block (the triangle tiles are loaded
-// cooperatively); `own` must be negative for all lanes of a warp or for
-// none.  The far field (coarse nodes of every triangle not near x) is an
+// Called by EVERY thread of the block (the triangle tiles and the near
+// field's fine nodes are loaded cooperatively); `own` must be negative for
+// all threads of the block or for none.  The far field (coarse nodes of every triangle not near x) is an
 // N-body sum over shared-memory tiles, FP32 within a tile and FP64 across
 // tiles.  Near triangles (fine nodes): per lane from the candidate list of
 // `own` when own >= 0; otherwise decided per triangle for the whole warp.
@@ -328,9 +341,33 @@ __device__ __forceinline__ float quad_sum(const CvGeom& c, FarTile& sm, float3 x
     }
     if (own >= 0) {
         float near_tot = 0.f;
-        for (int ci = own == 0 ? 0 : c.cand_off[own - 1]; ci < c.cand_off[own]; ++ci) {
-            const int j = c.cand[ci];
-            if (is_near(__ldg(c.tri_c + j), x)) near_tot += fine_tri(c, j, x, fx);
+        __syncthreads();  // the last far tile is no longer read
+        if (threadIdx.x == 0) sm.own0 = own;
+        __syncthreads();
+        if (__syncthreads_and(own == sm.own0)) {
+            // the whole block shares the triangle (the walks are bucketed by
+            // it): its candidates' fine nodes are staged in shared memory,
+            // chunk by chunk, and read by every lane as broadcasts; the
+            // candidates are visited in the same order as below
+            const int beg = own == 0 ? 0 : c.cand_off[own - 1], end = c.cand_off[own];
+            const int per = kNearStage / c.F;
+            for (int c0 = beg; c0 < end; c0 += per) {
+                const int nt = min(per, end - c0);
+                __syncthreads();  // the previous chunk is no longer read
+                for (int i = threadIdx.x; i < nt * c.F; i += blockDim.x)
+                    sm.fine[i] = __ldg(c.fine_pk + (int64_t)c.F * c.cand[c0 + i / c.F] + i % c.F);
+                __syncthreads();
+                for (int k = 0; k < nt; ++k) {
+                    const int j = c.cand[c0 + k];
+                    if (is_near(__ldg(c.tri_c + j), x))
+                        near_tot += fine_sum<true>(c, sm.fine + k * c.F, j, x, fx);
+                }
+            }
+        } else {
+            for (int ci = own == 0 ? 0 : c.cand_off[own - 1]; ci < c.cand_off[own]; ++ci) {
+                const int j = c.cand[ci];
+                if (is_near(__ldg(c.tri_c + j), x)) near_tot += fine_tri(c, j, x, fx);
+            }
         }
         tot += (double)near_tot;
     }
