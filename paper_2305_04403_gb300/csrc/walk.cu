@@ -364,25 +364,6 @@ struct FFPoint {
     ff n[3];      // unit normal of the triangle
 };
 
-// Sum of products a_i b_i of three float-float pairs, as a float-float
-// (two-product and two-sum on the hi parts, the lo cross terms added to the
-// error; the lo x lo products, below 2^-48 relative, are dropped).
-__device__ __forceinline__ ff ff_dot3(const ff (&a)[3], const ff (&b)[3])
-{
-    ff s = two_prod(a[0].hi, b[0].hi);
-    float e = __fmaf_rn(a[0].hi, b[0].lo, __fmul_rn(a[0].lo, b[0].hi));
-#pragma unroll
-    for (int c = 1; c < 3; ++c) {
-        const ff pc = two_prod(a[c].hi, b[c].hi);
-        const ff t = two_sum(s.hi, pc.hi);
-        s.hi = t.hi;
-        e = __fadd_rn(e, __fadd_rn(t.lo, pc.lo));
-        e = __fmaf_rn(a[c].hi, b[c].lo, __fmaf_rn(a[c].lo, b[c].hi, e));
-    }
-    e = __fadd_rn(e, s.lo);
-    return fast_two_sum(s.hi, e);
-}
-
 // Area-uniform boundary point of stream (q, w, step) in the compensated
 // form: triangle j by area_pick, then (frame_point_ff, uniforms uz, uw) the
 // square-root warp b1 = sqrt(u1) (1 - u2), b2 = sqrt(u1) u2 with sqrt(u1) in
