@@ -503,11 +503,14 @@ int wob_sample_boundary(wob_mesh m, int64_t n, uint64_t seed, uint32_t problem, 
  * with walk_seed).  Then `epochs` passes of Adam (lr) over minibatches of
  * `batch` consecutive points (the points are independent draws, so fixed
  * order is a valid stochastic gradient) at rate lr, the last tail_epochs of
- * them at lr_end; the Adam step counter starts at step0 + 1.  params / adam_m / adam_v (device, n_params floats each) are
- * updated in place; loss_out (device, optional) receives the minibatch MSE
- * of every step, epochs x ceil(points / batch) floats.  The library
- * allocates points x 36 bytes of scratch on `stream` and frees it before
- * returning.  prob: WOB_DIRICHLET_DL on c's mesh.
+ * them at lr_end; the Adam step counter starts at step0 + 1.  params /
+ * adam_m / adam_v (device, n_params floats each) are updated in place;
+ * loss_out (device, optional) receives the minibatch MSE of every step,
+ * epochs x ceil(points / batch) floats.  One epoch of steps is captured as
+ * a CUDA graph (on a stream of the library's own) and replayed on `stream`
+ * once per epoch; the call synchronises `stream` before returning.  The
+ * library allocates about points x 36 bytes of scratch on `stream` and
+ * frees it before returning.  prob: WOB_DIRICHLET_DL on c's mesh.
  */
 typedef struct {
     int64_t points;      /* training points (1 .. 2^31 - 1) */
