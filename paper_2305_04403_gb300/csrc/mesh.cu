@@ -229,8 +229,9 @@ int inclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s)
 template int inclusive_scan<double>(const double*, double*, int64_t, cudaStream_t);
 template int inclusive_scan<int>(const int*, int*, int64_t, cudaStream_t);
 
-// FP64 copy of the vertex positions: area samples are formed in FP64 from
-// it without a conversion per coordinate (exact: every float is a double).
+// FP64 copy of the vertex positions: the resampled single-layer walks form
+// their area samples in FP64 from it without a conversion per coordinate
+// (exact: every float is a double).
 __global__ void k_to_f64(const float* __restrict__ in, int64_t n, double* __restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

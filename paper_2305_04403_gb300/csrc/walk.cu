@@ -44,10 +44,11 @@ constexpr double kFourPi = 12.566370614359172953850573533118;
 // global counter until none are left (dynamic balance; consecutive walks of
 // a query start their first lines at the same point).  Per line:
 // draw the axis, traverse (descend to a leaf, test it, repeat), then pick
-// the hit (keys only when m > 1), refine it in FP64 and accumulate.  The
-// kernel is limited to 64 registers (8 blocks of 128 threads per SM): the
-// traversal is latency-bound and occupancy pays more than the few values
-// the compiler keeps in local memory.  Lanes that start their lines
+// the hit (keys only when m > 1), refine it in float-float and add the
+// data term (evaluated in FP32) to the FP64 walk sum.  The kernel is
+// limited to 64 registers (8 blocks of 128 threads per SM): the traversal
+// is latency-bound and occupancy pays more than the few values the
+// compiler keeps in local memory.  Lanes that start their lines
 // together share the fetches of the upper tree levels; variants that broke
 // this (persistent lanes refilled from a global counter, or a wavefront of
 // separate traversal and FP64-update kernels) measured 8-18% slower.

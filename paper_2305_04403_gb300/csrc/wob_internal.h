@@ -55,7 +55,7 @@ static_assert(sizeof(TriFrame) == 96, "six float4");
 
 struct MeshDev {
     float* verts = nullptr;   // V x 3
-    double* verts_d = nullptr;  // V x 3, the same positions in FP64 (area sampling)
+    double* verts_d = nullptr;  // V x 3, the same positions in FP64 (resampled area samples)
     int32_t* tris = nullptr;  // T x 3
     NormalArea* tri_n = nullptr;  // unit normal (FP64), area
     TriFrame* tri_f = nullptr;    // compensated FP32 frame of each triangle
@@ -101,7 +101,7 @@ struct WalkParams {
     const int32_t* inv_order;
     int iter_limit;  // traversal loop bound (4 x wide nodes + 64)
     const float* verts;
-    const double* verts_d;  // FP64 copy of verts
+    const double* verts_d;  // FP64 copy of verts (resampled area samples)
     const int32_t* tris;
     const NormalArea* tri_n;
     const TriFrame* tri_f;
