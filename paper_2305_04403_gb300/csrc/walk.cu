@@ -19,6 +19,7 @@
 #include <cstddef>
 #include <cstdlib>
 
+#include "bits.cuh"
 #include "ff.cuh"
 #include "wob_device.cuh"
 #include "wob_host.h"
@@ -158,17 +159,6 @@ __device__ __forceinline__ double sl_data(const WalkParams& p, int64_t j, double
 // pipe, which issues at 1/64 of the FP32 rate on this GPU).  The target is
 // one FP64 multiply, (U 2^-53) |Gamma|; U 2^-53 is exact and formed from its
 // bit pattern in the integer pipes (u53_unit).
-__device__ __forceinline__ double u53_unit(uint64_t U)
-{
-    // U = 1.f 2^k with k = 63 - clz(U): the significand is U shifted so its
-    // leading one sits at bit 52, where adding it carries 1 into the
-    // exponent field, which therefore holds 1023 + k - 53 - 1 beforehand
-    const int lz = __clzll((long long)U);
-    const unsigned long long bits =
-        ((unsigned long long)(1032 - lz) << 52) + ((unsigned long long)U << (lz - 11));
-    return U != 0 ? __longlong_as_double((long long)bits) : 0.0;
-}
-
 __device__ __forceinline__ int64_t area_pick(const WalkParams& p, uint32_t hi, uint32_t lo)
 {
     const uint64_t U = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
@@ -462,21 +452,6 @@ __device__ __forceinline__ float sl_data_ff(const WalkParams& p, int64_t j, cons
     }
     const float dhdn = -h * ri * ri * dn;
     return bc == WOB_BC_ROBIN ? __fmaf_rn(p.alpha, h, dhdn) : dhdn;
-}
-
-// The double t 2^e of an FP32 value t (exact), assembled from t's bits in
-// the integer pipes (sign, exponent rebiased and shifted by e, the 23-bit
-// significand at the top of the double's 52): no conversion on the FP64
-// pipe.  Zero, subnormal, infinite and NaN t and results outside the
-// normal range take ldexp.
-__device__ __forceinline__ double scale2(float t, int e)
-{
-    const uint32_t b = __float_as_uint(t);
-    const int ef = (int)((b >> 23) & 0xFFu);
-    const int ex = ef - 127 + 1023 + e;
-    if (ef == 0 || ef == 255 || ex <= 0 || ex >= 2047) return t == 0.f ? 0.0 : ldexp((double)t, e);
-    return __hiloint2double((int)((b & 0x80000000u) | ((uint32_t)ex << 20) | ((b & 0x7FFFFFu) >> 3)),
-                            (int)(b << 29));
 }
 
 // The single-layer walks of k_sl_walks for area sampling (p.ris <= 1), in
