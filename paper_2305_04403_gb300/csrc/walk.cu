@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(128) k_sl_walks(WalkParams p)
 // (whose terms can cancel) are float-float sums; 1 / r, G and dG/dn_x are
 // FP32 with relative error ~1e-7.  The product of weights is an FP32
 // significand renormalised every step with an integer exponent; FP64 holds
-// only the sum of terms (one conversion and one add per step) and the CDF
-// target.
+// only the sum of terms (one add per step, the term assembled exactly from
+// its bits by scale2) and the CDF target (one multiply).
 // ---------------------------------------------------------------------------
 
 // A boundary point in the compensated representation.
