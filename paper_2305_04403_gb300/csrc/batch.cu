@@ -533,7 +533,11 @@ int wob_solve_batched(const wob_problem* problems, int32_t P, const int64_t* que
     wob_batch b = nullptr;
     int rc = wob_batch_create(problems, P, query_offsets, walks, max_len, queries, est, var,
                               nullptr, stream, &b);
-    if (rc != WOB_OK) return rc;
+    if (rc != WOB_OK) {  // report under this entry point's name
+        const std::string inner = wob_last_error();
+        set_error("wob_solve_batched (creating the batch): %s", inner.c_str());
+        return rc;
+    }
     rc = wob_batch_run(b, seed, stream);
     const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     wob_batch_destroy(b);

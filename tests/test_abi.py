@@ -80,6 +80,75 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib_path):
     assert b"wob_probe_l2_read" in lib.wob_last_error()
 
 
+# Entry points without a required pointer argument (they succeed without a
+# device); every other declared function is in the NULL-argument sweep.
+_NO_REQUIRED_POINTER = {"wob_version", "wob_mlp_num_params", "wob_debug_set_tc_wait_limit",
+                        "wob_last_error"}
+
+_SWEEP = r"""
+import ctypes, json, sys
+lib = ctypes.CDLL(sys.argv[1])
+lib.wob_last_error.restype = ctypes.c_char_p
+kinds = {"p": (ctypes.c_void_p, None), "i64": (ctypes.c_int64, 4), "i32": (ctypes.c_int32, 4),
+         "u64": (ctypes.c_uint64, 0), "u32": (ctypes.c_uint32, 0), "f": (ctypes.c_float, 0.5),
+         "i": (ctypes.c_int, 0)}
+out = {}
+for name, ret, args in json.loads(sys.argv[2]):
+    f = getattr(lib, name)
+    f.argtypes = [kinds[a][0] for a in args]
+    f.restype = None if ret == "void" else ctypes.c_int
+    rc = f(*[kinds[a][1] for a in args])
+    out[name] = [rc, lib.wob_last_error().decode()]
+print(json.dumps(out))
+"""
+
+
+def _signatures():
+    """(name, return type, argument kinds) of the functions in include/wob.h:
+    "p" for pointers and opaque handles, else the integer or float width."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "wob.h")).read(), flags=re.S)
+    sigs = []
+    for ret, name, params in re.findall(r"^(int|void)\s+(wob_\w+)\s*\(([^;]*?)\)\s*;", src,
+                                        flags=re.M | re.S):
+        args = []
+        for p in " ".join(params.split()).split(","):
+            p = p.strip()
+            if not p or p == "void":
+                continue
+            t = p.split()[0] if p.split()[0] != "const" else p.split()[1]
+            if "*" in p or t in ("wob_mesh", "wob_bvh", "wob_cv", "wob_batch"):
+                args.append("p")
+            else:
+                args.append({"int64_t": "i64", "int32_t": "i32", "uint64_t": "u64",
+                             "uint32_t": "u32", "float": "f", "int": "i"}[t])
+        sigs.append((name, ret, args))
+    return sigs
+
+
+def test_every_entry_point_rejects_null_arguments(lib_path):
+    """Every declared call given NULL pointers and handles (and small sizes)
+    returns WOB_ERR_INVALID_ARG with a message, or for the destroy calls
+    returns quietly; -1 rather than WOB_ERR_CUDA on this GPU-less machine
+    also shows that the check comes before any CUDA call.  The calls run in
+    a child process, so a crash fails this test instead of the session."""
+    import json
+    import subprocess
+    import sys
+    sigs = [s for s in _signatures() if s[0] not in _NO_REQUIRED_POINTER]
+    assert {s[0] for s in sigs} | _NO_REQUIRED_POINTER == set(_declared())
+    r = subprocess.run([sys.executable, "-c", _SWEEP, lib_path, json.dumps(sigs)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    for name, ret, _ in sigs:
+        rc, msg = out[name]
+        if ret == "void":
+            assert rc is None, name
+        else:
+            assert rc == -1 and msg, (name, rc, msg)
+    assert out["wob_solve_batched"][1].startswith("wob_solve_batched")
+
+
 def _ptxas_functions(log):
     """(function, registers, spill-store bytes) from a ptxas -v log."""
     out = []
