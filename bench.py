@@ -305,7 +305,7 @@ def run_ours(args):
         "per_line": {"nodes": st["node_visits"] / lines, "tris": st["tri_tests"] / lines,
                      "hits": st["hits"] / lines, "flagged": st["flagged"] / lines},
     }
-    if not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline:  # the oracle's host timing: N = 1 only
         line["cpu_baseline"] = cpu_baseline(v, f, q, args.cpu_queries)
     if dist:
         dist.destroy_process_group()
