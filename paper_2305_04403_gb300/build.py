@@ -2,10 +2,14 @@
 
 Each .cu file is compiled by its own nvcc process (in parallel) and the
 objects are linked into ``paper_2305_04403_gb300/_build/libwob.so``.
+Processes that build at the same time (the ranks of a multi-GPU run)
+take turns under a file lock; the ones after the first find the library
+up to date.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -51,6 +55,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and up_to_date():  # built by another process meanwhile
+            return LIB
+        return _build_locked(verbose)
+
+
+def _build_locked(verbose: bool) -> str:
     nvcc = _nvcc()
     srcs = _sources()
 
