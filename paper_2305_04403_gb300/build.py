@@ -56,7 +56,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT, exist_ok=True)
     with open(os.path.join(OUT, ".build.lock"), "w") as lock:
-        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            fcntl.flock(lock, fcntl.LOCK_EX)
+        except OSError:  # a filesystem without locks: build unserialised
+            pass
         if not force and up_to_date():  # built by another process meanwhile
             return LIB
         return _build_locked(verbose)
